@@ -1,0 +1,229 @@
+"""Staggered (MAC) Stokes operator and its inverses (oracle, FP64).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Sec. 2, Eq. 8: the semi-implicit Stokes system [H_c  -grad_c p ; div u = 0].
+Scaling used here (the paper's Eq. 8 multiplied by -dt, viscosity 1/Re):
+
+    (I - lam*Delta_c) u_c + dt * (G p)_c = f_c,  c in {u, v, w},   D u = 0,
+    lam = dt / Re,
+
+on a staggered grid with no-slip walls: u on the interior x-faces, v on the
+interior y-faces, w on the interior z-faces, p at cell centres.  The velocity
+Laplacian of component c uses the face operator along c and the cell-Dirichlet
+operator across it; D and G are the staggered div and grad of
+oracle/operators1d.py.  Pressure is defined up to a constant (Sec. 2); it is
+returned with zero volume-weighted mean.
+
+The three-step semi-direct inverse (Sec. 2, 3D steps after Eq. 9), with q = dt*p:
+  1. u_hat_c = H_c^{-1} f_c
+  2. solve C q = D u_hat,  C = sum_c D_c H_c^{-1} G_c   (Eq. 9, the pressure matrix)
+  3. u_c = u_hat_c - H_c^{-1} (G q)_c
+Step 2 is solved by a Krylov method preconditioned by the inverse pressure
+Laplacian L_p = D G (Sec. 2, after Eq. 9); plain BiCGstab (van der Vorst) is
+used here in place of the paper's BiCGstab(2).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import assembled as asm
+from . import decomposition as dec
+from . import operators1d as o1
+
+COMPONENTS = ("u", "v", "w")
+
+
+def component_ops(faces, c):
+    """Three (m, K) 1D operators (x, y, z) of velocity component c (0, 1, 2)."""
+    ops = []
+    for d in range(3):
+        if d == c:
+            ops.append(o1.face_operator(faces[d]))
+        else:
+            ops.append(o1.cell_operator(faces[d], o1.DIRICHLET, o1.DIRICHLET))
+    return ops
+
+
+def pressure_ops(faces):
+    return [o1.cell_operator(faces[d], o1.NEUMANN, o1.NEUMANN) for d in range(3)]
+
+
+def _kron3(Az, Ay, Ax):
+    return sp.kron(sp.csr_matrix(Az), sp.kron(sp.csr_matrix(Ay), sp.csr_matrix(Ax))).tocsr()
+
+
+def div_grad_3d(faces):
+    """Sparse D_c (cells <- component c) and G_c (component c <- cells), Eq. 30-31."""
+    n = [len(f) - 1 for f in faces]
+    I = [sp.identity(n[d]) for d in range(3)]
+    Dd = [o1.div_1d(faces[d]) for d in range(3)]
+    Gd = [o1.grad_1d(faces[d]) for d in range(3)]
+    D = [_kron3(I[2], I[1], Dd[0]), _kron3(I[2], Dd[1], I[0]), _kron3(Dd[2], I[1], I[0])]
+    G = [_kron3(I[2], I[1], Gd[0]), _kron3(I[2], Gd[1], I[0]), _kron3(Gd[2], I[1], I[0])]
+    return D, G
+
+
+def shapes(faces):
+    nx, ny, nz = (len(f) - 1 for f in faces)
+    return [(nz, ny, nx - 1), (nz, ny - 1, nx), (nz - 1, ny, nx)], (nz, ny, nx)
+
+
+def saddle_matrix(faces, dt, Re):
+    """Assembled Stokes matrix of Eq. 8 in the scaling of the module docstring."""
+    lam = dt / Re
+    H = [asm.helmholtz(component_ops(faces, c), lam) for c in range(3)]
+    D, G = div_grad_3d(faces)
+    return sp.bmat([[H[0], None, None, dt * G[0]],
+                    [None, H[1], None, dt * G[1]],
+                    [None, None, H[2], dt * G[2]],
+                    [D[0], D[1], D[2], None]]).tocsr()
+
+
+def _split(x, faces):
+    vs, ps = shapes(faces)
+    out, o = [], 0
+    for s in vs + [ps]:
+        sz = int(np.prod(s))
+        out.append(x[o:o + sz].reshape(s))
+        o += sz
+    return out
+
+
+def stokes_direct(faces, dt, Re, f):
+    """Direct sparse solve of the bordered saddle system (the plain definition).
+
+    The extra unknown mu multiplies a column of ones on the continuity rows and
+    the extra row imposes zero volume-weighted mean pressure.
+    """
+    S = saddle_matrix(faces, dt, Re)
+    vs, ps = shapes(faces)
+    nv = sum(int(np.prod(s)) for s in vs)
+    npr = int(np.prod(ps))
+    vol = asm.volumes(pressure_ops(faces))
+    col = np.zeros((S.shape[0], 1))
+    col[nv:, 0] = 1.0
+    row = np.zeros((1, S.shape[0]))
+    row[0, nv:] = vol
+    B = sp.bmat([[S, sp.csr_matrix(col)], [sp.csr_matrix(row), None]]).tocsc()
+    rhs = np.concatenate([np.ravel(fc) for fc in f] + [np.zeros(npr), [0.0]])
+    x = spla.splu(B).solve(rhs)[:-1]
+    u, v, w, p = _split(x, faces)
+    return (u, v, w), p
+
+
+def saddle_residual(faces, dt, Re, f, vel, p):
+    """(momentum relative residual, ||D u||_2 / ||u||_2) with assembled operators."""
+    lam = dt / Re
+    D, G = div_grad_3d(faces)
+    num = 0.0
+    den = 0.0
+    for c in range(3):
+        Hc = asm.helmholtz(component_ops(faces, c), lam)
+        r = np.ravel(f[c]) - Hc @ np.ravel(vel[c]) - dt * (G[c] @ np.ravel(p))
+        num += float(np.dot(r, r))
+        den += float(np.dot(np.ravel(f[c]), np.ravel(f[c])))
+    div = sum(D[c] @ np.ravel(vel[c]) for c in range(3))
+    un = np.sqrt(sum(float(np.dot(np.ravel(vel[c]), np.ravel(vel[c]))) for c in range(3)))
+    return float(np.sqrt(num / den)), float(np.linalg.norm(div) / max(un, 1e-300))
+
+
+def pressure_matrix(faces, dt, Re):
+    """Dense C = sum_c D_c H_c^{-1} G_c (Eq. 9), for tiny grids."""
+    lam = dt / Re
+    D, G = div_grad_3d(faces)
+    C = None
+    for c in range(3):
+        Hc = asm.helmholtz(component_ops(faces, c), lam).tocsc()
+        X = spla.splu(Hc).solve(G[c].toarray())
+        term = D[c] @ X
+        C = term if C is None else C + term
+    return np.asarray(C)
+
+
+def stokes_three_step_dense(faces, dt, Re, f):
+    """The three steps of Sec. 2 with an explicitly formed dense C (tiny grids)."""
+    lam = dt / Re
+    D, G = div_grad_3d(faces)
+    Hs = [spla.splu(asm.helmholtz(component_ops(faces, c), lam).tocsc()) for c in range(3)]
+    uhat = [Hs[c].solve(np.ravel(f[c])) for c in range(3)]
+    b = sum(D[c] @ uhat[c] for c in range(3))
+    C = pressure_matrix(faces, dt, Re)
+    vol = asm.volumes(pressure_ops(faces))
+    N = C.shape[0]
+    B = np.zeros((N + 1, N + 1))
+    B[:N, :N] = C
+    B[:N, N] = 1.0
+    B[N, :N] = vol
+    q = np.linalg.solve(B, np.concatenate([b, [0.0]]))[:N]
+    vs, ps = shapes(faces)
+    vel = [(uhat[c] - Hs[c].solve(G[c] @ q)).reshape(vs[c]) for c in range(3)]
+    return tuple(vel), (q / dt).reshape(ps)
+
+
+def bicgstab(apply_A, apply_Minv, b, tol, maxiter):
+    """Right-preconditioned BiCGstab (van der Vorst 1992), FP64 scalars.
+
+    Returns (x, iterations, ||b - A x|| / ||b||)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return x, 0, 0.0
+    rhat = r.copy()
+    rho_old = alpha = omega = 1.0
+    v = np.zeros_like(b)
+    p = np.zeros_like(b)
+    it = 0
+    rel = 1.0
+    while it < maxiter:
+        it += 1
+        rho = float(np.dot(rhat, r))
+        beta = (rho / rho_old) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        phat = apply_Minv(p)
+        v = apply_A(phat)
+        alpha = rho / float(np.dot(rhat, v))
+        s = r - alpha * v
+        shat = apply_Minv(s)
+        t = apply_A(shat)
+        omega = float(np.dot(t, s)) / float(np.dot(t, t))
+        x = x + alpha * phat + omega * shat
+        r = s - omega * t
+        rho_old = rho
+        rel = float(np.linalg.norm(r)) / bnorm
+        if rel <= tol:
+            break
+    return x, it, rel
+
+
+def stokes_semi_direct(faces, dt, Re, f, tol=1e-11, maxiter=200, method="tpt"):
+    """Three-step semi-direct Stokes inverse (Sec. 2): direct Helmholtz inverses by
+    the decomposition solvers, BiCGstab on C preconditioned by L_p^{-1}.
+
+    Returns ((u, v, w), p, iterations, relative C-residual)."""
+    lam = dt / Re
+    D, G = div_grad_3d(faces)
+    vs, ps = shapes(faces)
+    cops = [component_ops(faces, c) for c in range(3)]
+    pops = pressure_ops(faces)
+
+    def Hinv(c, g):
+        return dec.solve(np.reshape(g, vs[c]), cops[c], lam, 1.0, method).ravel()
+
+    def Lp_inv(g):
+        # L_p = D G is the zero-flux Laplacian; -L_p^{-1} is the Laplace solve
+        return -dec.solve(np.reshape(g, ps), pops, 1.0, 0.0, method).ravel()
+
+    def C(q):
+        return sum(D[c] @ Hinv(c, G[c] @ q) for c in range(3))
+
+    uhat = [Hinv(c, f[c]) for c in range(3)]
+    b = sum(D[c] @ uhat[c] for c in range(3))
+    q, it, rel = bicgstab(C, Lp_inv, b, tol, maxiter)
+    vol = asm.volumes(pops)
+    q = q - np.dot(vol, q) / vol.sum()
+    vel = tuple((uhat[c] - Hinv(c, G[c] @ q)).reshape(vs[c]) for c in range(3))
+    return vel, (q / dt).reshape(ps), it, rel

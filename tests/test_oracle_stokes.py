@@ -1,0 +1,133 @@
+"""Pins of the oracle's staggered Stokes inverse (Sec. 2, Eq. 8-9, the three-step
+algorithm and the preconditioned Krylov solve of the pressure matrix)."""
+import numpy as np
+import pytest
+
+from oracle import assembled as asm
+from oracle import stokes as st
+from workloads import box_faces, mac_shapes, rhs_gaussian, tanh_faces
+
+
+def _faces():
+    return [tanh_faces(4, 1.5), tanh_faces(5, 1.5), tanh_faces(6, 2.0)]
+
+
+def _forcing(faces, seed=0):
+    vs, _ = st.shapes(faces)
+    return [rhs_gaussian(vs[c], seed + c) for c in range(3)]
+
+
+def test_shapes_match_workloads():
+    faces = _faces()
+    vs, ps = st.shapes(faces)
+    ms = mac_shapes((4, 5, 6))
+    assert vs == [ms["u"], ms["v"], ms["w"]] and ps == ms["p"]
+
+
+@pytest.mark.parametrize("dt", [1e-2, 1.0, 1e3])
+def test_direct_solve_residual_and_divergence(dt):
+    faces = _faces()
+    f = _forcing(faces)
+    vel, p = st.stokes_direct(faces, dt, 1000.0, f)
+    mom, div = st.saddle_residual(faces, dt, 1000.0, f, vel, p)
+    assert mom < 1e-12 and div < 1e-12
+    vol = asm.volumes(st.pressure_ops(faces))
+    assert abs(np.dot(vol, p.ravel())) < 1e-12 * np.abs(p).max()
+
+
+def test_manufactured_pressure_only():
+    # f = dt * G p0 with zero-mean p0 has the exact solution u = 0, p = p0
+    faces = _faces()
+    dt = 0.5
+    _, ps = st.shapes(faces)
+    vol = asm.volumes(st.pressure_ops(faces))
+    p0 = rhs_gaussian(ps, 11).ravel()
+    p0 -= np.dot(vol, p0) / vol.sum()
+    D, G = st.div_grad_3d(faces)
+    vs, _ = st.shapes(faces)
+    f = [(dt * (G[c] @ p0)).reshape(vs[c]) for c in range(3)]
+    vel, p = st.stokes_direct(faces, dt, 100.0, f)
+    assert max(np.abs(v).max() for v in vel) < 1e-11 * np.abs(p0).max()
+    assert np.abs(p.ravel() - p0).max() < 1e-11 * np.abs(p0).max()
+
+
+def test_manufactured_divergence_free_velocity():
+    # u = v - G (DG)^+ D v is discretely divergence free; with p0 it gives
+    # f = H u + dt G p0 and the solve must return (u, p0)
+    faces = _faces()
+    dt, Re = 2.0, 50.0
+    lam = dt / Re
+    D, G = st.div_grad_3d(faces)
+    vs, ps = st.shapes(faces)
+    vol = asm.volumes(st.pressure_ops(faces))
+    v = [rhs_gaussian(vs[c], 20 + c).ravel() for c in range(3)]
+    Lp = sum((D[c] @ G[c]).toarray() for c in range(3))
+    dv = sum(D[c] @ v[c] for c in range(3))
+    phi = np.linalg.lstsq(Lp, dv, rcond=None)[0]
+    u = [v[c] - G[c] @ phi for c in range(3)]
+    assert np.abs(sum(D[c] @ u[c] for c in range(3))).max() < 1e-10
+    p0 = rhs_gaussian(ps, 30).ravel()
+    p0 -= np.dot(vol, p0) / vol.sum()
+    f = [(asm.helmholtz(st.component_ops(faces, c), lam) @ u[c] + dt * (G[c] @ p0)).reshape(vs[c])
+         for c in range(3)]
+    vel, p = st.stokes_direct(faces, dt, Re, f)
+    for c in range(3):
+        assert np.abs(vel[c].ravel() - u[c]).max() < 1e-10 * np.abs(u[c]).max()
+    assert np.abs(p.ravel() - p0).max() < 1e-10 * np.abs(p0).max()
+
+
+@pytest.mark.parametrize("dt", [1e-2, 1e3])
+def test_three_step_equals_direct(dt):
+    faces = _faces()
+    f = _forcing(faces, 5)
+    vel_d, p_d = st.stokes_direct(faces, dt, 1000.0, f)
+    vel_t, p_t = st.stokes_three_step_dense(faces, dt, 1000.0, f)
+    for c in range(3):
+        assert np.abs(vel_t[c] - vel_d[c]).max() < 1e-10 * np.abs(vel_d[c]).max()
+    assert np.abs(p_t - p_d).max() < 1e-9 * np.abs(p_d).max()
+
+
+@pytest.mark.parametrize("dt", [1e-2, 1.0, 1e3])
+def test_semi_direct_bicgstab_equals_direct(dt):
+    faces = _faces()
+    f = _forcing(faces, 9)
+    vel_d, p_d = st.stokes_direct(faces, dt, 1000.0, f)
+    vel, p, it, rel = st.stokes_semi_direct(faces, dt, 1000.0, f, tol=1e-12)
+    assert rel <= 1e-12 and it < 60
+    for c in range(3):
+        assert np.abs(vel[c] - vel_d[c]).max() < 1e-9 * np.abs(vel_d[c]).max()
+    assert np.abs(p - p_d).max() < 1e-8 * np.abs(p_d).max()
+
+
+def test_chorin_limit():
+    # dt -> 0: H -> I and C -> D G, the pressure Laplacian (Sec. 2, after Eq. 9)
+    faces = _faces()
+    D, G = st.div_grad_3d(faces)
+    Lp = sum((D[c] @ G[c]).toarray() for c in range(3))
+    errs = []
+    for dt in (1e-4, 1e-5, 1e-6):
+        C = st.pressure_matrix(faces, dt, 1.0)
+        errs.append(np.abs(C - Lp).max() / np.abs(Lp).max())
+    errs = np.array(errs)
+    assert errs[-1] < 1e-2 and np.all(errs[:-1] / errs[1:] > 5.0), errs
+
+
+def test_pressure_matrix_is_volume_self_adjoint_not_symmetric():
+    # C is not symmetric as a plain matrix on a stretched grid (Sec. 2), but V*C is
+    # symmetric because D = -V^{-1} G^T M_u
+    faces = _faces()
+    C = st.pressure_matrix(faces, 0.3, 10.0)
+    vol = asm.volumes(st.pressure_ops(faces))
+    VC = vol[:, None] * C
+    assert np.abs(VC - VC.T).max() < 1e-11 * np.abs(VC).max()
+    assert np.abs(C - C.T).max() > 1e-6 * np.abs(C).max()
+    # singular: constants are in the null space
+    assert np.abs(C @ np.ones(C.shape[0])).max() < 1e-10 * np.abs(C).max()
+
+
+def test_preconditioned_iterations_small_at_small_dt():
+    # with the pressure-Laplacian preconditioner C is close to identity at small dt
+    faces = [tanh_faces(8, 1.5)] * 3
+    f = _forcing(faces, 2)
+    _, _, it_small, _ = st.stokes_semi_direct(faces, 1e-2, 1000.0, f, tol=1e-10)
+    assert it_small <= 3
