@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark: grid points per second of the 3D Helmholtz inverse at 256^3.
+
+Workload: 256^3 cell grid on [0,1]^3, tanh stretching factor 1.5 in every
+direction, Dirichlet walls, lambda = dt/Re = 1e3/1000 = 1, eigen transforms in
+x and y with the Thomas algorithm along z (TPT), right-hand side i.i.d.
+uniform[-1, 1] (seed 0 + rank).  One step = one complete solve
+(I - lambda*Delta) u = f to the path's residual tolerance, including every
+refinement step and the final residual check.
+
+Arms: the plain FP64 path (tolerance 1e-11) and, when available, the mixed
+path (split tensor-core transforms, tolerance 1e-10).  `value` is the faster
+arm that met its tolerance.  The field is 134 MB and the working set several
+times larger than the 129 MB L2, so no extra L2 flush is needed between steps.
+
+Multi-GPU: the solves are independent problems, so N GPUs run N replicas
+("scaling": "weak"), one per rank, with no data-path collective; value is the
+points solved by all ranks divided by the slowest rank's time.
+
+`--impl reference` times the FP64 CPU oracle (NumPy TPT) on the host cores on
+the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+N_DEFAULT = 256
+BETA = 1.5
+LAM = 1e3 / 1000.0
+METRIC = "grid-pts/s per Helmholtz solve at 256^3"
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07  # SMs x FP64 FMA/clk/SM x 2 flop x GHz (about 1.26 TFLOP/s)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_tpt_time(n, seed=0):
+    """Time one FP64 oracle TPT solve (NumPy) on the host cores."""
+    from oracle import assembled as asm
+    from oracle import decomposition as dec
+    faces = workloads.box_faces(n, BETA)
+    ops = asm.cell_ops(faces, (0, 0, 0), (0, 0, 0))
+    f = workloads.rhs_uniform(n[::-1], seed)
+    t0 = time.perf_counter()
+    dec.tpt_solve(f, ops, LAM)
+    return time.perf_counter() - t0
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        if info:
+            return max(int(i.get("num_threads", 1)) for i in info)
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def algorithmic_units(name, n):
+    """(bound, algorithmic flops or bytes per launch, unit) of a kernel on an n^3 solve."""
+    P = n[0] * n[1] * n[2]
+    table = {
+        "transform_x_f64": ("alu", 2.0 * P * n[0], "flop"),
+        "transform_y_f64": ("alu", 2.0 * P * n[1], "flop"),
+        "transform_z_f64": ("alu", 2.0 * P * n[2], "flop"),
+        "thomas_z_f64": ("hbm", 16.0 * P, "byte"),
+        "residual_f64": ("hbm", 24.0 * P, "byte"),
+    }
+    return table.get(name)
+
+
+def run_arm(fdi, torch, prec, n, K, W, dev, rank, stream):
+    faces = workloads.box_faces(n, BETA)
+    plan = fdi.plan_create(faces, n, prec=prec)
+    f = workloads.rhs_uniform(n[::-1], rank)
+    rhs = torch.from_numpy(f).to(dev)
+    out = torch.empty_like(rhs)
+    with torch.cuda.stream(stream):
+        for _ in range(W):
+            fdi.helmholtz_solve(plan, LAM, rhs, out, stream)
+    torch.cuda.synchronize()
+    _, steps, rel, st = fdi.last_result(plan)
+    launches_per = fdi.last_launch_count(plan)
+    fdi.enable_timing(plan, True)
+    fdi.reset_kernel_times(plan)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record(stream)
+        for _ in range(K):
+            fdi.helmholtz_solve(plan, LAM, rhs, out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    ktimes = fdi.kernel_times(plan)
+    fdi.enable_timing(plan, False)
+    _, steps, rel, st = fdi.last_result(plan)
+    # end to end through the C ABI with host buffers: H2D of f, solve, D2H of u
+    h_in = torch.from_numpy(f).pin_memory()
+    h_out = torch.empty(h_in.shape, dtype=torch.float64).pin_memory()
+    d_in = torch.empty_like(rhs)
+    d_out = torch.empty_like(rhs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(K):
+            d_in.copy_(h_in, non_blocking=True)
+            fdi.helmholtz_solve(plan, LAM, d_in, d_out, stream)
+            h_out.copy_(d_out, non_blocking=True)
+    stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    plan.destroy()
+    return {"ms": ms, "steps": steps, "rel": rel, "status": st, "ktimes": ktimes, "launches_per": launches_per,
+            "e2e_s": e2e_s, "h2d": f.nbytes, "d2h": f.nbytes, "clocks": clk.summary()}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fdi", choices=["fdi", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--arms", default="fp64,mixed")
+    args = ap.parse_args()
+    n = (args.n, args.n, args.n)
+    P = n[0] * n[1] * n[2]
+    K, W = args.steps, max(args.warmup, 3)
+    rank, world, local = dist_env()
+    workload = {"workload": f"helmholtz_tpt_{args.n}^3_tanh{BETA}_dirichlet_lambda{LAM:g}", "n": list(n),
+                "beta": BETA, "lambda": LAM, "bc": "dirichlet", "method": "TPT (eigen x,y; Thomas z)",
+                "rhs": "uniform[-1,1] seed 0+rank", "l2": "inputs+workspace larger than L2 (134 MB field)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+        t = [oracle_tpt_time(n) for _ in range(W)] if W and args.n <= 128 else []
+        times = []
+        budget = 150.0
+        t_start = time.perf_counter()
+        for k in range(K):
+            times.append(oracle_tpt_time(n, seed=k))
+            if time.perf_counter() - t_start > budget:
+                break
+        v = P * len(times) / sum(times)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "grid-pts/s", "n_gpus": args.gpus,
+                "steps": len(times), "warmup": len(t), "ms_per_step": 1e3 * sum(times) / len(times),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": workload,
+                "cpu_baseline": {"value": v, "unit": "grid-pts/s", "cores": blas_threads(), "kind": "oracle",
+                                 "sample": f"{len(times)} full {args.n}^3 TPT solves by the NumPy FP64 oracle"},
+                "e2e": {"value": v, "unit": "grid-pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1107_2461_gb300 import build as _b
+    _b.build()
+    import paper_1107_2461_gb300 as fdi
+    stream = torch.cuda.Stream()
+
+    arms = {}
+    precs = {"fp64": (fdi.PREC_FP64, 1e-11), "mixed": (fdi.PREC_MIXED_F16, 1e-10)}
+    for name in args.arms.split(","):
+        prec, tol = precs[name]
+        try:
+            arms[name] = run_arm(fdi, torch, prec, n, K, W, dev, rank, stream)
+            arms[name]["tol"] = tol
+        except fdi.FdiError as e:
+            if e.status == fdi.fdi.ERR_UNSUPPORTED:
+                continue
+            raise
+    # slowest rank
+    for a in arms.values():
+        t = torch.tensor([a["ms"], a["e2e_s"]], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        a["ms_max"], a["e2e_max"] = float(t[0]), float(t[1])
+        a["value"] = world * P * K / (a["ms_max"] * 1e-3)
+        a["ok"] = a["status"] == 0 and a["rel"] <= a["tol"]
+    best_name = max((k for k in arms if arms[k]["ok"]), key=lambda k: arms[k]["value"], default=None)
+    if best_name is None:
+        best_name = next(iter(arms))
+    best = arms[best_name]
+
+    # roofline of the dominant kernel of the reported arm
+    peaks, peak_kind = load_peaks()
+    roof = None
+    if best["ktimes"]:
+        dom = max(best["ktimes"].items(), key=lambda kv: kv[1][0])
+        name, (tot_ms, cnt) = dom
+        au = algorithmic_units(name, n)
+        if au is not None:
+            bound, units, kind = au
+            avg_s = tot_ms * 1e-3 / cnt
+            if kind == "flop":
+                achieved = units / avg_s / 1e9
+                peak = FP64_PEAK_GFLOPS if bound == "alu" else peaks["bf16_tflops"] * 1e3
+                unit = "GFLOP/s"
+            else:
+                achieved = units / avg_s / 1e9
+                peak = peaks["hbm_gbs"]
+                unit = "GB/s"
+            roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                    "frac": achieved / peak, "traffic": None, "avg_launch_ms": tot_ms / cnt,
+                    "launches": cnt,
+                    "peak_source": ("FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz" if bound == "alu"
+                                    else f"MEASURED_PEAKS.json ({peak_kind})")}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t = oracle_tpt_time(n)
+        cpu = {"value": P / t, "unit": "grid-pts/s", "cores": blas_threads(), "kind": "oracle",
+               "sample": f"one full {args.n}^3 TPT solve by the NumPy FP64 oracle ({t:.2f} s)"}
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": best["value"], "unit": "grid-pts/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": best["ms_max"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if best_name == "fp64" else "f16-split/f32-acc + f64 refinement",
+        "data": "synthetic", "config": dict(workload, arm=best_name, parallelism=f"replicas x{world}"),
+        "e2e": {"value": world * P * K / best["e2e_max"], "unit": "grid-pts/s", "h2d_bytes_per_step": best["h2d"],
+                "d2h_bytes_per_step": best["d2h"]},
+        "gpu_launches": best["launches_per"] * K,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": best["clocks"],
+        "arms": {k: {"value": a["value"], "ms_per_solve": a["ms_max"] / K, "rel_residual": a["rel"],
+                     "refine_steps": a["steps"], "tol": a["tol"], "met_tol": a["ok"],
+                     "kernels": {kn: {"ms_total": v[0], "launches": v[1]} for kn, v in a["ktimes"].items()}}
+                 for k, a in arms.items()},
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,181 @@
+/*
+ * fdi.h -- fast direct inverses of Helmholtz, Laplace and Stokes operators on
+ * stretched finite-volume grids, for one NVIDIA GB300 (sm_103a).
+ *
+ * Method (Vitoshkin & Gelfgat, arXiv:1107.2461):
+ *   - Sec. 3, Eq. 23-29: the discrete Laplacian on an orthogonal grid is a
+ *     Kronecker sum of 1D operators D = E Lambda E^{-1} (Eq. 24); the Helmholtz
+ *     and Laplace inverses are (E_x(x)E_y(x)E_z) Lambda^{-1} (E_x^{-1}(x)...) f
+ *     (TPF, Eq. 29), or the same with the Thomas algorithm in one direction (TPT,
+ *     end of Sec. 3);
+ *   - Sec. 2, Eq. 8-9: the Stokes operator is inverted in three steps, only the
+ *     pressure matrix C = sum_c D_c H_c^{-1} G_c being inverted iteratively, by a
+ *     Krylov method preconditioned with the inverse pressure Laplacian.
+ *
+ * Conventions
+ *   - Grids: per direction d (0 = x, 1 = y, 2 = z) the caller gives n[d] cells
+ *     and n[d]+1 strictly ascending face coordinates.  Cell-centred unknowns
+ *     use the finite-volume second derivative with the wall value imposed at
+ *     half a cell (Dirichlet) or a zero wall flux (Neumann).
+ *   - Fields are FP64, contiguous, C order [n_z][n_y][n_x] (x fastest), in
+ *     device memory owned by the caller.
+ *   - Operator: A = sigma*I - lambda*Delta.  fdi_helmholtz_solve uses sigma = 1
+ *     (the paper's H = Delta - I/dt of Eq. 1 multiplied by -dt, with viscosity
+ *     1/Re so lambda = dt/Re); fdi_laplace_solve uses sigma = 0, lambda = 1
+ *     (-Delta u = f).  The pure zero-flux Laplacian is singular (Eq. 28): f is
+ *     projected to zero volume-weighted mean and the zero-mean u is returned.
+ *   - Staggered (MAC) grid, FDI_GRID_MAC: u on the interior x-faces
+ *     ((n_x-1)*n_y*n_z values), v on the interior y-faces (n_x*(n_y-1)*n_z),
+ *     w on the interior z-faces (n_x*n_y*(n_z-1)), p at the cells; no-slip
+ *     walls.  fdi_stokes_solve solves
+ *         (I - lambda*Delta_c) u_c + dt*(G p)_c = f_c,  D u = 0,  lambda = dt/Re
+ *     (Eq. 8 scaled by -dt) and returns p with zero volume-weighted mean.
+ *
+ * Asynchrony: every solve is enqueued on `stream`.  Numerical results
+ * (iterations, refinement steps, relative residual) are read with
+ * fdi_last_result after the caller synchronises the stream.
+ * fdi_stokes_solve reads one convergence flag back per Krylov iteration and so
+ * synchronises `stream` internally.
+ *
+ * Threading: a plan owns one workspace.  Using one plan from two host threads,
+ * or on two streams at once, is a data race.
+ *
+ * Errors: argument errors are returned synchronously and leave the outputs
+ * untouched.  A CUDA error is returned as FDI_ERR_CUDA.  No C++ exception
+ * crosses this interface.
+ */
+#ifndef FDI_H
+#define FDI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* fdi_stream_t; /* the same handle as cudaStream_t; NULL = legacy default stream */
+typedef struct fdi_plan fdi_plan;         /* opaque; owns every device buffer it allocates */
+
+typedef enum {
+  FDI_OK = 0,
+  FDI_ERR_INVALID_ARG = 1,
+  FDI_ERR_OUT_OF_MEMORY = 2,
+  FDI_ERR_CUDA = 3,
+  FDI_ERR_NOT_CONVERGED = 4,
+  FDI_ERR_TIMEOUT = 5,
+  FDI_ERR_SINGULAR = 6,
+  FDI_ERR_UNSUPPORTED = 7
+} fdi_status;
+
+typedef enum { FDI_BC_DIRICHLET = 0, FDI_BC_NEUMANN = 1 } fdi_bc;
+typedef enum { FDI_GRID_CELL = 0, FDI_GRID_MAC = 1 } fdi_grid;
+
+/* Arithmetic of the x/y eigenvector transforms (the dense contractions of
+ * Eq. 25/29).  FDI_PREC_FP64: every step in FP64.  The mixed modes split each
+ * operand into a high and a low part in a 16-bit (or TF32) tensor-core type,
+ * form hi*hi + hi*lo + lo*hi with FP32 accumulation, keep the intermediate
+ * fields in FP32, run the Thomas sweep in FP32, and recover FP64 accuracy by
+ * iterative refinement against a residual evaluated in double-float (about 48
+ * significant bits) arithmetic. */
+typedef enum {
+  FDI_PREC_FP64 = 0,
+  FDI_PREC_MIXED_TF32 = 1,
+  FDI_PREC_MIXED_BF16 = 2,
+  FDI_PREC_MIXED_F16 = 3
+} fdi_precision;
+
+/* Fields of a plan.  FDI_FIELD_CELL is the cell-centred grid (for a MAC plan:
+ * the pressure grid, zero-flux walls). */
+typedef enum { FDI_FIELD_CELL = 0, FDI_FIELD_U = 1, FDI_FIELD_V = 2, FDI_FIELD_W = 3 } fdi_field;
+
+/* Create a plan: builds the 1D operators from the face coordinates (Sec. 3,
+ * Eq. 23) and computes their eigen decompositions D = E Lambda E^{-1} (Eq. 24)
+ * in FP64 on the current CUDA device -- O(n^3) once per grid, Sec. 3 -- and
+ * keeps E, E^{-1}, Lambda and the workspace resident.
+ *   faces[d]   host pointer to n[d]+1 ascending doubles (copied; not retained)
+ *   n[d]       cells per direction, 2 <= n[d] <= 256
+ *   bc_lo/hi   wall type of each side of each direction (FDI_GRID_CELL only;
+ *              ignored for FDI_GRID_MAC, whose walls are no-slip)
+ *   thomas_axis 2: Thomas along z (TPT); -1: eigen decomposition in all three
+ *              directions (TPF).  Other values: FDI_ERR_UNSUPPORTED.
+ * Synchronous.  On error *out is set to NULL. */
+fdi_status fdi_plan_create(const double* const faces[3], const int n[3], const fdi_bc bc_lo[3],
+                           const fdi_bc bc_hi[3], fdi_grid grid, fdi_precision prec, int thomas_axis,
+                           fdi_plan** out);
+
+/* Release every device buffer of the plan (synchronises the device first). */
+fdi_status fdi_plan_destroy(fdi_plan* plan);
+
+/* Convergence controls.  tol: target relative residual ||f - A u||/||f|| of the
+ * Helmholtz/Laplace solves (default 1e-11 for FP64, 1e-10 mixed); max_refine:
+ * refinement steps after the first solve (default 2 FP64, 3 mixed);
+ * krylov_tol / max_iters: relative residual and iteration cap of the
+ * pressure-matrix Krylov solve (defaults 1e-11 / 200). */
+fdi_status fdi_plan_set_tolerances(fdi_plan* plan, double tol, int max_refine, double krylov_tol,
+                                   int max_iters);
+
+/* (I - lambda*Delta) out = rhs on the plan's cell grid (Eq. 27 scaled), lambda >= 0.
+ * rhs, out: device, n_x*n_y*n_z doubles; out may alias rhs. */
+fdi_status fdi_helmholtz_solve(fdi_plan* plan, double lambda, const double* rhs, double* out,
+                               fdi_stream_t stream);
+
+/* -Delta out = rhs on the plan's cell grid (Eq. 23; Eq. 28 for zero-flux walls). */
+fdi_status fdi_laplace_solve(fdi_plan* plan, const double* rhs, double* out, fdi_stream_t stream);
+
+/* (sigma*I - lambda*Delta_field) out = rhs on any field of the plan (sigma in
+ * {0, 1}, lambda > 0; sigma = 0 only on the cell field).  Sizes as listed above. */
+fdi_status fdi_field_solve(fdi_plan* plan, fdi_field field, double sigma, double lambda,
+                           const double* rhs, double* out, fdi_stream_t stream);
+
+/* Semi-direct Stokes inverse on a FDI_GRID_MAC plan (Sec. 2, three steps after
+ * Eq. 9).  f[c], u[c]: device velocity fields (sizes above); p: device pressure.
+ * Outputs must not alias inputs. */
+fdi_status fdi_stokes_solve(fdi_plan* plan, double dt, double Re, const double* const f[3],
+                            double* const u[3], double* p, fdi_stream_t stream);
+
+/* count independent Helmholtz solves (plans[i] may repeat only if the solves
+ * are meant to run one after another on that plan's workspace). */
+fdi_status fdi_helmholtz_solve_batched(fdi_plan* const* plans, const double* lambdas,
+                                       const double* const* rhs, double* const* out, int count,
+                                       fdi_stream_t stream);
+
+/* Results of the last solve on this plan; call after synchronising its stream.
+ * iters: Krylov iterations (Stokes) or 0; refine_steps: solves after the first;
+ * rel_residual: final relative residual (Helmholtz/Laplace: of A u = f;
+ * Stokes: of the pressure-matrix system).  Any pointer may be NULL. */
+fdi_status fdi_last_result(const fdi_plan* plan, int* iters, int* refine_steps,
+                           double* rel_residual);
+
+/* Copy the plan's 1D eigen data for direction d of a field to host buffers:
+ * lam (m doubles), E and Einv (m*m doubles, row-major), m = unknowns along d.
+ * Any pointer may be NULL.  Synchronous. */
+fdi_status fdi_plan_eigen(const fdi_plan* plan, fdi_field field, int d, double* lam, double* E,
+                          double* Einv, int* m);
+
+/* Per-kernel device timing: with timing on, every kernel launch of this plan is
+ * bracketed by a CUDA event pair on the launching stream. */
+fdi_status fdi_plan_enable_timing(fdi_plan* plan, int on);
+
+/* Harvest the recorded event pairs (synchronises on them) and report, per
+ * kernel name, the accumulated device time in ms and the launch count since the
+ * last reset.  names[i] stay valid until the plan is destroyed.  Up to `max`
+ * entries are written; *count receives the number written. */
+fdi_status fdi_plan_kernel_times(fdi_plan* plan, int max, const char** names, double* total_ms,
+                                 long long* launches, int* count);
+
+/* Harvest pending events and clear the accumulated kernel times. */
+fdi_status fdi_plan_reset_kernel_times(fdi_plan* plan);
+
+/* Number of kernels the last solve on this plan enqueued (host-side count). */
+fdi_status fdi_last_launch_count(const fdi_plan* plan, long long* launches);
+
+/* Human-readable text of the last error recorded on the calling host thread. */
+const char* fdi_last_error_message(void);
+
+const char* fdi_status_string(fdi_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDI_H */

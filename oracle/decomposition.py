@@ -20,7 +20,9 @@ E = M^{-1/2} Q, E^{-1} = Q^T M^{1/2}.
 
 Reading of Eq. 28 used here: for the zero-flux operator the null eigenpair is
 known exactly (Lambda = 0, constant eigenvector), so it is set exactly instead
-of trusting a computed eigenvalue of size 1e-13; the right-hand side of the
+of trusting a computed eigenvalue of size 1e-13, and the other eigenvectors are
+projected onto its M-orthogonal complement (eigenvectors of the symmetric
+pencil (K, M) are M-orthogonal to it); the right-hand side of the
 singular problem is projected to zero volume-weighted mean first, after which
 Eq. 28's "divide by 1" leaves the null-mode coefficient at (rounding-level)
 zero.  In TPT the singular Thomas line (null mode in both transformed
@@ -49,6 +51,11 @@ def generalized_eig(m, K):
         if np.dot(q0, Q[:, i0]) < 0:
             q0 = -q0
         Q[:, i0] = q0
+        # the other eigenvectors are orthogonal to the exact null vector: remove
+        # the component rounding left along it
+        others = [k for k in range(Q.shape[1]) if k != i0]
+        Q[:, others] -= np.outer(q0, q0 @ Q[:, others])
+        Q[:, others] /= np.linalg.norm(Q[:, others], axis=0)[None, :]
     E = Q / s[:, None]
     Einv = Q.T * s[None, :]
     return lam, E, Einv

@@ -1,0 +1,13 @@
+"""GB300-native fast direct inverses of Helmholtz, Laplace and Stokes operators on
+stretched finite-volume grids (Vitoshkin & Gelfgat, arXiv:1107.2461).
+
+The compute path is libfdi.so (hand-written CUDA for sm_103a behind the C ABI
+of include/fdi.h); `fdi` is its thin ctypes binding.
+"""
+from . import fdi  # noqa: F401
+from .fdi import (  # noqa: F401
+    BC_DIRICHLET, BC_NEUMANN, FIELD_CELL, FIELD_U, FIELD_V, FIELD_W, GRID_CELL, GRID_MAC, PREC_FP64,
+    PREC_MIXED_BF16, PREC_MIXED_F16, PREC_MIXED_TF32, FdiError, Plan, field_solve, helmholtz_solve,
+    helmholtz_solve_batched, laplace_solve, last_launch_count, last_result, plan_create, plan_destroy,
+    status_string, stokes_solve,
+)

@@ -1,0 +1,173 @@
+// Internal declarations of libfdi: plan layout, device status, kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fdi.h"
+
+namespace fdi {
+
+constexpr int kMaxN = 256;       // cells per direction supported by the plan
+constexpr int kMaxRefineCap = 8;
+
+// Device-side status of the last solve on a plan (written by kernels).
+struct DevStatus {
+  int done;          // refinement / Krylov converged: later rounds early-exit
+  int refine_steps;  // solves after the first
+  int iters;         // Krylov iterations
+  int error;         // nonzero: numerical failure (non-finite residual ...)
+  double rel_res;    // relative residual of the last check
+  double bnorm2;     // ||b||^2 of the current solve
+  double mean_b;     // volume-weighted mean of b (singular problems)
+  double scal[16];   // Krylov scalars (rho, alpha, omega, ...)
+};
+
+// One 1D operator D = M^{-1} K along a direction (Eq. 23-24), resident on device.
+struct Axis {
+  int n = 0;
+  bool zero_flux = false;           // both walls zero-flux: Lambda_0 = 0 exactly
+  // device arrays
+  double* m = nullptr;              // M diagonal (control-volume widths), n
+  double* kd = nullptr;             // K diagonal, n
+  double* ko = nullptr;             // K off-diagonal K[i][i+1], n-1 (padded to n)
+  double* wp = nullptr;             // flux weights K[i][i+1]/m_i, n (0 at the last index)
+  double* wm = nullptr;             // K[i][i-1]/m_i, n (0 at index 0)
+  double* w0 = nullptr;             // (K_ii + K_i,i+1 + K_i,i-1)/m_i: wall term, n
+  double* lam = nullptr;            // eigenvalues, n, descending (closest to 0 first)
+  double* E = nullptr;              // n*n row-major E[r][k]   (column k = eigenvector k)
+  double* Einv = nullptr;           // n*n row-major Einv[k][r]
+  // mixed-precision copies (filled by the mixed-path setup)
+  void* tc_fwd = nullptr;           // split operand images of E^{-1} (tensor-core layout)
+  void* tc_bwd = nullptr;           // split operand images of E
+  float* tc_fwd_scale = nullptr;    // per-row power-of-two unscale factors
+  float* tc_bwd_scale = nullptr;
+  float* lam_f = nullptr;           // eigenvalues as float (mixed Thomas / divide)
+  float* m_f = nullptr;             // M, K as float for the FP32 Thomas sweep
+  float* kd_f = nullptr;
+  float* ko_f = nullptr;
+  // double-float (hi, lo) residual weights
+  float2* wp_df = nullptr;
+  float2* wm_df = nullptr;
+  float2* w0_df = nullptr;
+  // host copies
+  std::vector<double> h_m, h_kd, h_ko;
+};
+
+struct Field {
+  Axis* ax[3] = {nullptr, nullptr, nullptr};
+  int n[3] = {0, 0, 0};             // unknowns per direction
+  long long P = 0;
+  double vol_sum = 0.0;             // sum of control volumes
+  bool zero_flux_all = false;       // singular when sigma = 0
+};
+
+}  // namespace fdi
+
+struct fdi_plan {
+  fdi_grid grid;
+  fdi_precision prec;
+  int thomas_axis;
+  int n[3];
+  int device;
+  std::vector<fdi::Axis*> axes;
+  fdi::Field fields[4];
+  int nfields = 1;
+  long long Pmax = 0;
+  // workspace (FP64 path): 5 buffers of Pmax doubles
+  double* ws[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  // mixed-path workspace: FP32 buffers + double-float pairs
+  float* wf[4] = {nullptr, nullptr, nullptr, nullptr};
+  float2* xdf = nullptr;            // solution accumulator (hi, lo)
+  float2* rdf = nullptr;            // residual (hi, lo)
+  double* partials = nullptr;       // reduction partials
+  int npartials = 0;
+  fdi::DevStatus* d_status = nullptr;
+  int* h_flag = nullptr;            // pinned host flag for Krylov convergence
+  // Stokes workspace (MAC plans)
+  double* sk[12] = {nullptr};
+  // controls
+  double tol = 1e-11;
+  int max_refine = 2;
+  double ktol = 1e-11;
+  int kmaxit = 200;
+  // last results (host)
+  int last_iters = 0, last_refine = 0;
+  double last_res = 0.0;
+  long long launches = 0;
+  bool status_valid = false;
+  // optional per-kernel device timing (CUDA events around each launch)
+  bool timing = false;
+  struct TimedLaunch { const char* name; cudaEvent_t e0, e1; };
+  std::vector<TimedLaunch> pending;
+  std::vector<cudaEvent_t> event_pool;
+  struct KernelTime { std::string name; double ms; long long n; };
+  std::vector<KernelTime> ktimes;
+};
+
+namespace fdi {
+
+// error helpers
+void set_error(const std::string& msg);
+#define FDI_CUDA_TRY(expr)                                                      \
+  do {                                                                          \
+    cudaError_t _e = (expr);                                                    \
+    if (_e != cudaSuccess) {                                                    \
+      ::fdi::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));     \
+      return FDI_ERR_CUDA;                                                      \
+    }                                                                           \
+  } while (0)
+#define FDI_LAUNCH_CHECK(plan)                                                  \
+  do {                                                                          \
+    (plan)->launches++;                                                         \
+    cudaError_t _e = cudaGetLastError();                                        \
+    if (_e != cudaSuccess) {                                                    \
+      ::fdi::set_error(std::string("kernel launch: ") + cudaGetErrorString(_e)); \
+      return FDI_ERR_CUDA;                                                      \
+    }                                                                           \
+  } while (0)
+
+// Scoped per-kernel timer: records an event pair around the launches in its
+// scope when timing is enabled on the plan.
+struct KTimer {
+  fdi_plan* p;
+  const char* name;
+  cudaStream_t s;
+  cudaEvent_t e0 = nullptr;
+  KTimer(fdi_plan* p_, const char* name_, cudaStream_t s_);
+  ~KTimer();
+};
+#define FDI_KTIMER(plan, name, stream) ::fdi::KTimer _kt_##__LINE__((plan), (name), (stream))
+
+// plan-time eigen decomposition of the symmetric tridiagonal M^{-1/2} K M^{-1/2}
+fdi_status eigen_decompose_all(const std::vector<Axis*>& axes, cudaStream_t s, int* d_err);
+
+// FP64 path launchers (kernels_f64.cu)
+fdi_status launch_lines_f64(fdi_plan* p, const double* in, double* out, const double* T, int nin,
+                            int nout, long long lines, bool accumulate, const int* skip, cudaStream_t s);
+fdi_status launch_slab_f64(fdi_plan* p, const double* in, double* out, const double* T, int nin,
+                           int nout, long long ncols, int batch, const int* skip, cudaStream_t s);
+fdi_status launch_thomas_f64(fdi_plan* p, const Field& f, double sigma, double lambda, const double* in,
+                             double* out, double* scratch, const int* skip, cudaStream_t s);
+fdi_status launch_divide_f64(fdi_plan* p, const Field& f, double sigma, double lambda, double* data,
+                             const int* skip, cudaStream_t s);
+fdi_status launch_residual_f64(fdi_plan* p, const Field& f, double sigma, double lambda, const double* b,
+                               const double* u, double* r, bool subtract_mean, const int* skip,
+                               cudaStream_t s);
+fdi_status launch_finish_residual(fdi_plan* p, int nblocks, bool first, int count_step, const int* skip,
+                                  cudaStream_t s);
+fdi_status launch_mean_f64(fdi_plan* p, const Field& f, const double* b, cudaStream_t s);
+fdi_status launch_reset_status(fdi_plan* p, cudaStream_t s);
+
+// solve orchestration (solve.cu)
+fdi_status field_solve(fdi_plan* p, int field, double sigma, double lambda, const double* rhs, double* out,
+                       cudaStream_t s);
+fdi_status validate_field_args(const fdi_plan* p, int field, double sigma, double lambda);
+
+// mixed path (mixed.cu)
+fdi_status mixed_setup(fdi_plan* p);
+fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda, const double* rhs,
+                             double* out, cudaStream_t s);
+
+}  // namespace fdi

@@ -1,0 +1,477 @@
+// FP64 kernels of the direct Helmholtz / Laplace inverse (the plain FP64 path).
+//
+//   k_lines_f64   out[l][k] = sum_j T[k][j] in[l][j]     transform along x (Eq. 25/29,
+//                 the factor E_x^{-1} or E_x applied to every x-line)
+//   k_slab_f64    out[b][k][c] = sum_j T[k][j] in[b][j][c]  transform along y per
+//                 z-slab, or along z over all columns (TPF)
+//   k_thomas_f64  per (x-mode, y-mode) line the tridiagonal z-system
+//                 [(sigma - lam (Lx_i + Ly_j)) M_z - lam K_z] u = M_z f   (TPT,
+//                 end of Sec. 3: Thomas algorithm in one direction)
+//   k_divide_f64  u_ijk = f_ijk / (sigma - lam (Lx_i + Ly_j + Lz_k))  (Eq. 26-28)
+//   k_residual_f64 r = b - A u with the 7-point finite-volume stencil in flux form,
+//                 and per-block partial sums of r^2 and b^2 (fixed grid, so the
+//                 reduction order is deterministic)
+//
+// GB300 runs FP64 at about 2 FMA/clk/SM, so the transforms are FP64-pipe bound;
+// they are register-tiled (4x4 outputs per thread, 64x64 tiles staged in shared
+// memory) so that every shared-memory load feeds two FMAs.
+#include <cmath>
+
+#include "fdi_internal.h"
+
+namespace fdi {
+namespace {
+
+constexpr int TB = 64;   // tile edge
+constexpr int TK = 16;   // k-chunk
+constexpr int kResBlocks = 152 * 8;
+constexpr int kResThreads = 256;
+
+template <bool ACC>
+__global__ void __launch_bounds__(256) k_lines_f64(const double* __restrict__ A, double* __restrict__ C,
+                                                   const double* __restrict__ T, int nin, int nout,
+                                                   long long L, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ double As[TK][TB + 1];  // [j][line]
+  __shared__ double Bs[TK][TB + 1];  // [j][k]
+  const long long l0 = (long long)blockIdx.x * TB;
+  const int k0 = blockIdx.y * TB;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  for (int j0 = 0; j0 < nin; j0 += TK) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int jj = threadIdx.x % TK, ll = threadIdx.x / TK + 16 * r;
+      long long line = l0 + ll;
+      int j = j0 + jj, k = k0 + ll;
+      As[jj][ll] = (line < L && j < nin) ? A[line * nin + j] : 0.0;
+      Bs[jj][ll] = (k < nout && j < nin) ? T[(long long)k * nin + j] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int jj = 0; jj < TK; ++jj) {
+      double a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = As[jj][ty + 16 * q];
+        b[q] = Bs[jj][tx + 16 * q];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[q][c] = fma(a[q], b[c], acc[q][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    long long line = l0 + ty + 16 * q;
+    if (line >= L) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      int k = k0 + tx + 16 * c;
+      if (k < nout) {
+        long long idx = line * nout + k;
+        C[idx] = ACC ? C[idx] + acc[q][c] : acc[q][c];
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_slab_f64(const double* __restrict__ A, double* __restrict__ C,
+                                                  const double* __restrict__ T, int nin, int nout,
+                                                  long long ncols, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ double As[TK][TB + 1];  // T tile [j][k]
+  __shared__ double Bs[TK][TB + 1];  // data tile [j][c]
+  const long long b = blockIdx.z;
+  A += b * (long long)nin * ncols;
+  C += b * (long long)nout * ncols;
+  const long long c0 = (long long)blockIdx.x * TB;
+  const int k0 = blockIdx.y * TB;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[a][q] = 0.0;
+  for (int j0 = 0; j0 < nin; j0 += TK) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int jj = threadIdx.x % TK, kk = threadIdx.x / TK + 16 * r;
+      int j = j0 + jj, k = k0 + kk;
+      As[jj][kk] = (k < nout && j < nin) ? T[(long long)k * nin + j] : 0.0;
+      int cc = threadIdx.x % TB, jr = threadIdx.x / TB + 4 * r;
+      long long col = c0 + cc;
+      int j2 = j0 + jr;
+      Bs[jr][cc] = (col < ncols && j2 < nin) ? A[(long long)j2 * ncols + col] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int jj = 0; jj < TK; ++jj) {
+      double a[4], bb[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = As[jj][ty + 16 * q];
+        bb[q] = Bs[jj][tx + 16 * q];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[q][c] = fma(a[q], bb[c], acc[q][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int k = k0 + ty + 16 * q;
+    if (k >= nout) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      long long col = c0 + tx + 16 * c;
+      if (col < ncols) C[(long long)k * ncols + col] = acc[q][c];
+    }
+  }
+}
+
+struct ThomasArgs {
+  const double* in;
+  double* out;
+  double* cs;        // scratch c'_k
+  int nx, ny, nz;
+  const double* lamx;
+  const double* lamy;
+  const double* mz;
+  const double* kdz;
+  const double* koz;
+  double sigma, lambda;
+  int singular_possible;  // sigma == 0 and zero-flux walls everywhere
+};
+
+__global__ void __launch_bounds__(128) k_thomas_f64(ThomasArgs a, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const long long NL = (long long)a.nx * a.ny;
+  const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= NL) return;
+  const int i = (int)(l % a.nx), j = (int)(l / a.nx);
+  const double lab = a.lamx[i] + a.lamy[j];
+  const double s = a.sigma - a.lambda * lab;
+  const int nz = a.nz;
+  const double lam = a.lambda;
+  if (!(a.singular_possible && lab == 0.0)) {
+    double cprev = 0.0, dprev = 0.0;
+    for (int k = 0; k < nz; ++k) {
+      double lo = (k > 0) ? -lam * a.koz[k - 1] : 0.0;
+      double up = (k + 1 < nz) ? -lam * a.koz[k] : 0.0;
+      double di = s * a.mz[k] - lam * a.kdz[k];
+      double inv = 1.0 / (di - lo * cprev);
+      cprev = up * inv;
+      dprev = (a.mz[k] * a.in[k * NL + l] - lo * dprev) * inv;
+      a.cs[k * NL + l] = cprev;
+      a.out[k * NL + l] = dprev;
+    }
+    double u = dprev;
+    for (int k = nz - 2; k >= 0; --k) {
+      u = a.out[k * NL + l] - a.cs[k * NL + l] * u;
+      a.out[k * NL + l] = u;
+    }
+  } else {
+    // singular line of the zero-flux Laplacian (Eq. 28 reading): project the
+    // right-hand side to zero M_z-weighted mean, pin u_0 = 0, solve rows 1..nz-1,
+    // then remove the weighted mean of the solution.
+    double sm = 0.0, sf = 0.0;
+    for (int k = 0; k < nz; ++k) {
+      sm += a.mz[k];
+      sf += a.mz[k] * a.in[k * NL + l];
+    }
+    const double mu = sf / sm;
+    double cprev = 0.0, dprev = 0.0;
+    for (int k = 1; k < nz; ++k) {
+      double lo = (k > 1) ? -lam * a.koz[k - 1] : 0.0;
+      double up = (k + 1 < nz) ? -lam * a.koz[k] : 0.0;
+      double di = s * a.mz[k] - lam * a.kdz[k];
+      double inv = 1.0 / (di - lo * cprev);
+      cprev = up * inv;
+      dprev = (a.mz[k] * (a.in[k * NL + l] - mu) - lo * dprev) * inv;
+      a.cs[k * NL + l] = cprev;
+      a.out[k * NL + l] = dprev;
+    }
+    double u = dprev, su = a.mz[nz - 1] * dprev;
+    for (int k = nz - 2; k >= 1; --k) {
+      u = a.out[k * NL + l] - a.cs[k * NL + l] * u;
+      a.out[k * NL + l] = u;
+      su += a.mz[k] * u;
+    }
+    a.out[l] = 0.0;
+    const double mean = su / sm;
+    for (int k = 0; k < nz; ++k) a.out[k * NL + l] -= mean;
+  }
+}
+
+__global__ void k_divide_f64(double* __restrict__ data, int nx, int ny, int nz, const double* __restrict__ lx,
+                             const double* __restrict__ ly, const double* __restrict__ lz, double sigma,
+                             double lambda, int singular_possible, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const long long P = (long long)nx * ny * nz;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P;
+       p += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(p % nx);
+    long long t = p / nx;
+    int j = (int)(t % ny), k = (int)(t / ny);
+    double ls = lx[i] + ly[j] + lz[k];
+    double dv = sigma - lambda * ls;
+    data[p] = (singular_possible && ls == 0.0) ? 0.0 : data[p] / dv;
+  }
+}
+
+struct StencilArgs {
+  int nx, ny, nz;
+  const double* wp[3];
+  const double* wm[3];
+  const double* w0[3];
+  const double* m[3];
+};
+
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x / 32, ln = threadIdx.x % 32;
+  if (ln == 0) {
+    sh[2 * w] = a;
+    sh[2 * w + 1] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0, sb = 0;
+    for (int q = 0; q < (int)(blockDim.x / 32); ++q) {
+      sa += sh[2 * q];
+      sb += sh[2 * q + 1];
+    }
+    a = sa;
+    b = sb;
+  }
+}
+
+__global__ void __launch_bounds__(kResThreads) k_residual_f64(StencilArgs g, const double* __restrict__ b,
+                                                              const double* __restrict__ u, double* __restrict__ r,
+                                                              double sigma, double lambda,
+                                                              const DevStatus* __restrict__ st, int sub_mean,
+                                                              double* __restrict__ partials,
+                                                              const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ double sh[2 * (kResThreads / 32)];
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const long long sx = 1, sy = nx, sz = (long long)nx * ny;
+  const long long P = sz * nz;
+  const double mb = sub_mean ? st->mean_b : 0.0;
+  double srr = 0.0, sbb = 0.0;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P;
+       p += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(p % nx);
+    long long t = p / nx;
+    int j = (int)(t % ny), k = (int)(t / ny);
+    double uc = u[p];
+    double lx = g.w0[0][i] * uc, ly = g.w0[1][j] * uc, lz = g.w0[2][k] * uc;
+    if (i + 1 < nx) lx += g.wp[0][i] * (u[p + sx] - uc);
+    if (i > 0) lx += g.wm[0][i] * (u[p - sx] - uc);
+    if (j + 1 < ny) ly += g.wp[1][j] * (u[p + sy] - uc);
+    if (j > 0) ly += g.wm[1][j] * (u[p - sy] - uc);
+    if (k + 1 < nz) lz += g.wp[2][k] * (u[p + sz] - uc);
+    if (k > 0) lz += g.wm[2][k] * (u[p - sz] - uc);
+    double bb = b[p] - mb;
+    double rr = bb - (sigma * uc - lambda * ((lx + ly) + lz));
+    if (r) r[p] = rr;
+    srr += rr * rr;
+    sbb += bb * bb;
+  }
+  block_sum2(srr, sbb, sh);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = srr;
+    partials[2 * blockIdx.x + 1] = sbb;
+  }
+}
+
+__global__ void k_finish_residual(const double* __restrict__ partials, int nblocks, DevStatus* st, double tol,
+                                  int first, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ double sh[2 * 8];
+  double a = 0.0, b = 0.0;
+  for (int q = threadIdx.x; q < nblocks; q += blockDim.x) {
+    a += partials[2 * q];
+    b += partials[2 * q + 1];
+  }
+  block_sum2(a, b, sh);
+  if (threadIdx.x == 0) {
+    double rel = (b > 0.0) ? sqrt(a / b) : sqrt(a);
+    if (first) {
+      st->refine_steps = 0;
+      st->bnorm2 = b;
+    } else {
+      st->refine_steps += 1;
+    }
+    st->rel_res = rel;
+    if (!isfinite(rel)) {
+      st->error = 1;
+      st->done = 1;
+    } else {
+      st->done = rel <= tol ? 1 : 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kResThreads) k_vmean_partial(StencilArgs g, const double* __restrict__ b,
+                                                               double* __restrict__ partials) {
+  __shared__ double sh[2 * (kResThreads / 32)];
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const long long P = (long long)nx * ny * nz;
+  double sv = 0.0, sd = 0.0;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P;
+       p += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(p % nx);
+    long long t = p / nx;
+    int j = (int)(t % ny), k = (int)(t / ny);
+    double v = g.m[0][i] * g.m[1][j] * g.m[2][k];
+    sv += v * b[p];
+    sd += v;
+  }
+  block_sum2(sv, sd, sh);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = sv;
+    partials[2 * blockIdx.x + 1] = sd;
+  }
+}
+
+__global__ void k_vmean_finish(const double* __restrict__ partials, int nblocks, DevStatus* st) {
+  __shared__ double sh[2 * 8];
+  double a = 0.0, b = 0.0;
+  for (int q = threadIdx.x; q < nblocks; q += blockDim.x) {
+    a += partials[2 * q];
+    b += partials[2 * q + 1];
+  }
+  block_sum2(a, b, sh);
+  if (threadIdx.x == 0) st->mean_b = a / b;
+}
+
+__global__ void k_reset_status(DevStatus* st) {
+  st->done = 0;
+  st->refine_steps = 0;
+  st->iters = 0;
+  st->error = 0;
+  st->rel_res = 0.0;
+  st->bnorm2 = 0.0;
+  st->mean_b = 0.0;
+}
+
+StencilArgs stencil_args(const Field& f) {
+  StencilArgs g;
+  g.nx = f.n[0];
+  g.ny = f.n[1];
+  g.nz = f.n[2];
+  for (int d = 0; d < 3; ++d) {
+    g.wp[d] = f.ax[d]->wp;
+    g.wm[d] = f.ax[d]->wm;
+    g.w0[d] = f.ax[d]->w0;
+    g.m[d] = f.ax[d]->m;
+  }
+  return g;
+}
+
+}  // namespace
+
+fdi_status launch_lines_f64(fdi_plan* p, const double* in, double* out, const double* T, int nin, int nout,
+                            long long lines, bool accumulate, const int* skip, cudaStream_t s) {
+  FDI_KTIMER(p, "transform_x_f64", s);
+  dim3 grid((unsigned)((lines + TB - 1) / TB), (unsigned)((nout + TB - 1) / TB));
+  if (accumulate)
+    k_lines_f64<true><<<grid, 256, 0, s>>>(in, out, T, nin, nout, lines, skip);
+  else
+    k_lines_f64<false><<<grid, 256, 0, s>>>(in, out, T, nin, nout, lines, skip);
+  FDI_LAUNCH_CHECK(p);
+  return FDI_OK;
+}
+
+fdi_status launch_slab_f64(fdi_plan* p, const double* in, double* out, const double* T, int nin, int nout,
+                           long long ncols, int batch, const int* skip, cudaStream_t s) {
+  FDI_KTIMER(p, batch > 1 ? "transform_y_f64" : "transform_z_f64", s);
+  dim3 grid((unsigned)((ncols + TB - 1) / TB), (unsigned)((nout + TB - 1) / TB), (unsigned)batch);
+  k_slab_f64<<<grid, 256, 0, s>>>(in, out, T, nin, nout, ncols, skip);
+  FDI_LAUNCH_CHECK(p);
+  return FDI_OK;
+}
+
+fdi_status launch_thomas_f64(fdi_plan* p, const Field& f, double sigma, double lambda, const double* in,
+                             double* out, double* scratch, const int* skip, cudaStream_t s) {
+  FDI_KTIMER(p, "thomas_z_f64", s);
+  ThomasArgs a;
+  a.in = in;
+  a.out = out;
+  a.cs = scratch;
+  a.nx = f.n[0];
+  a.ny = f.n[1];
+  a.nz = f.n[2];
+  a.lamx = f.ax[0]->lam;
+  a.lamy = f.ax[1]->lam;
+  a.mz = f.ax[2]->m;
+  a.kdz = f.ax[2]->kd;
+  a.koz = f.ax[2]->ko;
+  a.sigma = sigma;
+  a.lambda = lambda;
+  a.singular_possible = (sigma == 0.0 && f.zero_flux_all) ? 1 : 0;
+  long long NL = (long long)a.nx * a.ny;
+  k_thomas_f64<<<(unsigned)((NL + 127) / 128), 128, 0, s>>>(a, skip);
+  FDI_LAUNCH_CHECK(p);
+  return FDI_OK;
+}
+
+fdi_status launch_divide_f64(fdi_plan* p, const Field& f, double sigma, double lambda, double* data,
+                             const int* skip, cudaStream_t s) {
+  FDI_KTIMER(p, "divide_f64", s);
+  int sp = (sigma == 0.0 && f.zero_flux_all) ? 1 : 0;
+  k_divide_f64<<<152 * 8, 256, 0, s>>>(data, f.n[0], f.n[1], f.n[2], f.ax[0]->lam, f.ax[1]->lam, f.ax[2]->lam,
+                                      sigma, lambda, sp, skip);
+  FDI_LAUNCH_CHECK(p);
+  return FDI_OK;
+}
+
+fdi_status launch_residual_f64(fdi_plan* p, const Field& f, double sigma, double lambda, const double* b,
+                               const double* u, double* r, bool subtract_mean, const int* skip,
+                               cudaStream_t s) {
+  FDI_KTIMER(p, "residual_f64", s);
+  k_residual_f64<<<kResBlocks, kResThreads, 0, s>>>(stencil_args(f), b, u, r, sigma, lambda, p->d_status,
+                                                    subtract_mean ? 1 : 0, p->partials, skip);
+  FDI_LAUNCH_CHECK(p);
+  return FDI_OK;
+}
+
+fdi_status launch_finish_residual(fdi_plan* p, int nblocks, bool first, int /*count_step*/, const int* skip,
+                                  cudaStream_t s) {
+  FDI_KTIMER(p, "reduce", s);
+  if (nblocks <= 0) nblocks = kResBlocks;
+  k_finish_residual<<<1, 256, 0, s>>>(p->partials, nblocks, p->d_status, p->tol, first ? 1 : 0, skip);
+  FDI_LAUNCH_CHECK(p);
+  return FDI_OK;
+}
+
+fdi_status launch_mean_f64(fdi_plan* p, const Field& f, const double* b, cudaStream_t s) {
+  FDI_KTIMER(p, "mean_f64", s);
+  k_vmean_partial<<<kResBlocks, kResThreads, 0, s>>>(stencil_args(f), b, p->partials);
+  FDI_LAUNCH_CHECK(p);
+  k_vmean_finish<<<1, 256, 0, s>>>(p->partials, kResBlocks, p->d_status);
+  FDI_LAUNCH_CHECK(p);
+  return FDI_OK;
+}
+
+fdi_status launch_reset_status(fdi_plan* p, cudaStream_t s) {
+  k_reset_status<<<1, 1, 0, s>>>(p->d_status);
+  FDI_LAUNCH_CHECK(p);
+  return FDI_OK;
+}
+
+}  // namespace fdi

@@ -1,0 +1,240 @@
+"""Thin ctypes binding over libfdi.so (argument marshalling only).
+
+Every numerical step runs in the CUDA kernels behind the C ABI declared in
+include/fdi.h; this module converts Python arguments (torch CUDA tensors or raw
+device pointers, host face arrays) into the C types and turns a non-OK status
+into an exception.  There is no fallback: if libfdi.so is missing the import
+fails with an explanation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libfdi.so")
+
+OK = 0
+ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_SINGULAR, ERR_UNSUPPORTED = range(1, 8)
+BC_DIRICHLET, BC_NEUMANN = 0, 1
+GRID_CELL, GRID_MAC = 0, 1
+PREC_FP64, PREC_MIXED_TF32, PREC_MIXED_BF16, PREC_MIXED_F16 = 0, 1, 2, 3
+FIELD_CELL, FIELD_U, FIELD_V, FIELD_W = 0, 1, 2, 3
+
+# every function declared in include/fdi.h: name -> (restype, argtypes)
+_vp = C.c_void_p
+_i = C.c_int
+_d = C.c_double
+SIGNATURES = {
+    "fdi_plan_create": (_i, [C.POINTER(C.POINTER(_d)), C.POINTER(_i), C.POINTER(_i), C.POINTER(_i), _i, _i, _i,
+                             C.POINTER(_vp)]),
+    "fdi_plan_destroy": (_i, [_vp]),
+    "fdi_plan_set_tolerances": (_i, [_vp, _d, _i, _d, _i]),
+    "fdi_helmholtz_solve": (_i, [_vp, _d, _vp, _vp, _vp]),
+    "fdi_laplace_solve": (_i, [_vp, _vp, _vp, _vp]),
+    "fdi_field_solve": (_i, [_vp, _i, _d, _d, _vp, _vp, _vp]),
+    "fdi_stokes_solve": (_i, [_vp, _d, _d, C.POINTER(_vp), C.POINTER(_vp), _vp, _vp]),
+    "fdi_helmholtz_solve_batched": (_i, [C.POINTER(_vp), C.POINTER(_d), C.POINTER(_vp), C.POINTER(_vp), _i, _vp]),
+    "fdi_last_result": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_d)]),
+    "fdi_plan_eigen": (_i, [_vp, _i, _i, C.POINTER(_d), C.POINTER(_d), C.POINTER(_d), C.POINTER(_i)]),
+    "fdi_last_launch_count": (_i, [_vp, C.POINTER(C.c_longlong)]),
+    "fdi_plan_enable_timing": (_i, [_vp, _i]),
+    "fdi_plan_kernel_times": (_i, [_vp, _i, C.POINTER(C.c_char_p), C.POINTER(_d), C.POINTER(C.c_longlong),
+                                   C.POINTER(_i)]),
+    "fdi_plan_reset_kernel_times": (_i, [_vp]),
+    "fdi_last_error_message": (C.c_char_p, []),
+    "fdi_status_string": (C.c_char_p, [_i]),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libfdi.so and declare the C signatures; raises if it was not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(
+            f"libfdi.so not found at {_LIB_PATH}: build it with "
+            "`python -m paper_1107_2461_gb300.build` (nvcc, sm_103a); there is no CPU fallback")
+    lib = C.CDLL(_LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class FdiError(RuntimeError):
+    def __init__(self, status, where):
+        lib = load()
+        self.status = status
+        msg = lib.fdi_last_error_message().decode(errors="replace")
+        super().__init__(f"{where}: {lib.fdi_status_string(status).decode()} {msg}")
+
+
+def _check(status, where):
+    if status != OK:
+        raise FdiError(status, where)
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor (must be contiguous FP64 on CUDA) or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("tensor must live on the CUDA device")
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if str(x.dtype) != "torch.float64":
+            raise ValueError("tensor must be float64")
+        return x.data_ptr()
+    raise TypeError(f"expected a CUDA tensor or a device pointer, got {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """Owning handle of an fdi_plan (fdi_plan_create / fdi_plan_destroy)."""
+
+    def __init__(self, faces, n=None, bc_lo=(0, 0, 0), bc_hi=(0, 0, 0), grid=GRID_CELL, prec=PREC_FP64,
+                 thomas_axis=2):
+        lib = load()
+        self._faces = [np.ascontiguousarray(np.asarray(f, dtype=np.float64)) for f in faces]
+        if n is None:
+            n = [f.size - 1 for f in self._faces]
+        self.n = tuple(int(v) for v in n)
+        self.grid, self.prec, self.thomas_axis = grid, prec, thomas_axis
+        fptrs = (C.POINTER(C.c_double) * 3)(*[f.ctypes.data_as(C.POINTER(C.c_double)) for f in self._faces])
+        nn = (C.c_int * 3)(*self.n)
+        lo = (C.c_int * 3)(*[int(b) for b in bc_lo])
+        hi = (C.c_int * 3)(*[int(b) for b in bc_hi])
+        h = C.c_void_p()
+        _check(lib.fdi_plan_create(fptrs, nn, lo, hi, grid, prec, thomas_axis, C.byref(h)), "fdi_plan_create")
+        self.handle = h.value
+
+    def destroy(self):
+        if self.handle:
+            _check(load().fdi_plan_destroy(self.handle), "fdi_plan_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def set_tolerances(self, tol, max_refine, krylov_tol=1e-11, max_iters=200):
+        _check(load().fdi_plan_set_tolerances(self.handle, tol, max_refine, krylov_tol, max_iters),
+               "fdi_plan_set_tolerances")
+
+    def field_shape(self, field=FIELD_CELL):
+        nx, ny, nz = self.n
+        return {FIELD_CELL: (nz, ny, nx), FIELD_U: (nz, ny, nx - 1), FIELD_V: (nz, ny - 1, nx),
+                FIELD_W: (nz - 1, ny, nx)}[field]
+
+    def eigen(self, field=FIELD_CELL, d=0):
+        """(lam, E, Einv) of direction d of a field, copied to host."""
+        lib = load()
+        m = C.c_int()
+        _check(lib.fdi_plan_eigen(self.handle, field, d, None, None, None, C.byref(m)), "fdi_plan_eigen")
+        lam = np.empty(m.value)
+        E = np.empty((m.value, m.value))
+        Einv = np.empty((m.value, m.value))
+        dp = C.POINTER(C.c_double)
+        _check(lib.fdi_plan_eigen(self.handle, field, d, lam.ctypes.data_as(dp), E.ctypes.data_as(dp),
+                                  Einv.ctypes.data_as(dp), C.byref(m)), "fdi_plan_eigen")
+        return lam, E, Einv
+
+
+def plan_create(faces, n=None, bc_lo=(0, 0, 0), bc_hi=(0, 0, 0), grid=GRID_CELL, prec=PREC_FP64, thomas_axis=2):
+    return Plan(faces, n, bc_lo, bc_hi, grid, prec, thomas_axis)
+
+
+def plan_destroy(plan: Plan):
+    plan.destroy()
+
+
+def helmholtz_solve(plan: Plan, lam, rhs, out, stream=None):
+    _check(load().fdi_helmholtz_solve(plan.handle, float(lam), _ptr(rhs), _ptr(out), _stream(stream)),
+           "fdi_helmholtz_solve")
+
+
+def laplace_solve(plan: Plan, rhs, out, stream=None):
+    _check(load().fdi_laplace_solve(plan.handle, _ptr(rhs), _ptr(out), _stream(stream)), "fdi_laplace_solve")
+
+
+def field_solve(plan: Plan, field, sigma, lam, rhs, out, stream=None):
+    _check(load().fdi_field_solve(plan.handle, int(field), float(sigma), float(lam), _ptr(rhs), _ptr(out),
+                                  _stream(stream)), "fdi_field_solve")
+
+
+def stokes_solve(plan: Plan, dt, Re, f, u, p, stream=None):
+    fa = (C.c_void_p * 3)(*[_ptr(t) for t in f])
+    ua = (C.c_void_p * 3)(*[_ptr(t) for t in u])
+    _check(load().fdi_stokes_solve(plan.handle, float(dt), float(Re), fa, ua, _ptr(p), _stream(stream)),
+           "fdi_stokes_solve")
+
+
+def helmholtz_solve_batched(plans, lambdas, rhs, out, stream=None):
+    k = len(plans)
+    pa = (C.c_void_p * k)(*[p.handle for p in plans])
+    la = (C.c_double * k)(*[float(v) for v in lambdas])
+    ra = (C.c_void_p * k)(*[_ptr(t) for t in rhs])
+    oa = (C.c_void_p * k)(*[_ptr(t) for t in out])
+    _check(load().fdi_helmholtz_solve_batched(pa, la, ra, oa, k, _stream(stream)), "fdi_helmholtz_solve_batched")
+
+
+def last_result(plan: Plan):
+    """(iters, refine_steps, rel_residual) of the last solve; synchronise first."""
+    it, rs, rr = C.c_int(), C.c_int(), C.c_double()
+    st = load().fdi_last_result(plan.handle, C.byref(it), C.byref(rs), C.byref(rr))
+    if st not in (OK, ERR_NOT_CONVERGED):
+        _check(st, "fdi_last_result")
+    return it.value, rs.value, rr.value, st
+
+
+def last_launch_count(plan: Plan) -> int:
+    v = C.c_longlong()
+    _check(load().fdi_last_launch_count(plan.handle, C.byref(v)), "fdi_last_launch_count")
+    return v.value
+
+
+def enable_timing(plan: Plan, on=True):
+    _check(load().fdi_plan_enable_timing(plan.handle, 1 if on else 0), "fdi_plan_enable_timing")
+
+
+def kernel_times(plan: Plan, max_entries=64):
+    """{kernel name: (total device ms, launches)} accumulated since the last reset."""
+    names = (C.c_char_p * max_entries)()
+    ms = (C.c_double * max_entries)()
+    cnt = (C.c_longlong * max_entries)()
+    c = C.c_int()
+    _check(load().fdi_plan_kernel_times(plan.handle, max_entries, names, ms, cnt, C.byref(c)),
+           "fdi_plan_kernel_times")
+    return {names[i].decode(): (ms[i], cnt[i]) for i in range(c.value)}
+
+
+def reset_kernel_times(plan: Plan):
+    _check(load().fdi_plan_reset_kernel_times(plan.handle), "fdi_plan_reset_kernel_times")
+
+
+def status_string(s: int) -> str:
+    return load().fdi_status_string(int(s)).decode()

@@ -1,0 +1,71 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/fdi.h; host-side argument checks answer without a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1107_2461_gb300 import build
+    build.build()
+    from paper_1107_2461_gb300 import fdi
+    return fdi.load()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "fdi.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fdi_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for req in ["fdi_plan_create", "fdi_plan_destroy", "fdi_helmholtz_solve", "fdi_laplace_solve",
+                "fdi_stokes_solve", "fdi_helmholtz_solve_batched", "fdi_last_result", "fdi_status_string"]:
+        assert req in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1107_2461_gb300 import fdi
+    assert set(_declared()) <= set(fdi.SIGNATURES)
+
+
+def test_status_strings(lib):
+    from paper_1107_2461_gb300 import fdi
+    assert fdi.status_string(0) == "FDI_OK"
+    assert fdi.status_string(4) == "FDI_ERR_NOT_CONVERGED"
+    assert fdi.status_string(99) == "FDI_ERR_UNKNOWN"
+
+
+def test_invalid_arguments_rejected_without_touching_the_gpu(lib):
+    from paper_1107_2461_gb300 import fdi
+    import numpy as np
+    faces = [np.linspace(0, 1, 9)] * 3
+    # n out of range
+    with pytest.raises(fdi.FdiError) as e:
+        fdi.plan_create(faces, (8, 8, 300))
+    assert e.value.status == fdi.ERR_INVALID_ARG
+    # non-ascending faces
+    bad = [np.linspace(0, 1, 9), np.linspace(1, 0, 9), np.linspace(0, 1, 9)]
+    with pytest.raises(fdi.FdiError) as e:
+        fdi.plan_create(bad, (8, 8, 8))
+    assert e.value.status == fdi.ERR_INVALID_ARG
+    # Thomas axis other than z
+    with pytest.raises(fdi.FdiError) as e:
+        fdi.plan_create(faces, (8, 8, 8), thomas_axis=0)
+    assert e.value.status == fdi.ERR_UNSUPPORTED
+    # null plan handles
+    assert lib.fdi_helmholtz_solve(None, 1.0, None, None, None) == fdi.ERR_INVALID_ARG
+    assert lib.fdi_plan_destroy(None) == fdi.ERR_INVALID_ARG
+    assert lib.fdi_last_result(None, None, None, None) == fdi.ERR_INVALID_ARG
+    assert lib.fdi_helmholtz_solve_batched(None, None, None, None, -1, None) == fdi.ERR_INVALID_ARG

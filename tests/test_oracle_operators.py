@@ -75,9 +75,9 @@ def test_uniform_mixed_walls_quarter_wave():
 @pytest.mark.parametrize("kind,bc", [("cell", (D, D)), ("cell", (N, N)), ("cell", (D, N)),
                                      ("cell", (N, D)), ("face", (D, D))])
 @pytest.mark.parametrize("beta", [1.5, 2.0])
-def test_eigen_invariants_stretched(kind, bc, beta):
+@pytest.mark.parametrize("n", [37, 64, 256])
+def test_eigen_invariants_stretched(kind, bc, beta, n):
     # Eq. 24: D = E Lambda E^{-1}; M-orthonormal eigenvectors E^T M E = I
-    n = 37
     m, K = o1.operator_for(tanh_faces(n, beta), kind, *bc)
     lam, E, Einv = dec.generalized_eig(m, K)
     Dm = o1.second_derivative(m, K)
