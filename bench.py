@@ -139,29 +139,39 @@ def blas_threads():
     return os.cpu_count() or 1
 
 
-def algorithmic_units(name, n):
-    """(bound, algorithmic flops or bytes per launch, unit) of a kernel on an n^3 solve."""
-    P = n[0] * n[1] * n[2]
-    table = {
-        "transform_x_f64": ("alu", 2.0 * P * n[0], "flop"),
-        "transform_y_f64": ("alu", 2.0 * P * n[1], "flop"),
-        "transform_z_f64": ("alu", 2.0 * P * n[2], "flop"),
-        "thomas_z_f64": ("hbm", 16.0 * P, "byte"),
-        "residual_f64": ("hbm", 24.0 * P, "byte"),
+def kernel_model(name, n, steps, K):
+    """(bound, algorithmic units per launch, unit kind, useful launches in K solves).
+
+    Algorithmic work: a transform along direction d costs 2 n_d flop per point
+    (FP64 path) or 3 split products = 6 n_d flop per point on the tensor cores
+    (mixed path); the bytes are one read of the input and one write of the
+    output field (FP32 intermediates, FP64 user arrays, 8-byte double-float
+    solution).  Refinement rounds after convergence return at once and are not
+    counted as useful launches."""
+    P = float(n[0] * n[1] * n[2])
+    rounds = 1 + steps
+    t = {
+        # FP64 path: fwd and back transform of a direction share a name
+        "transform_x_f64": ("alu", 2.0 * P * n[0], "flop", 2 * rounds * K),
+        "transform_y_f64": ("alu", 2.0 * P * n[1], "flop", 2 * rounds * K),
+        "thomas_z_f64": ("hbm", 16.0 * P, "byte", rounds * K),
+        "residual_f64": ("hbm", 24.0 * P, "byte", rounds * K),
+        # mixed path (bytes; the tensor flops are reported beside them)
+        "transform_xf_tc": ("hbm", 8.0 * P, "byte", rounds * K),
+        "transform_yf_tc": ("hbm", 8.0 * P, "byte", rounds * K),
+        "transform_yb_tc": ("hbm", 8.0 * P, "byte", rounds * K),
+        "transform_xb_set_tc": ("hbm", 12.0 * P, "byte", K),
+        "transform_xb_add_tc": ("hbm", 20.0 * P, "byte", steps * K),
+        "thomas_z_f32": ("hbm", 8.0 * P, "byte", rounds * K),
+        "residual_df": ("hbm", 24.0 * P, "byte", (rounds + 1) * K),
     }
-    return table.get(name)
+    return t.get(name)
 
 
-def useful_launches(name, steps, K):
-    # transform kernels run twice per solve pass (forward + back) and the Thomas /
-    # residual once; refinement rounds after convergence return at once and
-    # carry no work
-    per_pass = {"transform_x": 2, "transform_y": 2, "transform_z": 2, "thomas": 1, "residual": 1}
-    for key, v in per_pass.items():
-        if name.startswith(key):
-            passes = 1 + steps
-            return v * passes * K if not name.startswith("residual") else (1 + passes) * K
-    return None
+def tensor_flops(name, n):
+    P = float(n[0] * n[1] * n[2])
+    d = 0 if name.startswith("transform_x") else 1
+    return 6.0 * P * n[d] if name.endswith("_tc") else None
 
 
 def run_arm(fdi, torch, prec, n, K, W, dev, rank, stream):
@@ -294,30 +304,31 @@ def main():
     # roofline of the dominant kernel of the reported arm
     peaks, peak_kind = load_peaks()
     roof = None
-    if best["ktimes"]:
-        dom = max(best["ktimes"].items(), key=lambda kv: kv[1][0])
-        name, (tot_ms, cnt) = dom
-        au = algorithmic_units(name, n)
-        if au is not None:
-            bound, units, kind = au
-            useful = useful_launches(name, best["steps"], K) or cnt
-            if best["prec"] == 0 and name.startswith("residual"):
-                useful = (1 + best["steps"]) * K
-            cnt = min(cnt, useful)
-            avg_s = tot_ms * 1e-3 / cnt
-            if kind == "flop":
-                achieved = units / avg_s / 1e9
-                peak = FP64_PEAK_GFLOPS if bound == "alu" else peaks["bf16_tflops"] * 1e3
-                unit = "GFLOP/s"
-            else:
-                achieved = units / avg_s / 1e9
-                peak = peaks["hbm_gbs"]
-                unit = "GB/s"
-            roof = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                    "frac": achieved / peak, "traffic": None, "avg_launch_ms": tot_ms / cnt,
-                    "launches": cnt,
-                    "peak_source": ("FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz" if bound == "alu"
-                                    else f"MEASURED_PEAKS.json ({peak_kind})")}
+    per_kernel = {}
+    for name, (tot_ms, cnt) in best["ktimes"].items():
+        km = kernel_model(name, n, best["steps"], K)
+        if km is None:
+            continue
+        bound, units, kind, useful = km
+        useful = max(1, min(cnt, useful))
+        avg_s = tot_ms * 1e-3 / useful
+        if kind == "flop":
+            achieved, peak, unit = units / avg_s / 1e9, FP64_PEAK_GFLOPS, "GFLOP/s"
+            src = "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived)"
+        else:
+            achieved, peak, unit = units / avg_s / 1e9, peaks["hbm_gbs"], "GB/s"
+            src = f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"
+        e = {"kernel": name, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+             "frac": achieved / peak, "traffic": None, "avg_launch_ms": tot_ms / useful, "launches": useful,
+             "total_ms": tot_ms, "peak_source": src}
+        tf = tensor_flops(name, n)
+        if tf is not None:
+            e["tensor_tflops"] = tf / avg_s / 1e12
+            e["tensor_frac"] = e["tensor_tflops"] / peaks["bf16_tflops"]
+            e["tensor_peak_source"] = "MEASURED_PEAKS.json bf16_tflops (fp16 dense rate = bf16 rate)"
+        per_kernel[name] = e
+    if per_kernel:
+        roof = dict(max(per_kernel.values(), key=lambda e: e["total_ms"]))
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t = oracle_tpt_time(n)
@@ -336,6 +347,9 @@ def main():
         "roofline": roof,
         "cpu_baseline": cpu,
         "clocks": best["clocks"],
+        "kernels": {k: {kk: round(vv, 4) if isinstance(vv, float) else vv for kk, vv in e.items()
+                        if kk in ("achieved", "unit", "frac", "avg_launch_ms", "launches", "tensor_frac")}
+                    for k, e in per_kernel.items()},
         "arms": {k: {"value": a["value"], "ms_per_solve": a["ms_max"] / K, "rel_residual": a["rel"],
                      "refine_steps": a["steps"], "tol": a["tol"], "met_tol": a["ok"],
                      "kernels": {kn: {"ms_total": v[0], "launches": v[1]} for kn, v in a["ktimes"].items()}}

@@ -152,6 +152,15 @@ fdi_status fdi_last_result(const fdi_plan* plan, int* iters, int* refine_steps,
 fdi_status fdi_plan_eigen(const fdi_plan* plan, fdi_field field, int d, double* lam, double* E,
                           double* Einv, int* m);
 
+/* One split-precision tensor-core transform pass on its own, for testing the
+ * dominant kernel: out[r][k] = sum_j T[k][j] in[r][j] for r < rows, with
+ * T = E_d^{-1} (inverse != 0, the forward transform of Eq. 25) or E_d of
+ * direction d of a field; m = unknowns along d.  in/out: device FP32, row r at
+ * r * pitch, pitch = m rounded up to a multiple of 4; in and out must not
+ * overlap.  Needs a FDI_PREC_MIXED_F16 plan.  Asynchronous on stream. */
+fdi_status fdi_apply_transform(fdi_plan* plan, fdi_field field, int d, int inverse, const float* in, float* out,
+                               long long rows, fdi_stream_t stream);
+
 /* Per-kernel device timing: with timing on, every kernel launch of this plan is
  * bracketed by a CUDA event pair on the launching stream. */
 fdi_status fdi_plan_enable_timing(fdi_plan* plan, int on);

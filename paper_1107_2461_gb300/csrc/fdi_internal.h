@@ -38,19 +38,9 @@ struct Axis {
   double* lam = nullptr;            // eigenvalues, n, descending (closest to 0 first)
   double* E = nullptr;              // n*n row-major E[r][k]   (column k = eigenvector k)
   double* Einv = nullptr;           // n*n row-major Einv[k][r]
-  // mixed-precision copies (filled by the mixed-path setup)
-  void* tc_fwd = nullptr;           // split operand images of E^{-1} (tensor-core layout)
-  void* tc_bwd = nullptr;           // split operand images of E
-  float* tc_fwd_scale = nullptr;    // per-row power-of-two unscale factors
-  float* tc_bwd_scale = nullptr;
-  float* lam_f = nullptr;           // eigenvalues as float (mixed Thomas / divide)
-  float* m_f = nullptr;             // M, K as float for the FP32 Thomas sweep
-  float* kd_f = nullptr;
-  float* ko_f = nullptr;
-  // double-float (hi, lo) residual weights
-  float2* wp_df = nullptr;
-  float2* wm_df = nullptr;
-  float2* w0_df = nullptr;
+  // mixed-precision data of this operator (tensor-core matrices, FP32 and
+  // double-float coefficients); owned, see mixed.cu
+  void* mixed = nullptr;
   // host copies
   std::vector<double> h_m, h_kd, h_ko;
 };
@@ -80,7 +70,8 @@ struct fdi_plan {
   // mixed-path workspace: FP32 buffers + double-float pairs
   float* wf[4] = {nullptr, nullptr, nullptr, nullptr};
   float2* xdf = nullptr;            // solution accumulator (hi, lo)
-  float2* rdf = nullptr;            // residual (hi, lo)
+  float* d_scales = nullptr;        // per refinement round: max |field| of the pass inputs
+  int* d_err = nullptr;             // nonzero: a tensor-core kernel hit a wait limit
   double* partials = nullptr;       // reduction partials
   int npartials = 0;
   fdi::DevStatus* d_status = nullptr;
@@ -167,6 +158,7 @@ fdi_status validate_field_args(const fdi_plan* p, int field, double sigma, doubl
 
 // mixed path (mixed.cu)
 fdi_status mixed_setup(fdi_plan* p);
+void mixed_free_axis(Axis* ax);
 fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda, const double* rhs,
                              double* out, cudaStream_t s);
 

@@ -1,14 +1,595 @@
-// Mixed-precision path (split tensor-core transforms + double-float refinement).
+// Mixed-precision Helmholtz / Laplace inverse: TPT with the x and y transforms
+// on the tensor cores (split fp16, FP32 accumulation), the z Thomas sweep in
+// FP32, and iterative refinement against a double-float residual.
+//
+// One direct solve (Sec. 3, TPT at the end of the section) is five passes over
+// the field.  Each pass writes its output in the orientation the next pass
+// reads with the contraction index contiguous:
+//   r    [z][y][x]   residual (FP32), input of the forward x transform
+//   F1   [z][i][y]   after E_x^{-1}   (i: x mode)
+//   F2   [z][i][j]   after E_y^{-1}   (j: y mode); the Thomas sweep runs in place
+//   F4   [z][y][i]   after E_y
+//   x    [z][y][x]   solution accumulator, double-float (hi, lo)
+// Rows are padded to a multiple of 4 floats (16-byte rows for vector loads).
+//
+// Refinement (the tensor-core solve is accurate to about 1e-6 relative):
+//   r_0 = b;  x_1 = S(r_0);  r_k = b - A x_k (double-float, flux form);
+//   x_{k+1} = x_k + S(r_k)   until ||r_k|| / ||b|| <= tol.
+// Every refinement-round kernel reads the device "done" flag and returns at
+// once after convergence, so the solve is enqueued without host round trips.
+#include <cmath>
+
+#include "df.cuh"
 #include "fdi_internal.h"
+#include "tc_transform.h"
 
 namespace fdi {
 
-fdi_status mixed_setup(fdi_plan* p) { return FDI_OK; }
+struct MixedAxis {
+  TcMatrix fwd, bwd;      // E^{-1} and E on the tensor cores
+  float* m_f = nullptr;   // M, K of the Thomas direction in FP32
+  float* kd_f = nullptr;
+  float* ko_f = nullptr;
+  float2* wp = nullptr;   // residual flux weights in double-float
+  float2* wm = nullptr;
+  float2* w0 = nullptr;
+  float2* m_df = nullptr; // control-volume widths in double-float
+};
 
-fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda, const double* rhs,
-                             double* out, cudaStream_t s) {
-  set_error("mixed precision path not built yet");
-  return FDI_ERR_UNSUPPORTED;
+namespace {
+
+constexpr int kBlocks = 152 * 8;
+constexpr int kThreads = 256;
+
+int pitch4(int n) { return (n + 3) / 4 * 4; }
+
+struct ResidArgs {
+  int nx, ny, nz;
+  const float2* wp[3];
+  const float2* wm[3];
+  const float2* w0[3];
+  const float2* m[3];
+  float2 sigma, lambda;
+  const double* b;
+  const float2* x;      // null: first pass, r = b
+  float* r;
+  int r_pitch;
+  double* out;          // FP64 solution output (null: not written)
+  float* rmax;          // atomic max |r|
+  const DevStatus* st;
+  int sub_mean;
+  int want_mean;        // accumulate sum V b and sum V (first pass) or sum V x (later passes)
+  double* partials;     // per block: sum r^2, sum b^2, sum V b (or V x), sum V
+};
+
+__device__ __forceinline__ df::F2 ld2(const float2* p) {
+  float2 v = *p;
+  return df::make(v.x, v.y);
 }
 
+__global__ void __launch_bounds__(kThreads) k_resid_df(ResidArgs a, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ double sh[4 * (kThreads / 32)];
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const long long sy = nx, sz = (long long)nx * ny;
+  const long long P = sz * nz;
+  df::F2 mean = df::make(0.f, 0.f);
+  if (a.sub_mean) mean = df::from_f64(a.st->mean_b);
+  float srr = 0.f, sbb = 0.f, rmax = 0.f;
+  df::F2 svb = df::make(0.f, 0.f), sv = df::make(0.f, 0.f);
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(p % nx);
+    const long long t = p / nx;
+    const int j = (int)(t % ny), k = (int)(t / ny);
+    df::F2 bb = df::from_f64(a.b[p]);
+    if (a.want_mean) {
+      const df::F2 V = df::mul(df::mul(ld2(a.m[0] + i), ld2(a.m[1] + j)), ld2(a.m[2] + k));
+      svb = df::add(svb, df::mul(V, a.x ? ld2(a.x + p) : bb));
+      sv = df::add(sv, V);
+    }
+    if (a.sub_mean) bb = df::sub(bb, mean);
+    df::F2 r = bb;
+    if (a.x) {
+      const df::F2 uc = ld2(a.x + p);
+      df::F2 L = df::mul(ld2(a.w0[0] + i), uc);
+      L = df::add(L, df::mul(ld2(a.w0[1] + j), uc));
+      L = df::add(L, df::mul(ld2(a.w0[2] + k), uc));
+      if (i + 1 < nx) L = df::add(L, df::mul(ld2(a.wp[0] + i), df::sub(ld2(a.x + p + 1), uc)));
+      if (i > 0) L = df::add(L, df::mul(ld2(a.wm[0] + i), df::sub(ld2(a.x + p - 1), uc)));
+      if (j + 1 < ny) L = df::add(L, df::mul(ld2(a.wp[1] + j), df::sub(ld2(a.x + p + sy), uc)));
+      if (j > 0) L = df::add(L, df::mul(ld2(a.wm[1] + j), df::sub(ld2(a.x + p - sy), uc)));
+      if (k + 1 < nz) L = df::add(L, df::mul(ld2(a.wp[2] + k), df::sub(ld2(a.x + p + sz), uc)));
+      if (k > 0) L = df::add(L, df::mul(ld2(a.wm[2] + k), df::sub(ld2(a.x + p - sz), uc)));
+      r = df::add(df::sub(bb, df::mul(df::make(a.sigma.x, a.sigma.y), uc)),
+                  df::mul(df::make(a.lambda.x, a.lambda.y), L));
+      if (a.out) a.out[p] = df::to_f64(uc);
+    }
+    const float rf = r.hi + r.lo;
+    a.r[((long long)k * ny + j) * a.r_pitch + i] = rf;
+    srr = fmaf(rf, rf, srr);
+    sbb = fmaf(bb.hi, bb.hi, sbb);
+    rmax = fmaxf(rmax, fabsf(rf));
+  }
+  // block reduction (fixed grid and order: deterministic)
+  double v[4] = {(double)srr, (double)sbb, df::to_f64(svb), df::to_f64(sv)};
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  }
+  const int w = threadIdx.x / 32, ln = threadIdx.x % 32;
+  if (ln == 0) {
+    for (int q = 0; q < 4; ++q) sh[4 * w + q] = v[q];
+    if (rmax > 0.f) atomicMax(reinterpret_cast<unsigned int*>(a.rmax), __float_as_uint(rmax));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s[4] = {0, 0, 0, 0};
+    for (int q = 0; q < kThreads / 32; ++q)
+      for (int c = 0; c < 4; ++c) s[c] += sh[4 * q + c];
+    for (int c = 0; c < 4; ++c) a.partials[4 * blockIdx.x + c] = s[c];
+  }
+}
+
+// kind 0: initial pass (b only): record the volume-weighted mean if asked
+// kind 1: first residual check; kind 2: later check (counts a refinement step)
+__global__ void k_finish_mixed(const double* __restrict__ partials, int nblocks, DevStatus* st, double tol,
+                               int kind, int want_mean, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ double sh[4 * 8];
+  double s[4] = {0, 0, 0, 0};
+  for (int q = threadIdx.x; q < nblocks; q += blockDim.x)
+    for (int c = 0; c < 4; ++c) s[c] += partials[4 * q + c];
+  for (int o = 16; o > 0; o >>= 1)
+    for (int c = 0; c < 4; ++c) s[c] += __shfl_down_sync(0xffffffffu, s[c], o);
+  const int w = threadIdx.x / 32, ln = threadIdx.x % 32;
+  if (ln == 0)
+    for (int c = 0; c < 4; ++c) sh[4 * w + c] = s[c];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double t[4] = {0, 0, 0, 0};
+  for (int q = 0; q < (int)(blockDim.x / 32); ++q)
+    for (int c = 0; c < 4; ++c) t[c] += sh[4 * q + c];
+  if (kind == 0) {
+    st->bnorm2 = t[1];
+    if (want_mean) st->mean_b = t[2] / t[3];
+    st->rel_res = 1.0;
+    st->done = 0;
+    return;
+  }
+  const double rel = t[1] > 0.0 ? sqrt(t[0] / t[1]) : sqrt(t[0]);
+  if (kind == 1)
+    st->refine_steps = 0;
+  else
+    st->refine_steps += 1;
+  if (want_mean) st->scal[0] = t[2] / t[3];  // volume-weighted mean of the current solution
+  st->rel_res = rel;
+  st->bnorm2 = t[1];
+  if (!isfinite(rel)) {
+    st->error = 1;
+    st->done = 1;
+  } else {
+    st->done = rel <= tol ? 1 : 0;
+  }
+}
+
+// remove the volume-weighted mean of the FP64 solution (zero-flux Laplace)
+__global__ void k_sub_mean(double* __restrict__ out, long long P, const DevStatus* __restrict__ st) {
+  const double mu = st->scal[0];
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x)
+    out[p] -= mu;
+}
+
+struct Thomas32Args {
+  float* f;           // in/out, element (z, i, j) at z*plane + i*pitch + j
+  float* cs;          // scratch c'_k, same layout
+  int nx, ny, nz, pitch;
+  long long plane;
+  const double* lamx;
+  const double* lamy;
+  const float* mz;
+  const float* kdz;
+  const float* koz;
+  double sigma, lambda;
+  int singular_possible;
+  float* fmax;
+};
+
+__global__ void __launch_bounds__(128) k_thomas_f32(Thomas32Args a, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float vmax = 0.f;
+  if (t < (long long)a.nx * a.ny) {
+    const int i = (int)(t / a.ny), j = (int)(t % a.ny);
+    const long long o = (long long)i * a.pitch + j;
+    const long long pl = a.plane;
+    const int nz = a.nz;
+    const double lab = a.lamx[i] + a.lamy[j];
+    const float s = (float)(a.sigma - a.lambda * lab);
+    const float lam = (float)a.lambda;
+    float* f = a.f + o;
+    float* cs = a.cs + o;
+    if (!(a.singular_possible && lab == 0.0)) {
+      float cp = 0.f, dp = 0.f;
+      for (int k = 0; k < nz; ++k) {
+        const float lo = k > 0 ? -lam * a.koz[k - 1] : 0.f;
+        const float up = k + 1 < nz ? -lam * a.koz[k] : 0.f;
+        const float di = fmaf(s, a.mz[k], -lam * a.kdz[k]);
+        const float inv = __frcp_rn(fmaf(-lo, cp, di));
+        cp = up * inv;
+        dp = fmaf(a.mz[k], f[k * pl], -lo * dp) * inv;
+        cs[k * pl] = cp;
+        f[k * pl] = dp;
+      }
+      float u = dp;
+      vmax = fabsf(u);
+      for (int k = nz - 2; k >= 0; --k) {
+        u = fmaf(-cs[k * pl], u, f[k * pl]);
+        f[k * pl] = u;
+        vmax = fmaxf(vmax, fabsf(u));
+      }
+    } else {
+      // singular line of the zero-flux Laplacian: project, pin u_0 = 0, solve, re-centre
+      float sm = 0.f, sf = 0.f;
+      for (int k = 0; k < nz; ++k) {
+        sm += a.mz[k];
+        sf = fmaf(a.mz[k], f[k * pl], sf);
+      }
+      const float mu = sf / sm;
+      float cp = 0.f, dp = 0.f;
+      for (int k = 1; k < nz; ++k) {
+        const float lo = k > 1 ? -lam * a.koz[k - 1] : 0.f;
+        const float up = k + 1 < nz ? -lam * a.koz[k] : 0.f;
+        const float di = fmaf(s, a.mz[k], -lam * a.kdz[k]);
+        const float inv = __frcp_rn(fmaf(-lo, cp, di));
+        cp = up * inv;
+        dp = fmaf(a.mz[k], f[k * pl] - mu, -lo * dp) * inv;
+        cs[k * pl] = cp;
+        f[k * pl] = dp;
+      }
+      float u = dp, su = a.mz[nz - 1] * dp;
+      for (int k = nz - 2; k >= 1; --k) {
+        u = fmaf(-cs[k * pl], u, f[k * pl]);
+        f[k * pl] = u;
+        su = fmaf(a.mz[k], u, su);
+      }
+      f[0] = 0.f;
+      const float mean = su / sm;
+      for (int k = 0; k < nz; ++k) {
+        const float w = f[k * pl] - mean;
+        f[k * pl] = w;
+        vmax = fmaxf(vmax, fabsf(w));
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  if ((threadIdx.x & 31) == 0 && vmax > 0.f) atomicMax(reinterpret_cast<unsigned int*>(a.fmax), __float_as_uint(vmax));
+}
+
+__global__ void k_absmax(const float* __restrict__ in, long long rows, int n, int pitch, float* __restrict__ mx) {
+  float v = 0.f;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < rows * n;
+       q += (long long)gridDim.x * blockDim.x)
+    v = fmaxf(v, fabsf(in[(q / n) * pitch + q % n]));
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0 && v > 0.f) atomicMax(reinterpret_cast<unsigned int*>(mx), __float_as_uint(v));
+}
+
+#define FDI_TRY(expr)            \
+  do {                           \
+    fdi_status _s = (expr);      \
+    if (_s != FDI_OK) return _s; \
+  } while (0)
+
+float2 split_host(double v) {
+  float h = (float)v;
+  float l = (float)(v - (double)h);
+  return make_float2(h, l);
+}
+
+fdi_status upload_df(float2** dst, const std::vector<double>& v) {
+  std::vector<float2> h(v.size());
+  for (size_t i = 0; i < v.size(); ++i) h[i] = split_host(v[i]);
+  FDI_CUDA_TRY(cudaMalloc(dst, std::max<size_t>(1, h.size()) * sizeof(float2)));
+  FDI_CUDA_TRY(cudaMemcpy(*dst, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  return FDI_OK;
+}
+
+fdi_status upload_f(float** dst, const std::vector<double>& v) {
+  std::vector<float> h(v.size());
+  for (size_t i = 0; i < v.size(); ++i) h[i] = (float)v[i];
+  FDI_CUDA_TRY(cudaMalloc(dst, std::max<size_t>(1, h.size()) * sizeof(float)));
+  FDI_CUDA_TRY(cudaMemcpy(*dst, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+  return FDI_OK;
+}
+
+fdi_status setup_axis(fdi_plan* p, Axis* ax, cudaStream_t s) {
+  MixedAxis* mx = new MixedAxis();
+  ax->mixed = mx;
+  const int n = ax->n;
+  FDI_TRY(tc_prepare_matrix(p, ax->Einv, n, &mx->fwd, s));
+  FDI_TRY(tc_prepare_matrix(p, ax->E, n, &mx->bwd, s));
+  FDI_TRY(upload_f(&mx->m_f, ax->h_m));
+  FDI_TRY(upload_f(&mx->kd_f, ax->h_kd));
+  FDI_TRY(upload_f(&mx->ko_f, ax->h_ko));
+  std::vector<double> wp(n), wm(n), w0(n);
+  for (int i = 0; i < n; ++i) {
+    const double kp = (i + 1 < n) ? ax->h_ko[i] : 0.0;
+    const double km = (i > 0) ? ax->h_ko[i - 1] : 0.0;
+    wp[i] = kp / ax->h_m[i];
+    wm[i] = km / ax->h_m[i];
+    w0[i] = (ax->h_kd[i] + kp + km) / ax->h_m[i];
+  }
+  FDI_TRY(upload_df(&mx->wp, wp));
+  FDI_TRY(upload_df(&mx->wm, wm));
+  FDI_TRY(upload_df(&mx->w0, w0));
+  FDI_TRY(upload_df(&mx->m_df, ax->h_m));
+  return FDI_OK;
+}
+
+}  // namespace
+
+void mixed_free_axis(Axis* ax) {
+  MixedAxis* mx = static_cast<MixedAxis*>(ax->mixed);
+  if (!mx) return;
+  tc_free_matrix(&mx->fwd);
+  tc_free_matrix(&mx->bwd);
+  void* ptrs[] = {mx->m_f, mx->kd_f, mx->ko_f, mx->wp, mx->wm, mx->w0, mx->m_df};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete mx;
+  ax->mixed = nullptr;
+}
+
+fdi_status mixed_setup(fdi_plan* p) {
+  if (p->prec != FDI_PREC_MIXED_F16) {
+    set_error("mixed precision modes other than FDI_PREC_MIXED_F16 are not built");
+    return FDI_ERR_UNSUPPORTED;
+  }
+  if (p->thomas_axis != 2) {
+    set_error("the mixed-precision path runs TPT with Thomas along z (thomas_axis = 2)");
+    return FDI_ERR_UNSUPPORTED;
+  }
+  cudaStream_t s;
+  FDI_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  fdi_status st = FDI_OK;
+  for (Axis* ax : p->axes) {
+    st = setup_axis(p, ax, s);
+    if (st != FDI_OK) break;
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (st != FDI_OK) return st;
+  FDI_CUDA_TRY(e);
+  size_t szr = 1, szf = 1;
+  for (int fi = 0; fi < p->nfields; ++fi) {
+    const Field& f = p->fields[fi];
+    szr = std::max(szr, (size_t)f.n[2] * f.n[1] * pitch4(f.n[0]));
+    szf = std::max(szf, (size_t)f.n[2] * f.n[0] * pitch4(f.n[1]));
+  }
+  FDI_CUDA_TRY(cudaMalloc(&p->wf[0], szr * sizeof(float)));   // r, reused as F4
+  FDI_CUDA_TRY(cudaMalloc(&p->wf[1], szf * sizeof(float)));   // F1
+  FDI_CUDA_TRY(cudaMalloc(&p->wf[2], szf * sizeof(float)));   // F2 / F3
+  FDI_CUDA_TRY(cudaMalloc(&p->wf[3], szf * sizeof(float)));   // Thomas scratch
+  FDI_CUDA_TRY(cudaMalloc(&p->xdf, (size_t)p->Pmax * sizeof(float2)));
+  FDI_CUDA_TRY(cudaMalloc(&p->d_scales, (size_t)(kMaxRefineCap + 2) * 4 * sizeof(float)));
+  FDI_CUDA_TRY(cudaMalloc(&p->d_err, sizeof(int)));
+  FDI_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
+  return FDI_OK;
+}
+
+fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda, const double* rhs, double* out,
+                             cudaStream_t s) {
+  const Field& f = p->fields[field];
+  const int nx = f.n[0], ny = f.n[1], nz = f.n[2];
+  const int px = pitch4(nx), py = pitch4(ny);
+  const MixedAxis* mx = static_cast<const MixedAxis*>(f.ax[0]->mixed);
+  const MixedAxis* my = static_cast<const MixedAxis*>(f.ax[1]->mixed);
+  const MixedAxis* mz = static_cast<const MixedAxis*>(f.ax[2]->mixed);
+  p->launches = 0;
+  FDI_TRY(launch_reset_status(p, s));
+  FDI_CUDA_TRY(cudaMemsetAsync(p->d_scales, 0, (size_t)(kMaxRefineCap + 2) * 4 * sizeof(float), s));
+  const double* b = rhs;
+  if (out == rhs) {
+    FDI_CUDA_TRY(cudaMemcpyAsync(p->ws[4], rhs, f.P * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    b = p->ws[4];
+  }
+  const bool singular = sigma == 0.0 && f.zero_flux_all;
+  float* r = p->wf[0];
+  float* F1 = p->wf[1];
+  float* F2 = p->wf[2];
+  float* CS = p->wf[3];
+  float* F4 = p->wf[0];
+  const int* done = &p->d_status->done;
+
+  ResidArgs ra{};
+  ra.nx = nx;
+  ra.ny = ny;
+  ra.nz = nz;
+  for (int d = 0; d < 3; ++d) {
+    const MixedAxis* m = static_cast<const MixedAxis*>(f.ax[d]->mixed);
+    ra.wp[d] = m->wp;
+    ra.wm[d] = m->wm;
+    ra.w0[d] = m->w0;
+    ra.m[d] = m->m_df;
+  }
+  ra.sigma = split_host(sigma);
+  ra.lambda = split_host(lambda);
+  ra.b = b;
+  ra.r = r;
+  ra.r_pitch = px;
+  ra.st = p->d_status;
+  ra.partials = p->partials;
+
+  // r_0 = b (and the volume-weighted mean of b for the singular problem)
+  {
+    FDI_KTIMER(p, "residual_df", s);
+    ResidArgs a0 = ra;
+    a0.x = nullptr;
+    a0.out = nullptr;
+    a0.sub_mean = 0;
+    a0.want_mean = singular ? 1 : 0;
+    a0.rmax = p->d_scales + 0;
+    k_resid_df<<<kBlocks, kThreads, 0, s>>>(a0, nullptr);
+    FDI_LAUNCH_CHECK(p);
+  }
+  {
+    FDI_KTIMER(p, "reduce", s);
+    k_finish_mixed<<<1, 256, 0, s>>>(p->partials, kBlocks, p->d_status, p->tol, 0, singular ? 1 : 0, nullptr);
+    FDI_LAUNCH_CHECK(p);
+  }
+
+  for (int round = 0; round <= p->max_refine; ++round) {
+    const int* skip = round == 0 ? nullptr : done;
+    float* sc = p->d_scales + 4 * round;
+    float* sc_next = p->d_scales + 4 * (round + 1);
+    // forward x: r [z][y][x] -> F1 [z][i][y]
+    TcArgs t{};
+    t.skip = skip;
+    t.err = p->d_err;
+    t.in = r;
+    t.R = (long long)nz * ny;
+    t.K = nx;
+    t.in_pitch = px;
+    t.scale_in = sc + 0;
+    t.mode = TC_OUT_F32;
+    t.n_out = nx;
+    t.out_f32 = F1;
+    t.S = ny;
+    t.slab_stride = (long long)nx * py;
+    t.row_stride = 1;
+    t.col_stride = py;
+    t.scale_out = sc + 1;
+    FDI_TRY(launch_tc_transform(p, mx->fwd, t, "transform_xf_tc", s));
+    // forward y: F1 [z][i][y] -> F2 [z][i][j]
+    t.in = F1;
+    t.R = (long long)nz * nx;
+    t.K = ny;
+    t.in_pitch = py;
+    t.scale_in = sc + 1;
+    t.n_out = ny;
+    t.out_f32 = F2;
+    t.S = t.R;
+    t.slab_stride = 0;
+    t.row_stride = py;
+    t.col_stride = 1;
+    t.scale_out = nullptr;
+    FDI_TRY(launch_tc_transform(p, my->fwd, t, "transform_yf_tc", s));
+    // Thomas along z, in place on F2
+    {
+      FDI_KTIMER(p, "thomas_z_f32", s);
+      Thomas32Args ta;
+      ta.f = F2;
+      ta.cs = CS;
+      ta.nx = nx;
+      ta.ny = ny;
+      ta.nz = nz;
+      ta.pitch = py;
+      ta.plane = (long long)nx * py;
+      ta.lamx = f.ax[0]->lam;
+      ta.lamy = f.ax[1]->lam;
+      ta.mz = mz->m_f;
+      ta.kdz = mz->kd_f;
+      ta.koz = mz->ko_f;
+      ta.sigma = sigma;
+      ta.lambda = lambda;
+      ta.singular_possible = singular ? 1 : 0;
+      ta.fmax = sc + 2;
+      const long long lines = (long long)nx * ny;
+      k_thomas_f32<<<(unsigned)((lines + 127) / 128), 128, 0, s>>>(ta, skip);
+      FDI_LAUNCH_CHECK(p);
+    }
+    // back y: F2 [z][i][j] -> F4 [z][y][i]
+    t.in = F2;
+    t.R = (long long)nz * nx;
+    t.K = ny;
+    t.in_pitch = py;
+    t.scale_in = sc + 2;
+    t.n_out = ny;
+    t.out_f32 = F4;
+    t.S = nx;
+    t.slab_stride = (long long)ny * px;
+    t.row_stride = 1;
+    t.col_stride = px;
+    t.scale_out = sc + 3;
+    FDI_TRY(launch_tc_transform(p, my->bwd, t, "transform_yb_tc", s));
+    // back x: F4 [z][y][i] -> x (double-float) [z][y][x]
+    t.in = F4;
+    t.R = (long long)nz * ny;
+    t.K = nx;
+    t.in_pitch = px;
+    t.scale_in = sc + 3;
+    t.mode = round == 0 ? TC_OUT_DF_SET : TC_OUT_DF_ADD;
+    t.n_out = nx;
+    t.out_f32 = nullptr;
+    t.out_df = p->xdf;
+    t.scale_out = nullptr;
+    FDI_TRY(launch_tc_transform(p, mx->bwd, t, round == 0 ? "transform_xb_set_tc" : "transform_xb_add_tc", s));
+    // residual of the updated solution, FP64 output, convergence check
+    {
+      FDI_KTIMER(p, "residual_df", s);
+      ResidArgs ak = ra;
+      ak.x = p->xdf;
+      ak.out = out;
+      ak.sub_mean = singular ? 1 : 0;
+      ak.want_mean = singular ? 1 : 0;
+      ak.rmax = sc_next + 0;
+      k_resid_df<<<kBlocks, kThreads, 0, s>>>(ak, skip);
+      FDI_LAUNCH_CHECK(p);
+    }
+    {
+      FDI_KTIMER(p, "reduce", s);
+      k_finish_mixed<<<1, 256, 0, s>>>(p->partials, kBlocks, p->d_status, p->tol, round == 0 ? 1 : 2,
+                                       singular ? 1 : 0, skip);
+      FDI_LAUNCH_CHECK(p);
+    }
+  }
+  if (singular) {
+    // the FP32 sweep projects the null line only to single precision; the
+    // constant is outside the range of A, so shifting it leaves the residual
+    FDI_KTIMER(p, "mean_f64", s);
+    k_sub_mean<<<kBlocks, kThreads, 0, s>>>(out, f.P, p->d_status);
+    FDI_LAUNCH_CHECK(p);
+  }
+  return FDI_OK;
+}
+
+
 }  // namespace fdi
+
+extern "C" fdi_status fdi_apply_transform(fdi_plan* plan, fdi_field field, int d, int inverse, const float* in,
+                                          float* out, long long rows, fdi_stream_t stream) {
+  using namespace fdi;
+  if (!plan || !in || !out || rows < 0 || d < 0 || d > 2 || (int)field < 0 || (int)field >= plan->nfields)
+    return FDI_ERR_INVALID_ARG;
+  if (plan->prec != FDI_PREC_MIXED_F16) {
+    set_error("fdi_apply_transform needs a FDI_PREC_MIXED_F16 plan");
+    return FDI_ERR_UNSUPPORTED;
+  }
+  if (rows == 0) return FDI_OK;
+  const Axis* ax = plan->fields[(int)field].ax[d];
+  const MixedAxis* m = static_cast<const MixedAxis*>(ax->mixed);
+  const int n = ax->n, pitch = pitch4(n);
+  cudaStream_t s = (cudaStream_t)stream;
+  // input scale: max |in| reduced on the device into the first scale slot
+  FDI_CUDA_TRY(cudaMemsetAsync(plan->d_scales, 0, 4 * sizeof(float), s));
+  k_absmax<<<152 * 4, 256, 0, s>>>(in, rows, n, pitch, plan->d_scales);
+  FDI_LAUNCH_CHECK(plan);
+  TcArgs t{};
+  t.in = in;
+  t.R = rows;
+  t.K = n;
+  t.in_pitch = pitch;
+  t.scale_in = plan->d_scales;
+  t.mode = TC_OUT_F32;
+  t.n_out = n;
+  t.out_f32 = out;
+  t.S = rows;
+  t.row_stride = pitch;
+  t.col_stride = 1;
+  t.err = plan->d_err;
+  return launch_tc_transform(plan, inverse ? m->fwd : m->bwd, t, inverse ? "transform_fwd_tc" : "transform_bwd_tc", s);
+}

@@ -147,9 +147,8 @@ fdi_status make_axis(Axis** out, const std::vector<double>& m, const std::vector
 
 void free_axis(Axis* ax) {
   if (!ax) return;
-  void* ptrs[] = {ax->m, ax->kd, ax->ko, ax->wp, ax->wm, ax->w0, ax->lam, ax->E, ax->Einv,
-                  ax->tc_fwd, ax->tc_bwd, ax->tc_fwd_scale, ax->tc_bwd_scale, ax->lam_f,
-                  ax->m_f, ax->kd_f, ax->ko_f, ax->wp_df, ax->wm_df, ax->w0_df};
+  mixed_free_axis(ax);
+  void* ptrs[] = {ax->m, ax->kd, ax->ko, ax->wp, ax->wm, ax->w0, ax->lam, ax->E, ax->Einv};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete ax;
@@ -170,7 +169,8 @@ void free_plan(fdi_plan* p) {
   for (double* w : p->sk)
     if (w) cudaFree(w);
   if (p->xdf) cudaFree(p->xdf);
-  if (p->rdf) cudaFree(p->rdf);
+  if (p->d_scales) cudaFree(p->d_scales);
+  if (p->d_err) cudaFree(p->d_err);
   if (p->partials) cudaFree(p->partials);
   if (p->d_status) cudaFree(p->d_status);
   if (p->h_flag) cudaFreeHost(p->h_flag);
@@ -385,7 +385,23 @@ fdi_status fdi_last_result(const fdi_plan* plan, int* iters, int* refine_steps, 
   if (iters) *iters = st.iters;
   if (refine_steps) *refine_steps = st.refine_steps;
   if (rel_residual) *rel_residual = st.rel_res;
+  if (plan->d_err) {
+    int kerr = 0;
+    e = cudaMemcpy(&kerr, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      set_error(std::string("status copy: ") + cudaGetErrorString(e));
+      return FDI_ERR_CUDA;
+    }
+    if (kerr) {
+      set_error("a tensor-core kernel stopped at a wait limit");
+      return FDI_ERR_TIMEOUT;
+    }
+  }
   if (st.error) return FDI_ERR_NOT_CONVERGED;
+  if (!(st.rel_res <= plan->tol)) {
+    set_error("residual above the tolerance after the last refinement step");
+    return FDI_ERR_NOT_CONVERGED;
+  }
   return FDI_OK;
 }
 

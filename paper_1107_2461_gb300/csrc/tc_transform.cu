@@ -1,0 +1,433 @@
+// Split-precision eigenvector transform on the tcgen05 tensor cores.
+//
+// One pass of the tensor-product solver (Sec. 3, Eq. 25/29) applies a dense
+// n x n matrix T (E_d^{-1} forward, E_d back) along one direction of a field:
+//     out(r, k) = sum_j T[k][j] in(r, j)       for every row r of the field.
+// This is a GEMM with M = rows (128 per tile), N = n outputs and K = n; it is
+// run in mixed precision: every operand x is scaled by a power of two and
+// split into two fp16 parts, x = hi + lo, and the three products
+//     A_hi*B_hi + A_hi*B_lo + A_lo*B_hi
+// are accumulated in FP32 in tensor memory (about 22 significant bits of each
+// operand; the refinement loop around the solver restores FP64 accuracy).
+//
+// Data layout: the input field is a row-major [R][pitch] FP32 matrix with the
+// contraction index contiguous; the pass sequence of the solver writes each
+// intermediate field in the orientation the next pass reads (see mixed.cu).
+// The transform matrix T is split at plan time into B = [T_hi; T_lo] fp16
+// [2*N_pad][K_pad] (row k scaled by its own power of two, undone per output
+// column in the epilogue) and streamed by TMA.
+//
+// Warp roles of the persistent CTA (one per SM, 448 threads):
+//   warp 0      TMA producer of the B chunks
+//   warp 1      TMEM allocator and single-thread MMA issuer
+//   warps 2-9   converters: load FP32 rows of A, scale, split to fp16 hi/lo,
+//               store them in the 128-byte swizzled K-major layout
+//   warps 10-13 epilogue: TMEM -> registers -> unscale -> global store
+// Two shared-memory stages of K = 64, two TMEM accumulators of N_pad columns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "fdi_internal.h"
+#include "tc_common.cuh"
+#include "tc_transform.h"
+
+namespace fdi {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;
+constexpr int STAGES = 2;
+constexpr int NMAX = 256;
+constexpr int A_BYTES = BM * 128;            // one fp16 half of an A chunk: 16 KB
+constexpr int B_BYTES = NMAX * 128;          // one fp16 half of a B chunk: up to 32 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int NCONV = 8;
+constexpr int THREADS = 32 * (2 + NCONV + 4);
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+
+__device__ __forceinline__ float scale_from_max(float mx) {
+  // power of two that maps mx into [2^14, 2^15): fp16 keeps 11 bits there and
+  // the split low part stays a normal number for values down to mx * 2^-17
+  uint32_t b = __float_as_uint(mx);
+  int e = (int)((b >> 23) & 0xff);
+  if (e == 0 || e == 255) return 1.0f;
+  int se = 127 + 14 - (e - 127);
+  se = se < 1 ? 1 : (se > 254 ? 254 : se);
+  return __uint_as_float((uint32_t)se << 23);
+}
+
+__device__ __forceinline__ uint32_t pack_half2(__half a, __half b) {
+  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
+
+template <int C>
+__global__ void __launch_bounds__(THREADS, 1) k_tc_transform(const __grid_constant__ CUtensorMap tmB, TcArgs a) {
+  if (a.skip && *a.skip) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* full_b = bars;        // B chunk landed (TMA transaction bytes)
+  uint64_t* conv = bars + 2;      // A chunk converted (NCONV warp arrivals)
+  uint64_t* empty = bars + 4;     // stage consumed by the MMAs (C commits)
+  uint64_t* accf = bars + 6;      // accumulator complete
+  uint64_t* acce = bars + 8;      // accumulator drained by the epilogue
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
+  __shared__ volatile int s_abort;
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const uint32_t rank = (C > 1) ? tc::cluster_ctarank() : 0u;
+  const int N_pad = a.N_pad;
+  uint32_t tmem_cols = 32;
+  while (tmem_cols < (uint32_t)(2 * N_pad)) tmem_cols <<= 1;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&full_b[s], 1);
+      tc::mbar_init(&conv[s], NCONV);
+      tc::mbar_init(&empty[s], C);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&accf[b], 1);
+      tc::mbar_init(&acce[b], 4);
+    }
+    s_abort = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmB);
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, tmem_cols);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (C > 1) tc::cluster_sync();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const long long num_tiles = (a.R + BM - 1) / BM;
+  const long long iters_all = (num_tiles + gridDim.x - 1) / gridDim.x;
+  const long long my_iters =
+      (C > 1) ? iters_all
+              : (blockIdx.x < num_tiles ? (num_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0);
+  const int nK = a.nK;
+
+  if (warp == 0) {
+    // ---------------- TMA producer (B) ----------------
+    if (lane == 0) {
+      const uint32_t bbytes = (uint32_t)(2 * N_pad * 128);
+      const int rows_per = N_pad / C;
+      const int r0 = (int)rank * rows_per;
+      uint32_t g = 0;
+      for (long long it = 0; it < my_iters && !s_abort; ++it) {
+        for (int kc = 0; kc < nK; ++kc, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (g / STAGES) & 1;
+          if (!tc::mbar_wait(&empty[s], ph ^ 1, &s_abort)) {
+            s_abort = 1;
+            atomicExch(a.err, 1);
+            break;
+          }
+          tc::mbar_expect_tx(&full_b[s], bbytes);
+          uint8_t* st = smem + s * STAGE_BYTES;
+          const uint32_t dhi = tc::smem_u32(st + 2 * A_BYTES) + r0 * 128;
+          const uint32_t dlo = tc::smem_u32(st + 2 * A_BYTES + B_BYTES) + r0 * 128;
+          if (C == 1) {
+            tc::tma_load_2d(dhi, &tmB, kc * BK, r0, &full_b[s]);
+            tc::tma_load_2d(dlo, &tmB, kc * BK, N_pad + r0, &full_b[s]);
+          } else {
+            const uint16_t mask = (uint16_t)((1u << C) - 1u);
+            tc::tma_load_2d_mc(dhi, &tmB, kc * BK, r0, &full_b[s], mask);
+            tc::tma_load_2d_mc(dlo, &tmB, kc * BK, N_pad + r0, &full_b[s], mask);
+          }
+        }
+      }
+      if (C > 1 && !s_abort) {
+        // every CTA's commits for the last stages must have reached this CTA's
+        // barriers before the cluster may retire
+        const uint32_t total = (uint32_t)(my_iters * nK);
+        for (uint32_t g2 = (total > STAGES ? total - STAGES : 0); g2 < total; ++g2) {
+          if (!tc::mbar_wait(&empty[g2 % STAGES], (g2 / STAGES) & 1, &s_abort)) {
+            atomicExch(a.err, 1);
+            break;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_f16_f32(BM, N_pad);
+      uint32_t g = 0;
+      for (long long it = 0; it < my_iters && !s_abort; ++it) {
+        const int buf = (int)(it & 1);
+        const uint32_t aph = (uint32_t)((it >> 1) & 1);
+        if (!tc::mbar_wait(&acce[buf], aph ^ 1, &s_abort)) {
+          s_abort = 1;
+          atomicExch(a.err, 2);
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t d = tmem_base + (uint32_t)(buf * N_pad);
+        bool ok = true;
+        for (int kc = 0; kc < nK; ++kc, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (g / STAGES) & 1;
+          if (!tc::mbar_wait(&full_b[s], ph, &s_abort) || !tc::mbar_wait(&conv[s], ph, &s_abort)) {
+            ok = false;
+            break;
+          }
+          tc::tc_fence_after();
+          uint8_t* st = smem + s * STAGE_BYTES;
+          const uint32_t ahi = tc::smem_u32(st), alo = tc::smem_u32(st + A_BYTES);
+          const uint32_t bhi = tc::smem_u32(st + 2 * A_BYTES), blo = tc::smem_u32(st + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint32_t off = kk * 32;
+            const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
+            tc::mma_f16(d, tc::sdesc_k_sw128(ahi + off), tc::sdesc_k_sw128(bhi + off), idesc, acc);
+            tc::mma_f16(d, tc::sdesc_k_sw128(ahi + off), tc::sdesc_k_sw128(blo + off), idesc, 1u);
+            tc::mma_f16(d, tc::sdesc_k_sw128(alo + off), tc::sdesc_k_sw128(bhi + off), idesc, 1u);
+          }
+          if (C == 1)
+            tc::mma_commit(&empty[s]);
+          else
+            tc::mma_commit_mc(&empty[s], (uint16_t)((1u << C) - 1u));
+        }
+        if (!ok) {
+          s_abort = 1;
+          atomicExch(a.err, 3);
+          break;
+        }
+        tc::mma_commit(&accf[buf]);
+      }
+    }
+  } else if (warp < 2 + NCONV) {
+    // ---------------- converters ----------------
+    const int ct = (warp - 2) * 32 + lane;  // 0..255
+    const float sA = scale_from_max(a.scale_in ? *a.scale_in : 1.0f);
+    const int c8 = ct & 7;                  // 16-byte chunk within the 128-byte row
+    uint32_t g = 0;
+    for (long long it = 0; it < my_iters && !s_abort; ++it) {
+      const long long tile = blockIdx.x + it * gridDim.x;
+      const long long row0 = tile * BM;
+      for (int kc = 0; kc < nK && !s_abort; ++kc, ++g) {
+        const int s = g % STAGES;
+        const uint32_t ph = (g / STAGES) & 1;
+        float v[4][8];
+        const int k0 = kc * BK + c8 * 8;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int row = (ct >> 3) + 32 * q;
+          const long long grow = row0 + row;
+          float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+          if (tile < num_tiles && grow < a.R) {
+            const float* src = a.in + grow * (long long)a.in_pitch + k0;
+            if (k0 < a.in_pitch) x0 = *reinterpret_cast<const float4*>(src);
+            if (k0 + 4 < a.in_pitch) x1 = *reinterpret_cast<const float4*>(src + 4);
+          }
+          v[q][0] = x0.x; v[q][1] = x0.y; v[q][2] = x0.z; v[q][3] = x0.w;
+          v[q][4] = x1.x; v[q][5] = x1.y; v[q][6] = x1.z; v[q][7] = x1.w;
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            if (k0 + e >= a.K) v[q][e] = 0.f;
+        }
+        if (!tc::mbar_wait(&empty[s], ph ^ 1, &s_abort)) {
+          s_abort = 1;
+          atomicExch(a.err, 4);
+          break;
+        }
+        uint8_t* st = smem + s * STAGE_BYTES;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int row = (ct >> 3) + 32 * q;
+          uint32_t hw[4], lw[4];
+#pragma unroll
+          for (int e = 0; e < 8; e += 2) {
+            const float x0 = v[q][e] * sA, x1 = v[q][e + 1] * sA;
+            const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
+            const __half l0 = __float2half_rn(x0 - __half2float(h0));
+            const __half l1 = __float2half_rn(x1 - __half2float(h1));
+            hw[e / 2] = pack_half2(h0, h1);
+            lw[e / 2] = pack_half2(l0, l1);
+          }
+          const uint32_t off = tc::sw128_offset(row, c8 * 8);
+          *reinterpret_cast<uint4*>(st + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4*>(st + A_BYTES + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+        tc::fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&conv[s]);
+      }
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3;  // TMEM lane quarter accessible to this warp
+    const float inv_sA = 1.0f / scale_from_max(a.scale_in ? *a.scale_in : 1.0f);
+    float vmax = 0.f;
+    for (long long it = 0; it < my_iters && !s_abort; ++it) {
+      const long long tile = blockIdx.x + it * gridDim.x;
+      const int buf = (int)(it & 1);
+      const uint32_t aph = (uint32_t)((it >> 1) & 1);
+      if (!tc::mbar_wait(&accf[buf], aph, &s_abort)) {
+        s_abort = 1;
+        atomicExch(a.err, 5);
+        break;
+      }
+      tc::tc_fence_after();
+      const long long row = tile * BM + 32 * q + lane;
+      const bool vrow = tile < num_tiles && row < a.R;
+      long long base = 0;
+      if (vrow) base = (row / a.S) * a.slab_stride + (row % a.S) * a.row_stride;
+      for (int c0 = 0; c0 < N_pad; c0 += 32) {
+        uint32_t r[32];
+        tc::tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * N_pad + c0), r);
+        tc::tmem_ld_wait();
+        if (vrow) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int k = c0 + j;
+            if (k < a.n_out) {
+              const float val = __uint_as_float(r[j]) * inv_sA * a.col_scale[k];
+              if (a.mode == TC_OUT_F32) {
+                a.out_f32[base + (long long)k * a.col_stride] = val;
+                vmax = fmaxf(vmax, fabsf(val));
+              } else {
+                float2* x = a.out_df + row * (long long)a.n_out + k;
+                if (a.mode == TC_OUT_DF_SET) {
+                  *x = make_float2(val, 0.f);
+                } else {
+                  float2 o = *x;
+                  const float sh = o.x + val;
+                  const float bb = sh - o.x;
+                  const float er = (o.x - (sh - bb)) + (val - bb) + o.y;
+                  const float nh = sh + er;
+                  *x = make_float2(nh, er - (nh - sh));
+                }
+              }
+            }
+          }
+        }
+      }
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acce[buf]);
+    }
+    if (a.scale_out) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+      if (lane == 0 && vmax > 0.f) atomicMax(reinterpret_cast<unsigned int*>(a.scale_out), __float_as_uint(vmax));
+    }
+  }
+
+  tc::tc_fence_before();
+  __syncthreads();
+  if (C > 1) tc::cluster_sync();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem_base, tmem_cols);
+  }
+}
+
+__global__ void k_prep_b(const double* __restrict__ T, int n, int N_pad, int K_pad, __half* __restrict__ B,
+                         float* __restrict__ col_scale) {
+  // row k of T (output k) -> scaled by a power of two, split into fp16 hi/lo
+  const int k = blockIdx.x;
+  __shared__ double smax[256];
+  double mx = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    if (k < n) mx = fmax(mx, fabs(T[(size_t)k * n + j]));
+  smax[threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+    __syncthreads();
+  }
+  mx = smax[0];
+  double sc = 1.0;
+  if (mx > 0.0) sc = exp2(14.0 - floor(log2(mx)));
+  if (threadIdx.x == 0) col_scale[k] = (float)(1.0 / sc);
+  for (int j = threadIdx.x; j < K_pad; j += blockDim.x) {
+    double t = (k < n && j < n) ? T[(size_t)k * n + j] * sc : 0.0;
+    __half h = __double2half(t);
+    __half l = __double2half(t - (double)__half2float(h));
+    B[(size_t)k * K_pad + j] = h;
+    B[(size_t)(N_pad + k) * K_pad + j] = l;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+int tc_cluster_size() { return 1; }
+
+fdi_status tc_prepare_matrix(fdi_plan* p, const double* T, int n, TcMatrix* m, cudaStream_t s) {
+  m->n = n;
+  m->N_pad = ((n + 31) / 32) * 32;
+  m->K_pad = ((n + BK - 1) / BK) * BK;
+  const size_t elems = (size_t)2 * m->N_pad * m->K_pad;
+  FDI_CUDA_TRY(cudaMalloc(&m->B, elems * sizeof(__half)));
+  FDI_CUDA_TRY(cudaMalloc(&m->col_scale, m->N_pad * sizeof(float)));
+  FDI_CUDA_TRY(cudaMemsetAsync(m->col_scale, 0, m->N_pad * sizeof(float), s));
+  k_prep_b<<<m->N_pad, 256, 0, s>>>(T, n, m->N_pad, m->K_pad, (__half*)m->B, m->col_scale);
+  FDI_LAUNCH_CHECK(p);
+  auto enc = encode_fn();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled entry point unavailable");
+    return FDI_ERR_CUDA;
+  }
+  const int C = tc_cluster_size();
+  cuuint64_t dims[2] = {(cuuint64_t)m->K_pad, (cuuint64_t)(2 * m->N_pad)};
+  cuuint64_t strides[1] = {(cuuint64_t)m->K_pad * sizeof(__half)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)(m->N_pad / C)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(reinterpret_cast<CUtensorMap*>(m->tmap), CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, m->B, dims, strides,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed for a transform matrix");
+    return FDI_ERR_CUDA;
+  }
+  return FDI_OK;
+}
+
+void tc_free_matrix(TcMatrix* m) {
+  if (m->B) cudaFree(m->B);
+  if (m->col_scale) cudaFree(m->col_scale);
+  m->B = nullptr;
+  m->col_scale = nullptr;
+}
+
+fdi_status launch_tc_transform(fdi_plan* p, const TcMatrix& m, TcArgs args, const char* name, cudaStream_t s) {
+  FDI_KTIMER(p, name, s);
+  static bool attr_set = false;
+  if (!attr_set) {
+    FDI_CUDA_TRY(cudaFuncSetAttribute(k_tc_transform<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    attr_set = true;
+  }
+  args.N_pad = m.N_pad;
+  args.nK = (args.K + BK - 1) / BK;
+  args.col_scale = m.col_scale;
+  const long long tiles = (args.R + BM - 1) / BM;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+  const int grid = (int)(tiles < sms ? tiles : sms);
+  CUtensorMap map;
+  memcpy(&map, m.tmap, sizeof(CUtensorMap));
+  k_tc_transform<1><<<grid, THREADS, SMEM_BYTES, s>>>(map, args);
+  FDI_LAUNCH_CHECK(p);
+  return FDI_OK;
+}
+
+}  // namespace fdi

@@ -1,0 +1,48 @@
+// Split-precision tcgen05 transform pass: declarations shared by the solver.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "fdi_internal.h"
+
+namespace fdi {
+
+enum { TC_OUT_F32 = 0, TC_OUT_DF_SET = 1, TC_OUT_DF_ADD = 2 };
+
+// A transform matrix T (n x n, output index k, input index j) prepared for the
+// tensor cores: B = [hi; lo] fp16 [2*N_pad][K_pad], per-row power-of-two scale
+// undone by col_scale[k], and its TMA descriptor.
+struct TcMatrix {
+  int n = 0, N_pad = 0, K_pad = 0;
+  void* B = nullptr;
+  float* col_scale = nullptr;
+  alignas(64) unsigned char tmap[128];
+};
+
+struct TcArgs {
+  // input: rows of K contiguous FP32 values, row r at in + r * in_pitch
+  const float* in = nullptr;
+  long long R = 0;
+  int K = 0;
+  int in_pitch = 0;
+  const float* scale_in = nullptr;  // device: max |in| (sets the fp16 scaling)
+  // output: element (r, k) of an FP32 field at
+  //   (r / S) * slab_stride + (r % S) * row_stride + k * col_stride
+  // or the double-float accumulator out_df[r * n_out + k]
+  int mode = TC_OUT_F32;
+  int n_out = 0;
+  float* out_f32 = nullptr;
+  float2* out_df = nullptr;
+  long long S = 1, slab_stride = 0, row_stride = 0, col_stride = 1;
+  float* scale_out = nullptr;       // device: atomic max |out| (next pass's scaling)
+  const int* skip = nullptr;
+  int* err = nullptr;
+  // filled by the launcher
+  int N_pad = 0, nK = 0;
+  const float* col_scale = nullptr;
+};
+
+fdi_status tc_prepare_matrix(fdi_plan* p, const double* T, int n, TcMatrix* m, cudaStream_t s);
+void tc_free_matrix(TcMatrix* m);
+fdi_status launch_tc_transform(fdi_plan* p, const TcMatrix& m, TcArgs args, const char* name, cudaStream_t s);
+
+}  // namespace fdi

@@ -39,6 +39,7 @@ SIGNATURES = {
     "fdi_last_result": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_d)]),
     "fdi_plan_eigen": (_i, [_vp, _i, _i, C.POINTER(_d), C.POINTER(_d), C.POINTER(_d), C.POINTER(_i)]),
     "fdi_last_launch_count": (_i, [_vp, C.POINTER(C.c_longlong)]),
+    "fdi_apply_transform": (_i, [_vp, _i, _i, _i, _vp, _vp, C.c_longlong, _vp]),
     "fdi_plan_enable_timing": (_i, [_vp, _i]),
     "fdi_plan_kernel_times": (_i, [_vp, _i, C.POINTER(C.c_char_p), C.POINTER(_d), C.POINTER(C.c_longlong),
                                    C.POINTER(_i)]),
@@ -215,6 +216,18 @@ def last_launch_count(plan: Plan) -> int:
     v = C.c_longlong()
     _check(load().fdi_last_launch_count(plan.handle, C.byref(v)), "fdi_last_launch_count")
     return v.value
+
+
+def _fptr(x):
+    """Device pointer of a contiguous float32 CUDA tensor."""
+    if not (x.is_cuda and x.is_contiguous() and str(x.dtype) == "torch.float32"):
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    return x.data_ptr()
+
+
+def apply_transform(plan: Plan, field, d, inverse, inp, out, rows, stream=None):
+    _check(load().fdi_apply_transform(plan.handle, int(field), int(d), 1 if inverse else 0, _fptr(inp), _fptr(out),
+                                      int(rows), _stream(stream)), "fdi_apply_transform")
 
 
 def enable_timing(plan: Plan, on=True):
