@@ -163,7 +163,8 @@ def kernel_model(name, n, steps, K):
         "transform_xb_set_tc": ("hbm", 12.0 * P, "byte", K),
         "transform_xb_add_tc": ("hbm", 20.0 * P, "byte", steps * K),
         "thomas_z_f32": ("hbm", 8.0 * P, "byte", rounds * K),
-        "residual_df": ("hbm", 24.0 * P, "byte", (rounds + 1) * K),
+        "residual_df": ("hbm", 28.0 * P, "byte", rounds * K),
+        "residual_df_init": ("hbm", 12.0 * P, "byte", K),
     }
     return t.get(name)
 
@@ -174,9 +175,11 @@ def tensor_flops(name, n):
     return 6.0 * P * n[d] if name.endswith("_tc") else None
 
 
-def run_arm(fdi, torch, prec, n, K, W, dev, rank, stream):
+def run_arm(fdi, torch, prec, n, K, W, dev, rank, stream, cluster=None):
     faces = workloads.box_faces(n, BETA)
     plan = fdi.plan_create(faces, n, prec=prec)
+    if cluster is not None and prec != fdi.PREC_FP64:
+        fdi.set_transform_config(plan, cluster)
     f = workloads.rhs_uniform(n[::-1], rank)
     rhs = torch.from_numpy(f).to(dev)
     out = torch.empty_like(rhs)
@@ -233,6 +236,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--arms", default="fp64,mixed")
+    ap.add_argument("--cluster", type=int, default=None, help="tensor-core transform cluster size (1, 2, 4)")
     args = ap.parse_args()
     n = (args.n, args.n, args.n)
     P = n[0] * n[1] * n[2]
@@ -281,7 +285,7 @@ def main():
     for name in args.arms.split(","):
         prec, tol = precs[name]
         try:
-            arms[name] = run_arm(fdi, torch, prec, n, K, W, dev, rank, stream)
+            arms[name] = run_arm(fdi, torch, prec, n, K, W, dev, rank, stream, args.cluster)
             arms[name]["tol"] = tol
             arms[name]["prec"] = prec
         except fdi.FdiError as e:

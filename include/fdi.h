@@ -161,6 +161,13 @@ fdi_status fdi_plan_eigen(const fdi_plan* plan, fdi_field field, int d, double* 
 fdi_status fdi_apply_transform(fdi_plan* plan, fdi_field field, int d, int inverse, const float* in, float* out,
                                long long rows, fdi_stream_t stream);
 
+/* Launch shape of the tensor-core transforms of a mixed plan: `cluster` CTAs
+ * (1, 2 or 4) form a thread-block cluster and share each chunk of the
+ * transform matrix through TMA multicast, dividing its L2 reads by `cluster`.
+ * A tuning knob (see the autotuner in the Python package); results do not
+ * depend on it beyond FP32 rounding order.  Default 1. */
+fdi_status fdi_plan_set_transform_config(fdi_plan* plan, int cluster);
+
 /* Per-kernel device timing: with timing on, every kernel launch of this plan is
  * bracketed by a CUDA event pair on the launching stream. */
 fdi_status fdi_plan_enable_timing(fdi_plan* plan, int on);

@@ -67,51 +67,84 @@ __device__ __forceinline__ df::F2 ld2(const float2* p) {
   return df::make(v.x, v.y);
 }
 
-__global__ void __launch_bounds__(kThreads) k_resid_df(ResidArgs a, const int* __restrict__ skip) {
+// z-marching residual: a block covers a 32 (x) x 8 (y) tile of columns and a
+// range of planes; each thread keeps x at k-1, k, k+1 in registers, reuses the
+// z difference of the previous plane and gets the x difference of its left
+// neighbour by shuffle.  Work per block is fixed, so the reduction order is too.
+constexpr int kResTX = 32, kResTY = 8, kResZChunk = 16;
+
+__global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const int* __restrict__ skip) {
   if (skip && *skip) return;
-  __shared__ double sh[4 * (kThreads / 32)];
+  __shared__ double sh[4 * kResTY];
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const long long sy = nx, sz = (long long)nx * ny;
-  const long long P = sz * nz;
+  const int lane = threadIdx.x, wy = threadIdx.y;
+  const int i = blockIdx.x * kResTX + lane, j = blockIdx.y * kResTY + wy;
+  const int k0 = blockIdx.z * kResZChunk, k1 = min(nz, k0 + kResZChunk);
+  const bool act = i < nx && j < ny;
+  const int ic = min(i, nx - 1), jc = min(j, ny - 1);
   df::F2 mean = df::make(0.f, 0.f);
   if (a.sub_mean) mean = df::from_f64(a.st->mean_b);
+  const df::F2 sig = df::make(a.sigma.x, a.sigma.y), lam = df::make(a.lambda.x, a.lambda.y);
+  const df::F2 wpx = ld2(a.wp[0] + ic), wmx = ld2(a.wm[0] + ic), wpy = ld2(a.wp[1] + jc), wmy = ld2(a.wm[1] + jc);
+  const df::F2 w0xy = df::add(ld2(a.w0[0] + ic), ld2(a.w0[1] + jc));
+  df::F2 Vxy = df::make(0.f, 0.f);
+  if (a.want_mean) Vxy = df::mul(ld2(a.m[0] + ic), ld2(a.m[1] + jc));
   float srr = 0.f, sbb = 0.f, rmax = 0.f;
   df::F2 svb = df::make(0.f, 0.f), sv = df::make(0.f, 0.f);
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P;
-       p += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(p % nx);
-    const long long t = p / nx;
-    const int j = (int)(t % ny), k = (int)(t / ny);
-    df::F2 bb = df::from_f64(a.b[p]);
+  const df::F2 zero = df::make(0.f, 0.f);
+  const long long col = (long long)jc * nx + ic;
+  df::F2 xc = zero, dzm = zero;
+  if (a.x && k0 < k1) {
+    xc = ld2(a.x + (long long)k0 * sz + col);
+    if (k0 > 0) dzm = df::sub(ld2(a.x + (long long)(k0 - 1) * sz + col), xc);
+  }
+  for (int k = k0; k < k1; ++k) {
+    const long long p = (long long)k * sz + col;
+    df::F2 bb = act ? df::from_f64(a.b[p]) : zero;
     if (a.want_mean) {
-      const df::F2 V = df::mul(df::mul(ld2(a.m[0] + i), ld2(a.m[1] + j)), ld2(a.m[2] + k));
-      svb = df::add(svb, df::mul(V, a.x ? ld2(a.x + p) : bb));
-      sv = df::add(sv, V);
+      const df::F2 V = df::mul(Vxy, ld2(a.m[2] + k));
+      if (act) {
+        svb = df::add(svb, df::mul(V, a.x ? xc : bb));
+        sv = df::add(sv, V);
+      }
     }
     if (a.sub_mean) bb = df::sub(bb, mean);
     df::F2 r = bb;
     if (a.x) {
-      const df::F2 uc = ld2(a.x + p);
-      df::F2 L = df::mul(ld2(a.w0[0] + i), uc);
-      L = df::add(L, df::mul(ld2(a.w0[1] + j), uc));
-      L = df::add(L, df::mul(ld2(a.w0[2] + k), uc));
-      if (i + 1 < nx) L = df::add(L, df::mul(ld2(a.wp[0] + i), df::sub(ld2(a.x + p + 1), uc)));
-      if (i > 0) L = df::add(L, df::mul(ld2(a.wm[0] + i), df::sub(ld2(a.x + p - 1), uc)));
-      if (j + 1 < ny) L = df::add(L, df::mul(ld2(a.wp[1] + j), df::sub(ld2(a.x + p + sy), uc)));
-      if (j > 0) L = df::add(L, df::mul(ld2(a.wm[1] + j), df::sub(ld2(a.x + p - sy), uc)));
-      if (k + 1 < nz) L = df::add(L, df::mul(ld2(a.wp[2] + k), df::sub(ld2(a.x + p + sz), uc)));
-      if (k > 0) L = df::add(L, df::mul(ld2(a.wm[2] + k), df::sub(ld2(a.x + p - sz), uc)));
-      r = df::add(df::sub(bb, df::mul(df::make(a.sigma.x, a.sigma.y), uc)),
-                  df::mul(df::make(a.lambda.x, a.lambda.y), L));
-      if (a.out) a.out[p] = df::to_f64(uc);
+      df::F2 xp = zero;
+      if (k + 1 < nz) xp = ld2(a.x + p + sz);
+      // x direction: d+ = x[i+1] - x[i]; lane i-1's d+ is -(x[i-1] - x[i])
+      df::F2 xr;
+      xr.hi = __shfl_down_sync(0xffffffffu, xc.hi, 1);
+      xr.lo = __shfl_down_sync(0xffffffffu, xc.lo, 1);
+      if (lane == kResTX - 1 && i + 1 < nx) xr = ld2(a.x + p + 1);
+      const df::F2 dxp = (i + 1 < nx) ? df::sub(xr, xc) : zero;
+      df::F2 dxm;
+      dxm.hi = -__shfl_up_sync(0xffffffffu, dxp.hi, 1);
+      dxm.lo = -__shfl_up_sync(0xffffffffu, dxp.lo, 1);
+      if (lane == 0) dxm = (i > 0) ? df::sub(ld2(a.x + p - 1), xc) : zero;
+      df::F2 L = df::mul(df::add(w0xy, ld2(a.w0[2] + k)), xc);
+      if (i + 1 < nx) L = df::add(L, df::mul(wpx, dxp));
+      if (i > 0) L = df::add(L, df::mul(wmx, dxm));
+      if (j + 1 < ny) L = df::add(L, df::mul(wpy, df::sub(ld2(a.x + p + sy), xc)));
+      if (j > 0) L = df::add(L, df::mul(wmy, df::sub(ld2(a.x + p - sy), xc)));
+      const df::F2 dzp = (k + 1 < nz) ? df::sub(xp, xc) : zero;
+      if (k + 1 < nz) L = df::add(L, df::mul(ld2(a.wp[2] + k), dzp));
+      if (k > 0) L = df::add(L, df::mul(ld2(a.wm[2] + k), dzm));
+      r = df::add(df::sub(bb, df::mul(sig, xc)), df::mul(lam, L));
+      if (act && a.out) a.out[p] = df::to_f64(xc);
+      dzm = df::neg(dzp);
+      xc = xp;
     }
-    const float rf = r.hi + r.lo;
-    a.r[((long long)k * ny + j) * a.r_pitch + i] = rf;
-    srr = fmaf(rf, rf, srr);
-    sbb = fmaf(bb.hi, bb.hi, sbb);
-    rmax = fmaxf(rmax, fabsf(rf));
+    if (act) {
+      const float rf = r.hi + r.lo;
+      a.r[((long long)k * ny + j) * a.r_pitch + i] = rf;
+      srr = fmaf(rf, rf, srr);
+      sbb = fmaf(bb.hi, bb.hi, sbb);
+      rmax = fmaxf(rmax, fabsf(rf));
+    }
   }
-  // block reduction (fixed grid and order: deterministic)
   double v[4] = {(double)srr, (double)sbb, df::to_f64(svb), df::to_f64(sv)};
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -119,18 +152,23 @@ __global__ void __launch_bounds__(kThreads) k_resid_df(ResidArgs a, const int* _
     for (int q = 0; q < 4; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
     rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
   }
-  const int w = threadIdx.x / 32, ln = threadIdx.x % 32;
-  if (ln == 0) {
-    for (int q = 0; q < 4; ++q) sh[4 * w + q] = v[q];
+  if (lane == 0) {
+    for (int q = 0; q < 4; ++q) sh[4 * wy + q] = v[q];
     if (rmax > 0.f) atomicMax(reinterpret_cast<unsigned int*>(a.rmax), __float_as_uint(rmax));
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s[4] = {0, 0, 0, 0};
-    for (int q = 0; q < kThreads / 32; ++q)
-      for (int c = 0; c < 4; ++c) s[c] += sh[4 * q + c];
-    for (int c = 0; c < 4; ++c) a.partials[4 * blockIdx.x + c] = s[c];
+  if (lane == 0 && wy == 0) {
+    double t[4] = {0, 0, 0, 0};
+    for (int q = 0; q < kResTY; ++q)
+      for (int c = 0; c < 4; ++c) t[c] += sh[4 * q + c];
+    const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    for (int c = 0; c < 4; ++c) a.partials[4 * bid + c] = t[c];
   }
+}
+
+dim3 resid_grid(int nx, int ny, int nz) {
+  return dim3((unsigned)((nx + kResTX - 1) / kResTX), (unsigned)((ny + kResTY - 1) / kResTY),
+              (unsigned)((nz + kResZChunk - 1) / kResZChunk));
 }
 
 // kind 0: initial pass (b only): record the volume-weighted mean if asked
@@ -197,63 +235,113 @@ struct Thomas32Args {
   float* fmax;
 };
 
+constexpr int kTB = 16;  // Thomas checkpoint / prefetch block
+
+// one elimination step of the z sweep: c'_k and d'_k from c'_{k-1}, d'_{k-1}
+__device__ __forceinline__ void thomas_step(float s, float m, float lkd, float lo, float up, float f, float& cp,
+                                            float& dp) {
+  const float di = fmaf(s, m, -lkd);
+  const float inv = __frcp_rn(fmaf(-lo, cp, di));
+  cp = up * inv;
+  dp = fmaf(m, f, -lo * dp) * inv;
+}
+
 __global__ void __launch_bounds__(128) k_thomas_f32(Thomas32Args a, const int* __restrict__ skip) {
   if (skip && *skip) return;
+  // coefficients of the z operator (M, lambda*K) in shared memory
+  __shared__ float s_m[kMaxN], s_lkd[kMaxN], s_lko[kMaxN + 1];
+  const int nz = a.nz;
+  const float lam = (float)a.lambda;
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+    s_m[k] = a.mz[k];
+    s_lkd[k] = lam * a.kdz[k];
+    s_lko[k] = (k + 1 < nz) ? lam * a.koz[k] : 0.f;
+  }
+  __syncthreads();
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   float vmax = 0.f;
   if (t < (long long)a.nx * a.ny) {
     const int i = (int)(t / a.ny), j = (int)(t % a.ny);
-    const long long o = (long long)i * a.pitch + j;
     const long long pl = a.plane;
-    const int nz = a.nz;
     const double lab = a.lamx[i] + a.lamy[j];
     const float s = (float)(a.sigma - a.lambda * lab);
-    const float lam = (float)a.lambda;
-    float* f = a.f + o;
-    float* cs = a.cs + o;
+    float* f = a.f + (long long)i * a.pitch + j;
     if (!(a.singular_possible && lab == 0.0)) {
+      // forward elimination in blocks of kTB: loads of a block issued together,
+      // d'_k stored in place, c'_{k0-1} kept at each block start (checkpoint)
+      float ckp[kMaxN / kTB];
       float cp = 0.f, dp = 0.f;
-      for (int k = 0; k < nz; ++k) {
-        const float lo = k > 0 ? -lam * a.koz[k - 1] : 0.f;
-        const float up = k + 1 < nz ? -lam * a.koz[k] : 0.f;
-        const float di = fmaf(s, a.mz[k], -lam * a.kdz[k]);
-        const float inv = __frcp_rn(fmaf(-lo, cp, di));
-        cp = up * inv;
-        dp = fmaf(a.mz[k], f[k * pl], -lo * dp) * inv;
-        cs[k * pl] = cp;
-        f[k * pl] = dp;
+      const int nb = (nz + kTB - 1) / kTB;
+      for (int b = 0; b < nb; ++b) {
+        const int k0 = b * kTB;
+        ckp[b] = cp;
+        float fv[kTB];
+#pragma unroll
+        for (int e = 0; e < kTB; ++e) fv[e] = (k0 + e < nz) ? f[(k0 + e) * pl] : 0.f;
+#pragma unroll
+        for (int e = 0; e < kTB; ++e) {
+          const int k = k0 + e;
+          if (k < nz) {
+            const float lo = k > 0 ? -s_lko[k - 1] : 0.f;
+            thomas_step(s, s_m[k], s_lkd[k], lo, -s_lko[k], fv[e], cp, dp);
+            fv[e] = dp;
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < kTB; ++e)
+          if (k0 + e < nz) f[(k0 + e) * pl] = fv[e];
       }
-      float u = dp;
-      vmax = fabsf(u);
-      for (int k = nz - 2; k >= 0; --k) {
-        u = fmaf(-cs[k * pl], u, f[k * pl]);
-        f[k * pl] = u;
-        vmax = fmaxf(vmax, fabsf(u));
+      // back substitution block by block from the top, c'_k recomputed from
+      // the checkpoint with the same operations (bit-identical)
+      float u = 0.f;
+      for (int b = nb - 1; b >= 0; --b) {
+        const int k0 = b * kTB;
+        float cpb[kTB], dv[kTB];
+        float c = ckp[b], d = 0.f;
+#pragma unroll
+        for (int e = 0; e < kTB; ++e) {
+          const int k = k0 + e;
+          dv[e] = (k < nz) ? f[k * pl] : 0.f;
+          if (k < nz) {
+            const float lo = k > 0 ? -s_lko[k - 1] : 0.f;
+            thomas_step(s, s_m[k], s_lkd[k], lo, -s_lko[k], 0.f, c, d);
+          }
+          cpb[e] = c;
+        }
+#pragma unroll
+        for (int e = kTB - 1; e >= 0; --e) {
+          const int k = k0 + e;
+          if (k < nz) {
+            u = (k == nz - 1) ? dv[e] : fmaf(-cpb[e], u, dv[e]);
+            dv[e] = u;
+            vmax = fmaxf(vmax, fabsf(u));
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < kTB; ++e)
+          if (k0 + e < nz) f[(k0 + e) * pl] = dv[e];
       }
     } else {
       // singular line of the zero-flux Laplacian: project, pin u_0 = 0, solve, re-centre
+      float* cs = a.cs + (long long)i * a.pitch + j;
       float sm = 0.f, sf = 0.f;
       for (int k = 0; k < nz; ++k) {
-        sm += a.mz[k];
-        sf = fmaf(a.mz[k], f[k * pl], sf);
+        sm += s_m[k];
+        sf = fmaf(s_m[k], f[k * pl], sf);
       }
       const float mu = sf / sm;
       float cp = 0.f, dp = 0.f;
       for (int k = 1; k < nz; ++k) {
-        const float lo = k > 1 ? -lam * a.koz[k - 1] : 0.f;
-        const float up = k + 1 < nz ? -lam * a.koz[k] : 0.f;
-        const float di = fmaf(s, a.mz[k], -lam * a.kdz[k]);
-        const float inv = __frcp_rn(fmaf(-lo, cp, di));
-        cp = up * inv;
-        dp = fmaf(a.mz[k], f[k * pl] - mu, -lo * dp) * inv;
+        const float lo = k > 1 ? -s_lko[k - 1] : 0.f;
+        thomas_step(s, s_m[k], s_lkd[k], lo, -s_lko[k], f[k * pl] - mu, cp, dp);
         cs[k * pl] = cp;
         f[k * pl] = dp;
       }
-      float u = dp, su = a.mz[nz - 1] * dp;
+      float u = dp, su = s_m[nz - 1] * dp;
       for (int k = nz - 2; k >= 1; --k) {
         u = fmaf(-cs[k * pl], u, f[k * pl]);
         f[k * pl] = u;
-        su = fmaf(a.mz[k], u, su);
+        su = fmaf(s_m[k], u, su);
       }
       f[0] = 0.f;
       const float mean = su / sm;
@@ -405,6 +493,12 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
   float* F4 = p->wf[0];
   const int* done = &p->d_status->done;
 
+  const dim3 rgrid = resid_grid(nx, ny, nz);
+  const int rblocks = (int)(rgrid.x * rgrid.y * rgrid.z);
+  if (rblocks > p->npartials) {
+    set_error("grid too large for the reduction buffer");
+    return FDI_ERR_INVALID_ARG;
+  }
   ResidArgs ra{};
   ra.nx = nx;
   ra.ny = ny;
@@ -426,19 +520,19 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
 
   // r_0 = b (and the volume-weighted mean of b for the singular problem)
   {
-    FDI_KTIMER(p, "residual_df", s);
+    FDI_KTIMER(p, "residual_df_init", s);
     ResidArgs a0 = ra;
     a0.x = nullptr;
     a0.out = nullptr;
     a0.sub_mean = 0;
     a0.want_mean = singular ? 1 : 0;
     a0.rmax = p->d_scales + 0;
-    k_resid_df<<<kBlocks, kThreads, 0, s>>>(a0, nullptr);
+    k_resid_df<<<rgrid, dim3(kResTX, kResTY), 0, s>>>(a0, nullptr);
     FDI_LAUNCH_CHECK(p);
   }
   {
     FDI_KTIMER(p, "reduce", s);
-    k_finish_mixed<<<1, 256, 0, s>>>(p->partials, kBlocks, p->d_status, p->tol, 0, singular ? 1 : 0, nullptr);
+    k_finish_mixed<<<1, 256, 0, s>>>(p->partials, rblocks, p->d_status, p->tol, 0, singular ? 1 : 0, nullptr);
     FDI_LAUNCH_CHECK(p);
   }
 
@@ -537,12 +631,12 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
       ak.sub_mean = singular ? 1 : 0;
       ak.want_mean = singular ? 1 : 0;
       ak.rmax = sc_next + 0;
-      k_resid_df<<<kBlocks, kThreads, 0, s>>>(ak, skip);
+      k_resid_df<<<rgrid, dim3(kResTX, kResTY), 0, s>>>(ak, skip);
       FDI_LAUNCH_CHECK(p);
     }
     {
       FDI_KTIMER(p, "reduce", s);
-      k_finish_mixed<<<1, 256, 0, s>>>(p->partials, kBlocks, p->d_status, p->tol, round == 0 ? 1 : 2,
+      k_finish_mixed<<<1, 256, 0, s>>>(p->partials, rblocks, p->d_status, p->tol, round == 0 ? 1 : 2,
                                        singular ? 1 : 0, skip);
       FDI_LAUNCH_CHECK(p);
     }
@@ -592,4 +686,10 @@ extern "C" fdi_status fdi_apply_transform(fdi_plan* plan, fdi_field field, int d
   t.col_stride = 1;
   t.err = plan->d_err;
   return launch_tc_transform(plan, inverse ? m->fwd : m->bwd, t, inverse ? "transform_fwd_tc" : "transform_bwd_tc", s);
+}
+
+extern "C" fdi_status fdi_plan_set_transform_config(fdi_plan* plan, int cluster) {
+  if (!plan || (cluster != 1 && cluster != 2 && cluster != 4)) return FDI_ERR_INVALID_ARG;
+  plan->tc_cluster = cluster;
+  return FDI_OK;
 }

@@ -253,7 +253,7 @@ fdi_status build_plan(fdi_plan* p, const double* const faces[3], const fdi_bc bc
     if (f.P > p->Pmax) p->Pmax = f.P;
   }
   for (int i = 0; i < 5; ++i) FDI_TRY(dev_alloc(&p->ws[i], (size_t)p->Pmax));
-  p->npartials = 152 * 8;
+  p->npartials = 16384;  // per-block partial sums of the reductions (>= blocks of any reduction grid)
   FDI_TRY(dev_alloc(&p->partials, (size_t)p->npartials * 4));
   FDI_TRY(dev_alloc(&p->d_status, 1));
   FDI_CUDA_TRY(cudaMemset(p->d_status, 0, sizeof(DevStatus)));

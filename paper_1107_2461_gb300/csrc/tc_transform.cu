@@ -43,7 +43,8 @@ constexpr int B_BYTES = NMAX * 128;          // one fp16 half of a B chunk: up t
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int NCONV = 8;
 constexpr int THREADS = 32 * (2 + NCONV + 4);
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int TP_BYTES = 4 * 32 * 33 * 4;     // epilogue transpose tiles, one per epilogue warp
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256 + TP_BYTES;
 
 __device__ __forceinline__ float scale_from_max(float mx) {
   // power of two that maps mx into [2^14, 2^15): fp16 keeps 11 bits there and
@@ -203,78 +204,94 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_transform(const __grid_consta
     }
   } else if (warp < 2 + NCONV) {
     // ---------------- converters ----------------
+    // Each thread owns 4 (row, 16-byte chunk) slots of a 128 x 64 A chunk; the
+    // global loads of the next chunk are issued before the current one is
+    // converted, so two chunks of loads are in flight per converter warp.
     const int ct = (warp - 2) * 32 + lane;  // 0..255
     const float sA = scale_from_max(a.scale_in ? *a.scale_in : 1.0f);
     const int c8 = ct & 7;                  // 16-byte chunk within the 128-byte row
-    uint32_t g = 0;
-    for (long long it = 0; it < my_iters && !s_abort; ++it) {
+    const long long total = my_iters * nK;
+    auto load_chunk = [&](long long gi, float (&v)[4][8]) {
+      const long long it = gi / nK;
+      const int kc = (int)(gi % nK);
       const long long tile = blockIdx.x + it * gridDim.x;
       const long long row0 = tile * BM;
-      for (int kc = 0; kc < nK && !s_abort; ++kc, ++g) {
-        const int s = g % STAGES;
-        const uint32_t ph = (g / STAGES) & 1;
-        float v[4][8];
-        const int k0 = kc * BK + c8 * 8;
+      const int k0 = kc * BK + c8 * 8;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int row = (ct >> 3) + 32 * q;
-          const long long grow = row0 + row;
-          float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
-          if (tile < num_tiles && grow < a.R) {
-            const float* src = a.in + grow * (long long)a.in_pitch + k0;
-            if (k0 < a.in_pitch) x0 = *reinterpret_cast<const float4*>(src);
-            if (k0 + 4 < a.in_pitch) x1 = *reinterpret_cast<const float4*>(src + 4);
-          }
-          v[q][0] = x0.x; v[q][1] = x0.y; v[q][2] = x0.z; v[q][3] = x0.w;
-          v[q][4] = x1.x; v[q][5] = x1.y; v[q][6] = x1.z; v[q][7] = x1.w;
-#pragma unroll
-          for (int e = 0; e < 8; ++e)
-            if (k0 + e >= a.K) v[q][e] = 0.f;
+      for (int q = 0; q < 4; ++q) {
+        const long long grow = row0 + (ct >> 3) + 32 * q;
+        float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
+        if (tile < num_tiles && grow < a.R) {
+          const float* src = a.in + grow * (long long)a.in_pitch + k0;
+          if (k0 < a.in_pitch) x0 = __ldg(reinterpret_cast<const float4*>(src));
+          if (k0 + 4 < a.in_pitch) x1 = __ldg(reinterpret_cast<const float4*>(src + 4));
         }
-        if (!tc::mbar_wait(&empty[s], ph ^ 1, &s_abort)) {
-          s_abort = 1;
-          atomicExch(a.err, 4);
-          break;
-        }
-        uint8_t* st = smem + s * STAGE_BYTES;
+        v[q][0] = x0.x; v[q][1] = x0.y; v[q][2] = x0.z; v[q][3] = x0.w;
+        v[q][4] = x1.x; v[q][5] = x1.y; v[q][6] = x1.z; v[q][7] = x1.w;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int row = (ct >> 3) + 32 * q;
-          uint32_t hw[4], lw[4];
-#pragma unroll
-          for (int e = 0; e < 8; e += 2) {
-            const float x0 = v[q][e] * sA, x1 = v[q][e + 1] * sA;
-            const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
-            const __half l0 = __float2half_rn(x0 - __half2float(h0));
-            const __half l1 = __float2half_rn(x1 - __half2float(h1));
-            hw[e / 2] = pack_half2(h0, h1);
-            lw[e / 2] = pack_half2(l0, l1);
-          }
-          const uint32_t off = tc::sw128_offset(row, c8 * 8);
-          *reinterpret_cast<uint4*>(st + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-          *reinterpret_cast<uint4*>(st + A_BYTES + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-        }
-        tc::fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&conv[s]);
+        for (int e = 0; e < 8; ++e)
+          if (k0 + e >= a.K) v[q][e] = 0.f;
       }
+    };
+    float v[4][8], w[4][8];
+    if (total > 0) load_chunk(0, v);
+    for (long long gi = 0; gi < total && !s_abort; ++gi) {
+      const uint32_t g = (uint32_t)gi;
+      const int s = g % STAGES;
+      const uint32_t ph = (g / STAGES) & 1;
+      if (gi + 1 < total) load_chunk(gi + 1, w);
+      if (!tc::mbar_wait(&empty[s], ph ^ 1, &s_abort)) {
+        atomicExch(a.err, 4);
+        break;
+      }
+      uint8_t* st = smem + s * STAGE_BYTES;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int row = (ct >> 3) + 32 * q;
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+          const float x0 = v[q][e] * sA, x1 = v[q][e + 1] * sA;
+          const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
+          const __half l0 = __float2half_rn(x0 - __half2float(h0));
+          const __half l1 = __float2half_rn(x1 - __half2float(h1));
+          hw[e / 2] = pack_half2(h0, h1);
+          lw[e / 2] = pack_half2(l0, l1);
+        }
+        const uint32_t off = tc::sw128_offset(row, c8 * 8);
+        *reinterpret_cast<uint4*>(st + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(st + A_BYTES + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      }
+      tc::fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&conv[s]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[q][e] = w[q][e];
     }
   } else {
     // ---------------- epilogue ----------------
+    // Each thread holds one accumulator row (TMEM lane) and 32 columns per
+    // load.  Transposed outputs (consecutive rows contiguous) are stored
+    // directly; row-major outputs go through a 32 x 33 shared tile so that each
+    // warp store covers 32 consecutive columns of one row.
     const int q = warp & 3;  // TMEM lane quarter accessible to this warp
     const float inv_sA = 1.0f / scale_from_max(a.scale_in ? *a.scale_in : 1.0f);
+    float* tp = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256) + (warp - (2 + NCONV)) * (32 * 33);
+    const bool rowmajor = a.mode != TC_OUT_F32 || a.col_stride == 1;
     float vmax = 0.f;
     for (long long it = 0; it < my_iters && !s_abort; ++it) {
       const long long tile = blockIdx.x + it * gridDim.x;
       const int buf = (int)(it & 1);
       const uint32_t aph = (uint32_t)((it >> 1) & 1);
       if (!tc::mbar_wait(&accf[buf], aph, &s_abort)) {
-        s_abort = 1;
         atomicExch(a.err, 5);
         break;
       }
       tc::tc_fence_after();
-      const long long row = tile * BM + 32 * q + lane;
+      const long long wrow0 = tile * BM + 32 * q;   // first row of this warp
+      const long long row = wrow0 + lane;
       const bool vrow = tile < num_tiles && row < a.R;
       long long base = 0;
       if (vrow) base = (row / a.S) * a.slab_stride + (row % a.S) * a.row_stride;
@@ -282,30 +299,62 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_transform(const __grid_consta
         uint32_t r[32];
         tc::tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * N_pad + c0), r);
         tc::tmem_ld_wait();
-        if (vrow) {
+        if (!rowmajor) {
+          if (vrow) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int k = c0 + j;
-            if (k < a.n_out) {
-              const float val = __uint_as_float(r[j]) * inv_sA * a.col_scale[k];
-              if (a.mode == TC_OUT_F32) {
+            for (int j = 0; j < 32; ++j) {
+              const int k = c0 + j;
+              if (k < a.n_out) {
+                const float val = __uint_as_float(r[j]) * inv_sA * a.col_scale[k];
                 a.out_f32[base + (long long)k * a.col_stride] = val;
                 vmax = fmaxf(vmax, fabsf(val));
-              } else {
-                float2* x = a.out_df + row * (long long)a.n_out + k;
-                if (a.mode == TC_OUT_DF_SET) {
-                  *x = make_float2(val, 0.f);
-                } else {
-                  float2 o = *x;
-                  const float sh = o.x + val;
-                  const float bb = sh - o.x;
-                  const float er = (o.x - (sh - bb)) + (val - bb) + o.y;
-                  const float nh = sh + er;
-                  *x = make_float2(nh, er - (nh - sh));
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) tp[lane * 33 + j] = __uint_as_float(r[j]);
+          __syncwarp();
+          const int k = c0 + lane;
+          const bool kval = k < a.n_out;
+          const float cs = kval ? a.col_scale[k] * inv_sA : 0.f;
+          const int nrows = (int)min((long long)32, a.R - wrow0);  // rows of this warp inside the field
+          if (a.mode == TC_OUT_F32) {
+            for (int i = 0; i < 32; ++i) {
+              const long long bi = __shfl_sync(0xffffffffu, base, i);
+              if (tile < num_tiles && i < nrows && kval) {
+                const float val = tp[i * 33 + lane] * cs;
+                a.out_f32[bi + k] = val;
+                vmax = fmaxf(vmax, fabsf(val));
+              }
+            }
+          } else if (tile < num_tiles && kval) {
+            float2* xcol = a.out_df + wrow0 * (long long)a.n_out + k;
+            const long long rs = a.n_out;
+            if (a.mode == TC_OUT_DF_SET) {
+              for (int i = 0; i < nrows; ++i) xcol[i * rs] = make_float2(tp[i * 33 + lane] * cs, 0.f);
+            } else {
+              // read-modify-write of the double-float accumulator, loads batched
+              for (int i0 = 0; i0 < nrows; i0 += 8) {
+                float2 o[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                  if (i0 + i < nrows) o[i] = xcol[(i0 + i) * rs];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                  if (i0 + i < nrows) {
+                    const float val = tp[(i0 + i) * 33 + lane] * cs;
+                    const float sh = o[i].x + val;
+                    const float bb = sh - o[i].x;
+                    const float er = (o[i].x - (sh - bb)) + (val - bb) + o[i].y;
+                    const float nh = sh + er;
+                    xcol[(i0 + i) * rs] = make_float2(nh, er - (nh - sh));
+                  }
                 }
               }
             }
           }
+          __syncwarp();
         }
       }
       tc::tc_fence_before();
@@ -370,8 +419,6 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
-int tc_cluster_size() { return 1; }
-
 fdi_status tc_prepare_matrix(fdi_plan* p, const double* T, int n, TcMatrix* m, cudaStream_t s) {
   m->n = n;
   m->N_pad = ((n + 31) / 32) * 32;
@@ -387,17 +434,19 @@ fdi_status tc_prepare_matrix(fdi_plan* p, const double* T, int n, TcMatrix* m, c
     set_error("cuTensorMapEncodeTiled entry point unavailable");
     return FDI_ERR_CUDA;
   }
-  const int C = tc_cluster_size();
-  cuuint64_t dims[2] = {(cuuint64_t)m->K_pad, (cuuint64_t)(2 * m->N_pad)};
-  cuuint64_t strides[1] = {(cuuint64_t)m->K_pad * sizeof(__half)};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)(m->N_pad / C)};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(reinterpret_cast<CUtensorMap*>(m->tmap), CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, m->B, dims, strides,
-                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) {
-    set_error("cuTensorMapEncodeTiled failed for a transform matrix");
-    return FDI_ERR_CUDA;
+  const int Cs[3] = {1, 2, 4};
+  for (int ci = 0; ci < 3; ++ci) {
+    cuuint64_t dims[2] = {(cuuint64_t)m->K_pad, (cuuint64_t)(2 * m->N_pad)};
+    cuuint64_t strides[1] = {(cuuint64_t)m->K_pad * sizeof(__half)};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)(m->N_pad / Cs[ci])};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(reinterpret_cast<CUtensorMap*>(m->tmap[ci]), CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, m->B, dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      set_error("cuTensorMapEncodeTiled failed for a transform matrix");
+      return FDI_ERR_CUDA;
+    }
   }
   return FDI_OK;
 }
@@ -409,25 +458,48 @@ void tc_free_matrix(TcMatrix* m) {
   m->col_scale = nullptr;
 }
 
-fdi_status launch_tc_transform(fdi_plan* p, const TcMatrix& m, TcArgs args, const char* name, cudaStream_t s) {
-  FDI_KTIMER(p, name, s);
+template <int C>
+fdi_status launch_cluster(fdi_plan* p, const TcMatrix& m, const TcArgs& args, long long tiles, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
-    FDI_CUDA_TRY(cudaFuncSetAttribute(k_tc_transform<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    FDI_CUDA_TRY(cudaFuncSetAttribute(k_tc_transform<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     attr_set = true;
   }
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+  long long grid = tiles < sms ? tiles : sms;
+  grid = (grid + C - 1) / C * C;
+  if (grid > sms) grid = sms / C * C;
+  CUtensorMap map;
+  memcpy(&map, m.tmap[tc_cluster_index(C)], sizeof(CUtensorMap));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  FDI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_transform<C>, map, args));
+  FDI_LAUNCH_CHECK(p);
+  return FDI_OK;
+}
+
+fdi_status launch_tc_transform(fdi_plan* p, const TcMatrix& m, TcArgs args, const char* name, cudaStream_t s) {
+  FDI_KTIMER(p, name, s);
   args.N_pad = m.N_pad;
   args.nK = (args.K + BK - 1) / BK;
   args.col_scale = m.col_scale;
   const long long tiles = (args.R + BM - 1) / BM;
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-  const int grid = (int)(tiles < sms ? tiles : sms);
-  CUtensorMap map;
-  memcpy(&map, m.tmap, sizeof(CUtensorMap));
-  k_tc_transform<1><<<grid, THREADS, SMEM_BYTES, s>>>(map, args);
-  FDI_LAUNCH_CHECK(p);
-  return FDI_OK;
+  switch (p->tc_cluster) {
+    case 2: return launch_cluster<2>(p, m, args, tiles, s);
+    case 4: return launch_cluster<4>(p, m, args, tiles, s);
+    default: return launch_cluster<1>(p, m, args, tiles, s);
+  }
 }
 
 }  // namespace fdi

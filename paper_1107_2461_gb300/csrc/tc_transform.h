@@ -15,8 +15,13 @@ struct TcMatrix {
   int n = 0, N_pad = 0, K_pad = 0;
   void* B = nullptr;
   float* col_scale = nullptr;
-  alignas(64) unsigned char tmap[128];
+  // TMA descriptors of B for clusters of 1, 2 and 4 CTAs (each CTA of a cluster
+  // loads N_pad / C rows of every chunk and multicasts them to the others)
+  alignas(64) unsigned char tmap[3][128];
 };
+
+// cluster sizes the transform kernel is built for
+inline int tc_cluster_index(int c) { return c == 4 ? 2 : (c == 2 ? 1 : 0); }
 
 struct TcArgs {
   // input: rows of K contiguous FP32 values, row r at in + r * in_pitch
