@@ -168,6 +168,30 @@ fdi_status fdi_apply_transform(fdi_plan* plan, fdi_field field, int d, int inver
  * depend on it beyond FP32 rounding order.  Default 1. */
 fdi_status fdi_plan_set_transform_config(fdi_plan* plan, int cluster);
 
+/* Allocation-free eigen decomposition of one 1D operator (the same kernel as
+ * plan creation).  No counterpart in the paper: it exists for callers that may
+ * not allocate device memory -- code that runs where cudaMalloc is forbidden or
+ * would stall (an allocation-free real-time or serving loop, a runtime that owns
+ * every device allocation) -- and that still need the eigenbasis of a new grid.
+ * It calls no cudaMalloc, cudaFree or other allocating routine: the kernel's
+ * scratch (the 1D operator, its job descriptor, its convergence flag) lives in a
+ * file-scope device array of 3*256+16 doubles, present on every device that
+ * loads the library until the process exits.
+ *   faces       host, n+1 ascending doubles; face_kind 0: n cell unknowns with
+ *               the walls bc_lo / bc_hi; face_kind 1: the n-1 interior-face
+ *               unknowns of a staggered velocity component (no-slip walls)
+ *   lam, E, Einv device outputs: m, m*m, m*m doubles (m unknowns, row-major
+ *               as fdi_plan_eigen)
+ *   converged   optional host pointer: if given, the call synchronises `stream`
+ *               and stores 1 if the QL iteration converged, else 0
+ * Limits: 2 <= n <= 256 (3 <= n for face_kind 1); larger n is rejected with
+ * FDI_ERR_INVALID_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call shares the one array and overwrites it (the flag is
+ * cleared per call): calls that overlap on the GPU, on any stream, race. */
+fdi_status fdi_eigen_noalloc(const double* faces, int n, int face_kind, fdi_bc bc_lo, fdi_bc bc_hi, double* lam,
+                             double* E, double* Einv, int* converged, fdi_stream_t stream);
+
 /* Per-kernel device timing: with timing on, every kernel launch of this plan is
  * bracketed by a CUDA event pair on the launching stream. */
 fdi_status fdi_plan_enable_timing(fdi_plan* plan, int on);

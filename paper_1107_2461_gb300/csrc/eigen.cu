@@ -13,6 +13,8 @@
 // For a zero-flux operator the null pair is set exactly: Lambda = 0 with the
 // constant eigenvector (the reading of Eq. 28 used throughout).
 #include <cmath>
+#include <mutex>
+#include <string>
 
 #include "fdi_internal.h"
 
@@ -197,4 +199,119 @@ fdi_status eigen_decompose_all(const std::vector<Axis*>& axes, cudaStream_t s, i
   return FDI_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the eigen decomposition.
+//
+// For callers that may not allocate device memory (code running where
+// cudaMalloc is forbidden or unsafe, such as allocation-free real-time loops or
+// runtimes that own every device allocation) and that still want the 1D
+// eigenbasis of a new grid: the kernel's scratch -- the 1D operator it reads,
+// its job descriptor and its convergence flag -- lives in the file-scope array
+// below instead of in buffers allocated per call.  The eigenvector matrix is
+// accumulated in the caller's E^{-1} output, as in the plan path.
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+// layout: m[kMaxN] | kd[kMaxN] | ko[kMaxN] | job (8 doubles) | flag (8 doubles)
+constexpr int kNoallocDoubles = 3 * kMaxN + 16;
+static __device__ __align__(256) double g_eigen_scratch[kNoallocDoubles];
+static double* g_eigen_scratch_ptr[kNoallocMaxDevices] = {};
+static std::mutex g_eigen_scratch_mu;
+
+static_assert(sizeof(EigenJob) <= 8 * sizeof(double), "job slot too small");
+
+}  // namespace
 }  // namespace fdi
+
+extern "C" fdi_status fdi_eigen_noalloc(const double* faces, int n, int face_kind, fdi_bc bc_lo, fdi_bc bc_hi,
+                                        double* lam, double* E, double* Einv, int* converged,
+                                        fdi_stream_t stream) {
+  using namespace fdi;
+  if (!faces || !lam || !E || !Einv) return FDI_ERR_INVALID_ARG;
+  if (face_kind != 0 && face_kind != 1) return FDI_ERR_INVALID_ARG;
+  if ((unsigned)bc_lo > 1u || (unsigned)bc_hi > 1u) return FDI_ERR_INVALID_ARG;
+  if (n < (face_kind ? 3 : 2) || n > kMaxN) {
+    set_error("fdi_eigen_noalloc: n must lie in [2, 256] (cell) or [3, 256] (face); its scratch holds 256 unknowns");
+    return FDI_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < n; ++i)
+    if (!(faces[i + 1] > faces[i]) || !std::isfinite(faces[i]) || !std::isfinite(faces[i + 1])) {
+      set_error("fdi_eigen_noalloc: faces must be finite and strictly ascending");
+      return FDI_ERR_INVALID_ARG;
+    }
+  // 1D finite-volume operator on the stack (no heap allocation)
+  double m[kMaxN], kd[kMaxN], ko[kMaxN];
+  int u = n;
+  bool zero_flux = false;
+  if (face_kind == 0) {
+    for (int i = 0; i < n; ++i) {
+      m[i] = faces[i + 1] - faces[i];
+      kd[i] = 0.0;
+      ko[i] = 0.0;
+    }
+    for (int i = 0; i + 1 < n; ++i) {
+      const double g = 1.0 / (0.5 * (faces[i + 1] + faces[i + 2]) - 0.5 * (faces[i] + faces[i + 1]));
+      ko[i] = g;
+      kd[i] -= g;
+      kd[i + 1] -= g;
+    }
+    if (bc_lo == FDI_BC_DIRICHLET) kd[0] -= 2.0 / m[0];
+    if (bc_hi == FDI_BC_DIRICHLET) kd[n - 1] -= 2.0 / m[n - 1];
+    zero_flux = bc_lo == FDI_BC_NEUMANN && bc_hi == FDI_BC_NEUMANN;
+  } else {
+    u = n - 1;
+    for (int j = 1; j < n; ++j) {
+      m[j - 1] = 0.5 * (faces[j] + faces[j + 1]) - 0.5 * (faces[j - 1] + faces[j]);
+      kd[j - 1] = 0.0;
+      ko[j - 1] = 0.0;
+    }
+    for (int i = 0; i < n; ++i) {
+      const double g = 1.0 / (faces[i + 1] - faces[i]);
+      const int a = i - 1, b = i;
+      if (a >= 0 && a < u) kd[a] -= g;
+      if (b >= 0 && b < u) kd[b] -= g;
+      if (a >= 0 && b < u) ko[a] = g;
+    }
+  }
+  // per-device set-up: the device address of the scratch array
+  int dev = 0;
+  FDI_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoallocMaxDevices) return FDI_ERR_UNSUPPORTED;
+  double* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_eigen_scratch_mu);
+    if (!g_eigen_scratch_ptr[dev]) {
+      void* ptr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&ptr, g_eigen_scratch);
+      if (e != cudaSuccess || !ptr) {
+        set_error(std::string("fdi_eigen_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        return FDI_ERR_CUDA;
+      }
+      g_eigen_scratch_ptr[dev] = static_cast<double*>(ptr);
+    }
+    base = g_eigen_scratch_ptr[dev];
+  }
+  double* d_m = base;
+  double* d_kd = base + kMaxN;
+  double* d_ko = base + 2 * kMaxN;
+  EigenJob* d_job = reinterpret_cast<EigenJob*>(base + 3 * kMaxN);
+  int* d_flag = reinterpret_cast<int*>(base + 3 * kMaxN + 8);
+  const EigenJob job{u, zero_flux ? 1 : 0, d_m, d_kd, d_ko, lam, E, Einv};
+  cudaStream_t s = (cudaStream_t)stream;
+  // pageable-source copies return once the source has been staged, so the
+  // stack arrays may go out of scope afterwards
+  FDI_CUDA_TRY(cudaMemcpyAsync(d_m, m, u * sizeof(double), cudaMemcpyHostToDevice, s));
+  FDI_CUDA_TRY(cudaMemcpyAsync(d_kd, kd, u * sizeof(double), cudaMemcpyHostToDevice, s));
+  FDI_CUDA_TRY(cudaMemcpyAsync(d_ko, ko, u * sizeof(double), cudaMemcpyHostToDevice, s));
+  FDI_CUDA_TRY(cudaMemcpyAsync(d_job, &job, sizeof(EigenJob), cudaMemcpyHostToDevice, s));
+  FDI_CUDA_TRY(cudaMemsetAsync(d_flag, 0, sizeof(int), s));  // the flag keeps the last call's value
+  k_eigen<<<1, kEigThreads, 0, s>>>(d_job, d_flag);
+  FDI_CUDA_TRY(cudaGetLastError());
+  if (converged) {
+    int flag = 0;
+    FDI_CUDA_TRY(cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FDI_CUDA_TRY(cudaStreamSynchronize(s));
+    *converged = flag == 0 ? 1 : 0;
+  }
+  return FDI_OK;
+}
