@@ -227,6 +227,36 @@ def run_arm(fdi, torch, prec, n, K, W, dev, rank, stream, cluster=None):
             "e2e_s": e2e_s, "h2d": f.nbytes, "d2h": f.nbytes, "clocks": clk.summary()}
 
 
+def run_stokes(fdi, torch, prec, n, reps, warm, stream):
+    """Stokes-inverse latency on the staggered n^3 no-slip box (tanh 1.5, Re 1000,
+    dt in {1e-2, 1e3}, Gaussian forcing seeds 0-2): p50 / p99 of the wall time of
+    complete solves (each call ends with the stream synchronised)."""
+    faces = workloads.box_faces((n, n, n), BETA)
+    plan = fdi.plan_create(faces, (n, n, n), grid=fdi.GRID_MAC, prec=prec)
+    shapes = workloads.mac_shapes((n, n, n))
+    f = [torch.from_numpy(workloads.rhs_gaussian(shapes[c], i)).cuda() for i, c in enumerate("uvw")]
+    u = [torch.empty_like(t) for t in f]
+    p = torch.empty(shapes["p"], dtype=torch.float64, device="cuda")
+    out = {}
+    for dt in (1e-2, 1e3):
+        for _ in range(warm):
+            fdi.stokes_solve(plan, dt, 1000.0, f, u, p, stream)
+        stream.synchronize()
+        lat = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fdi.stokes_solve(plan, dt, 1000.0, f, u, p, stream)
+            stream.synchronize()
+            lat.append(1e3 * (time.perf_counter() - t0))
+        it, _, rel, st = fdi.last_result(plan)
+        lat.sort()
+        out[f"dt={dt:g}"] = {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                             "krylov_iters": it, "rel_residual": rel, "status": st, "reps": reps,
+                             "launches_per_solve": fdi.last_launch_count(plan)}
+    plan.destroy()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -237,6 +267,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--arms", default="fp64,mixed")
     ap.add_argument("--cluster", type=int, default=None, help="tensor-core transform cluster size (1, 2, 4)")
+    ap.add_argument("--stokes-n", type=int, default=64, help="Stokes latency grid (0: skip)")
+    ap.add_argument("--stokes-reps", type=int, default=10)
     args = ap.parse_args()
     n = (args.n, args.n, args.n)
     P = n[0] * n[1] * n[2]
@@ -333,6 +365,15 @@ def main():
         per_kernel[name] = e
     if per_kernel:
         roof = dict(max(per_kernel.values(), key=lambda e: e["total_ms"]))
+    stokes = None
+    if args.stokes_n > 0:
+        stokes = {}
+        for name in args.arms.split(","):
+            prec = precs[name][0]
+            try:
+                stokes[name] = run_stokes(fdi, torch, prec, args.stokes_n, args.stokes_reps, 2, stream)
+            except fdi.FdiError as e:
+                stokes[name] = {"error": str(e)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t = oracle_tpt_time(n)
@@ -351,6 +392,8 @@ def main():
         "roofline": roof,
         "cpu_baseline": cpu,
         "clocks": best["clocks"],
+        "stokes_latency": ({"config": f"MAC {args.stokes_n}^3, tanh {BETA}, no-slip, Re 1000, Gaussian forcing",
+                            **stokes} if stokes is not None else None),
         "kernels": {k: {kk: round(vv, 4) if isinstance(vv, float) else vv for kk, vv in e.items()
                         if kk in ("achieved", "unit", "frac", "avg_launch_ms", "launches", "tensor_frac")}
                     for k, e in per_kernel.items()},

@@ -133,6 +133,13 @@ fdi_status fdi_field_solve(fdi_plan* plan, fdi_field field, double sigma, double
 fdi_status fdi_stokes_solve(fdi_plan* plan, double dt, double Re, const double* const f[3],
                             double* const u[3], double* p, fdi_stream_t stream);
 
+/* Preconditioner of the pressure-matrix Krylov solve: mode 0 is the paper's
+ * inverse pressure Laplacian L_p^{-1} (Sec. 2, after Eq. 9); mode 1 (default)
+ * adds the viscous term, L_p^{-1} - lambda*I (Cahouet & Chabard 1988), which is
+ * the exact inverse of C when the discrete operators commute and reduces to
+ * mode 0 as dt -> 0; with mode 0 the iteration stagnates at large dt/Re. */
+fdi_status fdi_plan_set_stokes_preconditioner(fdi_plan* plan, int mode);
+
 /* count independent Helmholtz solves (plans[i] may repeat only if the solves
  * are meant to run one after another on that plan's workspace). */
 fdi_status fdi_helmholtz_solve_batched(fdi_plan* const* plans, const double* lambdas,

@@ -199,9 +199,12 @@ def bicgstab(apply_A, apply_Minv, b, tol, maxiter):
     return x, it, rel
 
 
-def stokes_semi_direct(faces, dt, Re, f, tol=1e-11, maxiter=200, method="tpt"):
+def stokes_semi_direct(faces, dt, Re, f, tol=1e-11, maxiter=200, method="tpt", precond="laplace"):
     """Three-step semi-direct Stokes inverse (Sec. 2): direct Helmholtz inverses by
-    the decomposition solvers, BiCGstab on C preconditioned by L_p^{-1}.
+    the decomposition solvers, BiCGstab on C preconditioned by L_p^{-1}
+    (precond="laplace", the paper's choice) or by L_p^{-1} - lam*I
+    (precond="cahouet-chabard": Cahouet & Chabard 1988, the exact inverse of
+    C = L_p (I - lam L_p)^{-1} when the discrete operators commute).
 
     Returns ((u, v, w), p, iterations, relative C-residual)."""
     lam = dt / Re
@@ -215,7 +218,10 @@ def stokes_semi_direct(faces, dt, Re, f, tol=1e-11, maxiter=200, method="tpt"):
 
     def Lp_inv(g):
         # L_p = D G is the zero-flux Laplacian; -L_p^{-1} is the Laplace solve
-        return -dec.solve(np.reshape(g, ps), pops, 1.0, 0.0, method).ravel()
+        out = -dec.solve(np.reshape(g, ps), pops, 1.0, 0.0, method).ravel()
+        if precond == "cahouet-chabard":
+            out = out - lam * np.ravel(g)
+        return out
 
     def C(q):
         return sum(D[c] @ Hinv(c, G[c] @ q) for c in range(3))

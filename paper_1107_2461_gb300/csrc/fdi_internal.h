@@ -21,8 +21,11 @@ struct DevStatus {
   double rel_res;    // relative residual of the last check
   double bnorm2;     // ||b||^2 of the current solve
   double mean_b;     // volume-weighted mean of b (singular problems)
-  double scal[16];   // Krylov scalars (rho, alpha, omega, ...)
+  double tol_used;   // tolerance the last solve was run to
+  double scal[16];   // scratch scalars (volume-weighted mean of the solution, ...)
 };
+
+struct KryState;     // Krylov scalars of the Stokes pressure solve (stokes.cu)
 
 // One 1D operator D = M^{-1} K along a direction (Eq. 23-24), resident on device.
 struct Axis {
@@ -77,8 +80,14 @@ struct fdi_plan {
   int npartials = 0;
   fdi::DevStatus* d_status = nullptr;
   int* h_flag = nullptr;            // pinned host flag for Krylov convergence
-  // Stokes workspace (MAC plans)
+  // Stokes workspace (MAC plans): 10 cell vectors, 6 face fields, geometry
   double* sk[12] = {nullptr};
+  double* skf[6] = {nullptr};
+  double* mac_ih[3] = {nullptr, nullptr, nullptr};
+  double* mac_idc[3] = {nullptr, nullptr, nullptr};
+  fdi::KryState* d_kry = nullptr;
+  int stokes_precond = 1;           // 0: L_p^{-1} (paper), 1: L_p^{-1} - lambda I
+  double* kpartials = nullptr;
   // controls
   double tol = 1e-11;
   int max_refine = 2;
@@ -160,6 +169,11 @@ fdi_status validate_field_args(const fdi_plan* p, int field, double sigma, doubl
 // mixed path (mixed.cu)
 fdi_status mixed_setup(fdi_plan* p);
 void mixed_free_axis(Axis* ax);
+
+// Stokes (stokes.cu)
+fdi_status stokes_setup(fdi_plan* p);
+fdi_status stokes_solve(fdi_plan* p, double dt, double Re, const double* const f[3], double* const u[3], double* pr,
+                        cudaStream_t s);
 fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda, const double* rhs,
                              double* out, cudaStream_t s);
 

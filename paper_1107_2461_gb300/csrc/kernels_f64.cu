@@ -359,7 +359,8 @@ __global__ void k_vmean_finish(const double* __restrict__ partials, int nblocks,
   if (threadIdx.x == 0) st->mean_b = a / b;
 }
 
-__global__ void k_reset_status(DevStatus* st) {
+__global__ void k_reset_status(DevStatus* st, double tol) {
+  st->tol_used = tol;
   st->done = 0;
   st->refine_steps = 0;
   st->iters = 0;
@@ -469,7 +470,7 @@ fdi_status launch_mean_f64(fdi_plan* p, const Field& f, const double* b, cudaStr
 }
 
 fdi_status launch_reset_status(fdi_plan* p, cudaStream_t s) {
-  k_reset_status<<<1, 1, 0, s>>>(p->d_status);
+  k_reset_status<<<1, 1, 0, s>>>(p->d_status, p->tol);
   FDI_LAUNCH_CHECK(p);
   return FDI_OK;
 }

@@ -477,7 +477,6 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
   const MixedAxis* mx = static_cast<const MixedAxis*>(f.ax[0]->mixed);
   const MixedAxis* my = static_cast<const MixedAxis*>(f.ax[1]->mixed);
   const MixedAxis* mz = static_cast<const MixedAxis*>(f.ax[2]->mixed);
-  p->launches = 0;
   FDI_TRY(launch_reset_status(p, s));
   FDI_CUDA_TRY(cudaMemsetAsync(p->d_scales, 0, (size_t)(kMaxRefineCap + 2) * 4 * sizeof(float), s));
   const double* b = rhs;

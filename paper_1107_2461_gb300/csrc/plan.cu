@@ -168,6 +168,14 @@ void free_plan(fdi_plan* p) {
     if (w) cudaFree(w);
   for (double* w : p->sk)
     if (w) cudaFree(w);
+  for (double* w : p->skf)
+    if (w) cudaFree(w);
+  for (int d = 0; d < 3; ++d) {
+    if (p->mac_ih[d]) cudaFree(p->mac_ih[d]);
+    if (p->mac_idc[d]) cudaFree(p->mac_idc[d]);
+  }
+  if (p->d_kry) cudaFree(p->d_kry);
+  if (p->kpartials) cudaFree(p->kpartials);
   if (p->xdf) cudaFree(p->xdf);
   if (p->d_scales) cudaFree(p->d_scales);
   if (p->d_err) cudaFree(p->d_err);
@@ -259,6 +267,7 @@ fdi_status build_plan(fdi_plan* p, const double* const faces[3], const fdi_bc bc
   FDI_CUDA_TRY(cudaMemset(p->d_status, 0, sizeof(DevStatus)));
   FDI_CUDA_TRY(cudaMallocHost((void**)&p->h_flag, sizeof(int) * 4));
   if (p->prec != FDI_PREC_FP64) FDI_TRY(mixed_setup(p));
+  if (p->grid == FDI_GRID_MAC) FDI_TRY(stokes_setup(p));
   return FDI_OK;
 }
 
@@ -329,9 +338,11 @@ fdi_status fdi_plan_create(const double* const faces[3], const int n[3], const f
   if (prec == FDI_PREC_FP64) {
     p->tol = 1e-11;
     p->max_refine = 2;
+    p->ktol = 1e-11;
   } else {
     p->tol = 1e-10;
     p->max_refine = 3;
+    p->ktol = 1e-10;
   }
   cudaStream_t s;
   if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
@@ -398,7 +409,7 @@ fdi_status fdi_last_result(const fdi_plan* plan, int* iters, int* refine_steps, 
     }
   }
   if (st.error) return FDI_ERR_NOT_CONVERGED;
-  if (!(st.rel_res <= plan->tol)) {
+  if (!(st.rel_res <= (st.tol_used > 0.0 ? st.tol_used : plan->tol))) {
     set_error("residual above the tolerance after the last refinement step");
     return FDI_ERR_NOT_CONVERGED;
   }

@@ -80,7 +80,6 @@ fdi_status field_solve(fdi_plan* p, int field, double sigma, double lambda, cons
   if (!rhs || !out) return FDI_ERR_INVALID_ARG;
   if (p->prec != FDI_PREC_FP64) return mixed_field_solve(p, field, sigma, lambda, rhs, out, s);
   const Field& f = p->fields[field];
-  p->launches = 0;
   FDI_TRY(launch_reset_status(p, s));
   const double* b = rhs;
   if (out == rhs) {
@@ -110,15 +109,18 @@ extern "C" {
 
 fdi_status fdi_field_solve(fdi_plan* plan, fdi_field field, double sigma, double lambda, const double* rhs,
                            double* out, fdi_stream_t stream) {
+  if (plan) plan->launches = 0;
   return field_solve(plan, (int)field, sigma, lambda, rhs, out, (cudaStream_t)stream);
 }
 
 fdi_status fdi_helmholtz_solve(fdi_plan* plan, double lambda, const double* rhs, double* out,
                                fdi_stream_t stream) {
+  if (plan) plan->launches = 0;
   return field_solve(plan, FDI_FIELD_CELL, 1.0, lambda, rhs, out, (cudaStream_t)stream);
 }
 
 fdi_status fdi_laplace_solve(fdi_plan* plan, const double* rhs, double* out, fdi_stream_t stream) {
+  if (plan) plan->launches = 0;
   return field_solve(plan, FDI_FIELD_CELL, 0.0, 1.0, rhs, out, (cudaStream_t)stream);
 }
 
@@ -130,6 +132,7 @@ fdi_status fdi_helmholtz_solve_batched(fdi_plan* const* plans, const double* lam
     if (st != FDI_OK) return st;
     if (!rhs[i] || !out[i]) return FDI_ERR_INVALID_ARG;
   }
+  for (int i = 0; i < count; ++i) plans[i]->launches = 0;
   for (int i = 0; i < count; ++i) {
     fdi_status st = field_solve(plans[i], FDI_FIELD_CELL, 1.0, lambdas[i], rhs[i], out[i], (cudaStream_t)stream);
     if (st != FDI_OK) return st;

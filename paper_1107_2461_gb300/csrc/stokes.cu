@@ -1,8 +1,486 @@
-// Semi-direct Stokes inverse (Sec. 2).
+// Semi-direct inverse of the staggered Stokes operator (Sec. 2).
+//
+// System (Eq. 8 scaled by -dt, viscosity 1/Re, lambda = dt/Re):
+//     (I - lambda Delta_c) u_c + dt (G p)_c = f_c   (c = u, v, w),     D u = 0.
+// Three steps (Sec. 2, after Eq. 9), with q = dt * p:
+//   1. u_hat_c = H_c^{-1} f_c                                   (3 direct solves)
+//   2. C q = D u_hat,  C = sum_c D_c H_c^{-1} G_c (Eq. 9), by BiCGstab preconditioned
+//      with the inverse pressure Laplacian L_p^{-1}, L_p = D G (zero-flux, solved by
+//      the same direct method); every C-product costs three direct Helmholtz solves
+//   3. u_c = u_hat_c - H_c^{-1} (G q)_c                          (3 direct solves)
+// Preconditioner: the paper's inverse pressure Laplacian L_p^{-1} (mode 0), or,
+// by default (mode 1), L_p^{-1} - lambda I (Cahouet & Chabard, Int. J. Numer.
+// Meth. Fluids 8, 1988): with H = I - lambda Delta and commuting discrete
+// operators C = L_p (I - lambda L_p)^{-1}, whose inverse is exactly
+// L_p^{-1} - lambda I; it reduces to the paper's choice as dt -> 0 and keeps
+// the iteration count bounded at large dt, where L_p^{-1} alone stagnates.
+// The Krylov scalars, dot products and vector updates stay on the device in
+// FP64 (deterministic two-stage reductions); the host reads one convergence
+// flag per iteration.  The pressure is returned with zero volume-weighted mean.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
 #include "fdi_internal.h"
+
+namespace fdi {
+
+struct KryState {
+  double rho, rho_old, alpha, omega;
+  double bnorm2, rnorm2, rel;
+  double tol;
+  int iters, maxit, done, error;
+};
+
+namespace {
+
+constexpr int kDotBlocks = 152 * 4;
+constexpr int kDotThreads = 256;
+
+struct MacGeom {
+  int nx, ny, nz;
+  const double* ih[3];   // 1 / h_i (cell widths), n_d each
+  const double* idc[3];  // 1 / (c_j - c_{j-1}), interior faces, n_d - 1 each
+  const double* m[3];    // cell widths (volumes = products)
+};
+
+// g_c = scale * (G q)_c on the interior faces (Eq. 31's D_p)
+__global__ void k_grad(MacGeom g, const double* __restrict__ q, double scale, double* __restrict__ gu,
+                       double* __restrict__ gv, double* __restrict__ gw) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  if (i >= nx || j >= ny) return;
+  const long long c = ((long long)k * ny + j) * nx + i;
+  const double qc = q[c];
+  if (i + 1 < nx) gu[((long long)k * ny + j) * (nx - 1) + i] = scale * ((q[c + 1] - qc) * g.idc[0][i]);
+  if (j + 1 < ny) gv[((long long)k * (ny - 1) + j) * nx + i] = scale * ((q[c + nx] - qc) * g.idc[1][j]);
+  if (k + 1 < nz) gw[((long long)k * ny + j) * nx + i] = scale * ((q[c + (long long)nx * ny] - qc) * g.idc[2][k]);
+}
+
+// y = D h at the cells (Eq. 30's D_u), wall velocities zero
+__global__ void k_div(MacGeom g, const double* __restrict__ hu, const double* __restrict__ hv,
+                      const double* __restrict__ hw, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  if (i >= nx || j >= ny) return;
+  const long long ru = ((long long)k * ny + j) * (nx - 1);
+  const double ur = (i + 1 < nx) ? hu[ru + i] : 0.0, ul = (i > 0) ? hu[ru + i - 1] : 0.0;
+  const long long rv = (long long)k * (ny - 1) * nx;
+  const double vr = (j + 1 < ny) ? hv[rv + (long long)j * nx + i] : 0.0;
+  const double vl = (j > 0) ? hv[rv + (long long)(j - 1) * nx + i] : 0.0;
+  const long long pw = (long long)ny * nx;
+  const double wr = (k + 1 < nz) ? hw[(long long)k * pw + (long long)j * nx + i] : 0.0;
+  const double wl = (k > 0) ? hw[(long long)(k - 1) * pw + (long long)j * nx + i] : 0.0;
+  y[((long long)k * ny + j) * nx + i] = (ur - ul) * g.ih[0][i] + (vr - vl) * g.ih[1][j] + (wr - wl) * g.ih[2][k];
+}
+
+__device__ __forceinline__ void block_reduce2(double& a, double& b) {
+  __shared__ double sh[2 * (kDotThreads / 32)];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int w = threadIdx.x / 32, ln = threadIdx.x % 32;
+  if (ln == 0) {
+    sh[2 * w] = a;
+    sh[2 * w + 1] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0, sb = 0;
+    for (int q = 0; q < kDotThreads / 32; ++q) {
+      sa += sh[2 * q];
+      sb += sh[2 * q + 1];
+    }
+    a = sa;
+    b = sb;
+  }
+}
+
+// partial sums of a.b and c.d (c, d may be null) over n values
+__global__ void __launch_bounds__(kDotThreads) k_dot2(const double* __restrict__ a, const double* __restrict__ b,
+                                                      const double* __restrict__ c, const double* __restrict__ d,
+                                                      long long n, double* __restrict__ partials) {
+  double s0 = 0.0, s1 = 0.0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    s0 = fma(a[q], b[q], s0);
+    if (c) s1 = fma(c[q], d[q], s1);
+  }
+  block_reduce2(s0, s1);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = s0;
+    partials[2 * blockIdx.x + 1] = s1;
+  }
+}
+
+__device__ __forceinline__ void sum_partials(const double* partials, double& a, double& b) {
+  a = 0.0;
+  b = 0.0;
+  for (int q = threadIdx.x; q < kDotBlocks; q += blockDim.x) {
+    a += partials[2 * q];
+    b += partials[2 * q + 1];
+  }
+  block_reduce2(a, b);
+}
+
+// kinds of scalar updates after a reduction
+enum { KF_INIT = 0, KF_ALPHA = 1, KF_OMEGA = 2, KF_ITER = 3, KF_MEAN = 4 };
+
+__global__ void __launch_bounds__(kDotThreads) k_kry_finish(const double* __restrict__ partials, KryState* st,
+                                                            int kind) {
+  double a, b;
+  sum_partials(partials, a, b);
+  if (threadIdx.x != 0) return;
+  if (st->done && kind != KF_INIT && kind != KF_MEAN) return;
+  switch (kind) {
+    case KF_INIT:  // a = ||b||^2 (= rhat.r)
+      st->bnorm2 = a;
+      st->rnorm2 = a;
+      st->rho = a;
+      st->rho_old = 1.0;
+      st->alpha = 1.0;
+      st->omega = 1.0;
+      st->iters = 0;
+      st->rel = a > 0.0 ? 1.0 : 0.0;
+      st->done = a > 0.0 ? 0 : 1;
+      st->error = 0;
+      break;
+    case KF_ALPHA:  // a = rhat.v
+      if (a == 0.0 || !isfinite(a)) {
+        st->error = 2;
+        st->done = 1;
+      } else {
+        st->alpha = st->rho / a;
+      }
+      break;
+    case KF_OMEGA:  // a = t.s, b = t.t
+      if (b == 0.0 || !isfinite(b)) {
+        st->omega = 0.0;
+        st->error = st->error ? st->error : 3;
+        st->done = 1;
+      } else {
+        st->omega = a / b;
+      }
+      break;
+    case KF_ITER: {  // a = r.r, b = rhat.r
+      st->iters += 1;
+      st->rnorm2 = a;
+      st->rho_old = st->rho;
+      st->rho = b;
+      const double rel = sqrt(a / st->bnorm2);
+      st->rel = rel;
+      if (!isfinite(rel)) {
+        st->error = 4;
+        st->done = 1;
+      } else if (rel <= st->tol) {
+        st->done = 1;
+      } else if (st->iters >= st->maxit) {
+        st->done = 1;
+        st->error = 5;
+      } else if (b == 0.0 || st->omega == 0.0) {
+        st->done = 1;
+        st->error = 6;
+      }
+      break;
+    }
+    case KF_MEAN:  // a = sum V x, b = sum V: store the mean in rho_old slot of a scratch state
+      st->rnorm2 = a / b;
+      break;
+  }
+}
+
+// p = r + beta (p - omega v),  beta = (rho / rho_old)(alpha / omega)
+__global__ void k_bicg_p(const KryState* __restrict__ st, double* __restrict__ p, const double* __restrict__ r,
+                         const double* __restrict__ v, long long n, int first) {
+  if (st->done) return;
+  const double beta = first ? 0.0 : (st->rho / st->rho_old) * (st->alpha / st->omega);
+  const double om = st->omega;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    p[q] = first ? r[q] : r[q] + beta * (p[q] - om * v[q]);
+}
+
+// s = r - alpha v
+__global__ void k_bicg_s(const KryState* __restrict__ st, double* __restrict__ s, const double* __restrict__ r,
+                         const double* __restrict__ v, long long n) {
+  if (st->done) return;
+  const double al = st->alpha;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    s[q] = r[q] - al * v[q];
+}
+
+// x <- x + alpha phat + omega shat with phat = -y, shat = -z (the Laplace solves
+// return -L_p^{-1}); r = s - omega t; partial sums of r.r and rhat.r
+__global__ void __launch_bounds__(kDotThreads) k_bicg_xr(const KryState* __restrict__ st, double* __restrict__ x,
+                                                         const double* __restrict__ y, const double* __restrict__ z,
+                                                         double* __restrict__ r, const double* __restrict__ s,
+                                                         const double* __restrict__ t,
+                                                         const double* __restrict__ rhat, long long n,
+                                                         double* __restrict__ partials) {
+  const bool live = !st->done;
+  const double al = st->alpha, om = st->omega;
+  double s0 = 0.0, s1 = 0.0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    if (live) {
+      x[q] = x[q] - al * y[q] - om * z[q];
+      const double rq = s[q] - om * t[q];
+      r[q] = rq;
+      s0 = fma(rq, rq, s0);
+      s1 = fma(rhat[q], rq, s1);
+    }
+  }
+  block_reduce2(s0, s1);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = s0;
+    partials[2 * blockIdx.x + 1] = s1;
+  }
+}
+
+// partial sums of V x and V over the cells
+__global__ void __launch_bounds__(kDotThreads) k_vsum(MacGeom g, const double* __restrict__ x,
+                                                      double* __restrict__ partials) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  double s0 = 0.0, s1 = 0.0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % g.nx);
+    const long long t = q / g.nx;
+    const int j = (int)(t % g.ny), k = (int)(t / g.ny);
+    const double v = g.m[0][i] * g.m[1][j] * g.m[2][k];
+    s0 = fma(v, x[q], s0);
+    s1 += v;
+  }
+  block_reduce2(s0, s1);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = s0;
+    partials[2 * blockIdx.x + 1] = s1;
+  }
+}
+
+// p = (x - mean) / dt
+__global__ void k_pressure(const KryState* __restrict__ mst, const double* __restrict__ x, double inv_dt,
+                           double* __restrict__ p, long long n) {
+  const double mu = mst->rnorm2;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    p[q] = (x[q] - mu) * inv_dt;
+}
+
+__global__ void k_sub(double* __restrict__ u, const double* __restrict__ h, long long n) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    u[q] -= h[q];
+}
+
+// y <- y + c x  (adds the viscous part of the pressure preconditioner)
+__global__ void k_axpy(double* __restrict__ y, double c, const double* __restrict__ x, long long n) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    y[q] = fma(c, x[q], y[q]);
+}
+
+__global__ void k_zero(double* __restrict__ a, long long n) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    a[q] = 0.0;
+}
+
+__global__ void k_stokes_report(const KryState* __restrict__ st, DevStatus* ds) {
+  ds->iters = st->iters;
+  ds->refine_steps = 0;
+  ds->rel_res = st->rel;
+  ds->error = st->error ? 1 : 0;
+  ds->done = 1;
+  ds->tol_used = st->tol;
+}
+
+__global__ void k_kry_setup(KryState* st, double tol, int maxit) {
+  st->tol = tol;
+  st->maxit = maxit;
+  st->done = 0;
+  st->error = 0;
+  st->iters = 0;
+}
+
+#define FDI_TRY(expr)            \
+  do {                           \
+    fdi_status _s = (expr);      \
+    if (_s != FDI_OK) return _s; \
+  } while (0)
+
+template <typename T>
+fdi_status dalloc(T** p, size_t n) {
+  cudaError_t e = cudaMalloc((void**)p, (n ? n : 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? FDI_ERR_OUT_OF_MEMORY : FDI_ERR_CUDA;
+  }
+  return FDI_OK;
+}
+
+MacGeom geom(const fdi_plan* p) {
+  MacGeom g;
+  g.nx = p->n[0];
+  g.ny = p->n[1];
+  g.nz = p->n[2];
+  for (int d = 0; d < 3; ++d) {
+    g.ih[d] = p->mac_ih[d];
+    g.idc[d] = p->mac_idc[d];
+    g.m[d] = p->fields[FDI_FIELD_CELL].ax[d]->m;
+  }
+  return g;
+}
+
+}  // namespace
+
+fdi_status stokes_setup(fdi_plan* p) {
+  // geometry of the staggered derivatives, from the cell-Neumann operators' widths
+  for (int d = 0; d < 3; ++d) {
+    const std::vector<double>& h = p->fields[FDI_FIELD_CELL].ax[d]->h_m;
+    const int n = (int)h.size();
+    std::vector<double> ih(n), idc(std::max(1, n - 1));
+    for (int i = 0; i < n; ++i) ih[i] = 1.0 / h[i];
+    for (int j = 1; j < n; ++j) idc[j - 1] = 1.0 / (0.5 * (h[j - 1] + h[j]));
+    FDI_TRY(dalloc(&p->mac_ih[d], n));
+    FDI_TRY(dalloc(&p->mac_idc[d], idc.size()));
+    FDI_CUDA_TRY(cudaMemcpy(p->mac_ih[d], ih.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    FDI_CUDA_TRY(cudaMemcpy(p->mac_idc[d], idc.data(), idc.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  const long long Pc = p->fields[FDI_FIELD_CELL].P;
+  long long Pf = 0;
+  for (int c = 1; c <= 3; ++c) Pf = std::max(Pf, p->fields[c].P);
+  for (int i = 0; i < 10; ++i) FDI_TRY(dalloc(&p->sk[i], Pc));   // b x r rhat p v s t y z
+  for (int i = 0; i < 6; ++i) FDI_TRY(dalloc(&p->skf[i], Pf));  // g_u g_v g_w h_u h_v h_w
+  FDI_TRY(dalloc(&p->d_kry, 2));
+  FDI_TRY(dalloc(&p->kpartials, 2 * kDotBlocks));
+  return FDI_OK;
+}
+
+namespace {
+
+fdi_status cmatvec(fdi_plan* p, const MacGeom& g, double lambda, double* q, double* out, cudaStream_t s) {
+  // out = C (-q) = -sum_c D_c H_c^{-1} G_c q   (q holds -phat, see k_bicg_xr)
+  dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+  {
+    FDI_KTIMER(p, "stokes_grad", s);
+    k_grad<<<grd, blk, 0, s>>>(g, q, -1.0, p->skf[0], p->skf[1], p->skf[2]);
+    FDI_LAUNCH_CHECK(p);
+  }
+  for (int c = 0; c < 3; ++c) FDI_TRY(field_solve(p, 1 + c, 1.0, lambda, p->skf[c], p->skf[3 + c], s));
+  FDI_KTIMER(p, "stokes_div", s);
+  k_div<<<grd, blk, 0, s>>>(g, p->skf[3], p->skf[4], p->skf[5], out);
+  FDI_LAUNCH_CHECK(p);
+  return FDI_OK;
+}
+
+fdi_status dots(fdi_plan* p, const double* a, const double* b, const double* c, const double* d, long long n,
+                int kind, cudaStream_t s) {
+  FDI_KTIMER(p, "stokes_dot", s);
+  k_dot2<<<kDotBlocks, kDotThreads, 0, s>>>(a, b, c, d, n, p->kpartials);
+  FDI_LAUNCH_CHECK(p);
+  k_kry_finish<<<1, kDotThreads, 0, s>>>(p->kpartials, p->d_kry, kind);
+  FDI_LAUNCH_CHECK(p);
+  return FDI_OK;
+}
+
+}  // namespace
+
+fdi_status stokes_solve(fdi_plan* p, double dt, double Re, const double* const f[3], double* const u[3], double* pr,
+                        cudaStream_t s) {
+  const double lambda = dt / Re;
+  const MacGeom g = geom(p);
+  const long long Pc = p->fields[FDI_FIELD_CELL].P;
+  double *b = p->sk[0], *x = p->sk[1], *r = p->sk[2], *rhat = p->sk[3], *pv = p->sk[4], *v = p->sk[5];
+  double *sv = p->sk[6], *t = p->sk[7], *y = p->sk[8], *z = p->sk[9];
+  const unsigned vb = 152 * 4, vt = 256;
+  const dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
+  // step 1: predictors u_hat_c = H_c^{-1} f_c, kept in the outputs
+  for (int c = 0; c < 3; ++c) FDI_TRY(field_solve(p, 1 + c, 1.0, lambda, f[c], u[c], s));
+  // b = D u_hat; r = rhat = b; x = p = v = 0
+  k_div<<<grd, blk, 0, s>>>(g, u[0], u[1], u[2], b);
+  FDI_LAUNCH_CHECK(p);
+  k_kry_setup<<<1, 1, 0, s>>>(p->d_kry, p->ktol, p->kmaxit);
+  FDI_LAUNCH_CHECK(p);
+  FDI_CUDA_TRY(cudaMemcpyAsync(r, b, Pc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  FDI_CUDA_TRY(cudaMemcpyAsync(rhat, b, Pc * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  k_zero<<<vb, vt, 0, s>>>(x, Pc);
+  FDI_LAUNCH_CHECK(p);
+  FDI_TRY(dots(p, b, b, nullptr, nullptr, Pc, KF_INIT, s));
+  // step 2: BiCGstab on C q = b, right-preconditioned by L_p^{-1}
+  for (int it = 0; it < p->kmaxit; ++it) {
+    k_bicg_p<<<vb, vt, 0, s>>>(p->d_kry, pv, r, v, Pc, it == 0 ? 1 : 0);
+    FDI_LAUNCH_CHECK(p);
+    // y = (-L_p)^{-1} p (+ lambda p) = -phat ; v = C phat
+    FDI_TRY(field_solve(p, FDI_FIELD_CELL, 0.0, 1.0, pv, y, s));
+    if (p->stokes_precond == 1) {
+      k_axpy<<<vb, vt, 0, s>>>(y, lambda, pv, Pc);
+      FDI_LAUNCH_CHECK(p);
+    }
+    FDI_TRY(cmatvec(p, g, lambda, y, v, s));
+    FDI_TRY(dots(p, rhat, v, nullptr, nullptr, Pc, KF_ALPHA, s));
+    k_bicg_s<<<vb, vt, 0, s>>>(p->d_kry, sv, r, v, Pc);
+    FDI_LAUNCH_CHECK(p);
+    FDI_TRY(field_solve(p, FDI_FIELD_CELL, 0.0, 1.0, sv, z, s));
+    if (p->stokes_precond == 1) {
+      k_axpy<<<vb, vt, 0, s>>>(z, lambda, sv, Pc);
+      FDI_LAUNCH_CHECK(p);
+    }
+    FDI_TRY(cmatvec(p, g, lambda, z, t, s));
+    FDI_TRY(dots(p, t, sv, t, t, Pc, KF_OMEGA, s));
+    {
+      FDI_KTIMER(p, "stokes_update", s);
+      k_bicg_xr<<<kDotBlocks, kDotThreads, 0, s>>>(p->d_kry, x, y, z, r, sv, t, rhat, Pc, p->kpartials);
+      FDI_LAUNCH_CHECK(p);
+      k_kry_finish<<<1, kDotThreads, 0, s>>>(p->kpartials, p->d_kry, KF_ITER);
+      FDI_LAUNCH_CHECK(p);
+    }
+    FDI_CUDA_TRY(cudaMemcpyAsync(p->h_flag, &p->d_kry->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FDI_CUDA_TRY(cudaStreamSynchronize(s));
+    if (*p->h_flag) break;
+  }
+  // zero-mean pressure q -> p = q / dt
+  {
+    k_vsum<<<kDotBlocks, kDotThreads, 0, s>>>(g, x, p->kpartials);
+    FDI_LAUNCH_CHECK(p);
+    k_kry_finish<<<1, kDotThreads, 0, s>>>(p->kpartials, p->d_kry + 1, KF_MEAN);
+    FDI_LAUNCH_CHECK(p);
+    k_pressure<<<vb, vt, 0, s>>>(p->d_kry + 1, x, 1.0 / dt, pr, Pc);
+    FDI_LAUNCH_CHECK(p);
+  }
+  // step 3: u_c = u_hat_c - H_c^{-1} (G q)_c   (x holds q; grad with +1)
+  k_grad<<<grd, blk, 0, s>>>(g, x, 1.0, p->skf[0], p->skf[1], p->skf[2]);
+  FDI_LAUNCH_CHECK(p);
+  for (int c = 0; c < 3; ++c) {
+    FDI_TRY(field_solve(p, 1 + c, 1.0, lambda, p->skf[c], p->skf[3 + c], s));
+    k_sub<<<vb, vt, 0, s>>>(u[c], p->skf[3 + c], p->fields[1 + c].P);
+    FDI_LAUNCH_CHECK(p);
+  }
+  k_stokes_report<<<1, 1, 0, s>>>(p->d_kry, p->d_status);
+  FDI_LAUNCH_CHECK(p);
+  return FDI_OK;
+}
+
+}  // namespace fdi
+
+using namespace fdi;
 
 extern "C" fdi_status fdi_stokes_solve(fdi_plan* plan, double dt, double Re, const double* const f[3],
                                        double* const u[3], double* p, fdi_stream_t stream) {
-  fdi::set_error("Stokes solve not built yet");
-  return FDI_ERR_UNSUPPORTED;
+  if (!plan || !f || !u || !p) return FDI_ERR_INVALID_ARG;
+  if (plan->grid != FDI_GRID_MAC) {
+    set_error("fdi_stokes_solve needs a FDI_GRID_MAC plan");
+    return FDI_ERR_INVALID_ARG;
+  }
+  if (!(dt > 0.0) || !(Re > 0.0) || !std::isfinite(dt) || !std::isfinite(Re)) {
+    set_error("dt and Re must be finite and positive");
+    return FDI_ERR_INVALID_ARG;
+  }
+  for (int c = 0; c < 3; ++c)
+    if (!f[c] || !u[c]) return FDI_ERR_INVALID_ARG;
+  plan->launches = 0;
+  return stokes_solve(plan, dt, Re, f, u, p, (cudaStream_t)stream);
+}
+
+extern "C" fdi_status fdi_plan_set_stokes_preconditioner(fdi_plan* plan, int mode) {
+  if (!plan || (mode != 0 && mode != 1)) return FDI_ERR_INVALID_ARG;
+  plan->stokes_precond = mode;
+  return FDI_OK;
 }

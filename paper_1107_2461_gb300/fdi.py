@@ -41,6 +41,7 @@ SIGNATURES = {
     "fdi_last_launch_count": (_i, [_vp, C.POINTER(C.c_longlong)]),
     "fdi_apply_transform": (_i, [_vp, _i, _i, _i, _vp, _vp, C.c_longlong, _vp]),
     "fdi_plan_set_transform_config": (_i, [_vp, _i]),
+    "fdi_plan_set_stokes_preconditioner": (_i, [_vp, _i]),
     "fdi_eigen_noalloc": (_i, [C.POINTER(_d), _i, _i, _i, _i, _vp, _vp, _vp, C.POINTER(_i), _vp]),
     "fdi_plan_enable_timing": (_i, [_vp, _i]),
     "fdi_plan_kernel_times": (_i, [_vp, _i, C.POINTER(C.c_char_p), C.POINTER(_d), C.POINTER(C.c_longlong),
@@ -230,6 +231,10 @@ def _fptr(x):
 def apply_transform(plan: Plan, field, d, inverse, inp, out, rows, stream=None):
     _check(load().fdi_apply_transform(plan.handle, int(field), int(d), 1 if inverse else 0, _fptr(inp), _fptr(out),
                                       int(rows), _stream(stream)), "fdi_apply_transform")
+
+
+def set_stokes_preconditioner(plan: Plan, mode: int):
+    _check(load().fdi_plan_set_stokes_preconditioner(plan.handle, int(mode)), "fdi_plan_set_stokes_preconditioner")
 
 
 def set_transform_config(plan: Plan, cluster: int):

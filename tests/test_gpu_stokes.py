@@ -1,0 +1,109 @@
+"""GPU parity of the semi-direct Stokes inverse (Sec. 2, Eq. 8-9 and the three
+steps after Eq. 9) against the FP64 CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+from oracle import assembled as asm
+from oracle import stokes as st
+from workloads import box_faces, rhs_gaussian, tanh_faces
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fdi():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1107_2461_gb300 import build
+    build.build()
+    import paper_1107_2461_gb300 as pkg
+    return pkg
+
+
+def gpu_stokes(fdi, faces, dt, Re, f, prec, precond=1):
+    import torch
+    n = tuple(len(fc) - 1 for fc in faces)
+    plan = fdi.plan_create(faces, n, grid=fdi.GRID_MAC, prec=prec)
+    fdi.set_stokes_preconditioner(plan, precond)
+    ft = [torch.from_numpy(np.ascontiguousarray(fc)).cuda() for fc in f]
+    ut = [torch.empty_like(t) for t in ft]
+    vs, ps = st.shapes(faces)
+    pt = torch.empty(ps, dtype=torch.float64, device="cuda")
+    fdi.stokes_solve(plan, dt, Re, ft, ut, pt)
+    torch.cuda.synchronize()
+    it, _, rel, status = fdi.last_result(plan)
+    plan.destroy()
+    return [t.cpu().numpy() for t in ut], pt.cpu().numpy(), it, rel, status
+
+
+def forcing(faces, seed):
+    vs, _ = st.shapes(faces)
+    return [rhs_gaussian(vs[c], seed + c) for c in range(3)]
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (3, 1e-10)])
+@pytest.mark.parametrize("dt", [1e-2, 1.0, 1e3])
+def test_small_stokes_matches_direct(fdi, prec, tol, dt):
+    faces = [tanh_faces(6, 1.5), tanh_faces(7, 1.5), tanh_faces(8, 2.0)]
+    f = forcing(faces, 0)
+    vel_d, p_d = st.stokes_direct(faces, dt, 1000.0, f)
+    vel, p, it, res, status = gpu_stokes(fdi, faces, dt, 1000.0, f, prec)
+    assert status == 0 and res <= tol and it >= 1, (it, res)
+    for c in range(3):
+        assert rel(vel[c], vel_d[c]) <= 1e-8
+    assert rel(p, p_d) <= 1e-7
+    mom, div = st.saddle_residual(faces, dt, 1000.0, f, vel, p)
+    # D u equals the pressure-system residual, so ||D u|| / ||u|| is the Krylov
+    # tolerance times ||D u_hat|| / ||u||
+    assert mom <= 1e-9 and div <= 100 * tol, (mom, div)
+
+
+def test_manufactured_pressure_only(fdi):
+    # f = dt * G p0 has the exact solution u = 0, p = p0 (zero-mean p0)
+    faces = [tanh_faces(9, 1.5), tanh_faces(6, 1.2), tanh_faces(7, 1.8)]
+    dt = 0.5
+    _, ps = st.shapes(faces)
+    vol = asm.volumes(st.pressure_ops(faces))
+    p0 = rhs_gaussian(ps, 11).ravel()
+    p0 -= np.dot(vol, p0) / vol.sum()
+    D, G = st.div_grad_3d(faces)
+    vs, _ = st.shapes(faces)
+    f = [(dt * (G[c] @ p0)).reshape(vs[c]) for c in range(3)]
+    vel, p, it, res, status = gpu_stokes(fdi, faces, dt, 100.0, f, 0)
+    assert status == 0
+    assert max(np.abs(v).max() for v in vel) <= 1e-9 * np.abs(p0).max()
+    assert np.abs(p.ravel() - p0).max() <= 1e-9 * np.abs(p0).max()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (3, 1e-10)])
+@pytest.mark.parametrize("dt", [1e-2, 1e3])
+def test_config3_stokes_64(fdi, prec, tol, dt):
+    # 64^3 staggered no-slip box, tanh 1.5, Re = 1000, Gaussian forcing seeds 0-2;
+    # checked with the oracle's assembled operators and its semi-direct solve
+    faces = box_faces((64, 64, 64), 1.5)
+    f = forcing(faces, 0)
+    vel, p, it, res, status = gpu_stokes(fdi, faces, dt, 1000.0, f, prec)
+    assert status == 0 and res <= tol, (it, res)
+    mom, div = st.saddle_residual(faces, dt, 1000.0, f, vel, p)
+    assert mom <= 1e-9 and div <= 1000 * tol, (mom, div)
+    vel_o, p_o, it_o, _ = st.stokes_semi_direct(faces, dt, 1000.0, f, tol=1e-12, precond="cahouet-chabard")
+    for c in range(3):
+        assert rel(vel[c], vel_o[c]) <= 1e-8
+    assert rel(p, p_o) <= 1e-6
+
+
+def test_paper_preconditioner_small_dt(fdi):
+    # the paper's inverse pressure Laplacian alone: few iterations at small dt
+    # (Sec. 2 reports 2-4 BiCGstab(2) iterations at dt = 0.01 on its 2D grid)
+    faces = box_faces((32, 32, 32), 1.5)
+    f = forcing(faces, 4)
+    vel, p, it, res, status = gpu_stokes(fdi, faces, 1e-2, 1000.0, f, 0, precond=0)
+    assert status == 0 and res <= 1e-11 and it <= 12, (it, res)
+    vel_o, p_o, it_o, _ = st.stokes_semi_direct(faces, 1e-2, 1000.0, f, tol=1e-12)
+    for c in range(3):
+        assert rel(vel[c], vel_o[c]) <= 1e-8

@@ -131,3 +131,28 @@ def test_preconditioned_iterations_small_at_small_dt():
     f = _forcing(faces, 2)
     _, _, it_small, _ = st.stokes_semi_direct(faces, 1e-2, 1000.0, f, tol=1e-10)
     assert it_small <= 3
+
+
+@pytest.mark.parametrize("dt", [1e-2, 1.0, 1e3])
+def test_cahouet_chabard_preconditioner_equals_direct(dt):
+    # the viscous-corrected preconditioner changes the iteration, not the answer
+    faces = _faces()
+    f = _forcing(faces, 13)
+    vel_d, p_d = st.stokes_direct(faces, dt, 1000.0, f)
+    vel, p, it, rel = st.stokes_semi_direct(faces, dt, 1000.0, f, tol=1e-12, precond="cahouet-chabard")
+    assert rel <= 1e-12
+    for c in range(3):
+        assert np.abs(vel[c] - vel_d[c]).max() < 1e-9 * np.abs(vel_d[c]).max()
+    assert np.abs(p - p_d).max() < 1e-8 * np.abs(p_d).max()
+
+
+def test_cahouet_chabard_exact_on_uniform_periodic_analogue():
+    # with commuting operators C = L (I - lam L)^{-1}; check that L^{-1} - lam I inverts it
+    rng = np.random.default_rng(0)
+    Q, _ = np.linalg.qr(rng.standard_normal((12, 12)))
+    mu = -np.linspace(0.5, 40.0, 12)
+    L = Q @ np.diag(mu) @ Q.T
+    lam = 0.7
+    C = L @ np.linalg.inv(np.eye(12) - lam * L)
+    P = np.linalg.inv(L) - lam * np.eye(12)
+    assert np.abs(P @ C - np.eye(12)).max() < 1e-12
