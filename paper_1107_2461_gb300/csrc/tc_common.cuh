@@ -170,6 +170,17 @@ __device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
   return d;
 }
 
+// Same for the 64-byte swizzle layout (8-row x 64-byte atoms, 512 bytes apart).
+__device__ __forceinline__ uint64_t sdesc_k_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);          // start address, bits 0-13
+  d |= (uint64_t)1 << 16;                           // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;                  // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                           // descriptor version (sm_100 family)
+  d |= (uint64_t)4 << 61;                           // layout: 64-byte swizzle
+  return d;
+}
+
 // Instruction descriptor, kind::f16: D = f32, A = B = f16, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
   return (1u << 4)                       // D format: f32
@@ -184,6 +195,13 @@ __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
 __device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
   int chunk = k >> 3;  // 16-byte chunk (8 fp16)
   return (uint32_t)(row * 128 + ((chunk ^ (row & 7)) << 4) + ((k & 7) << 1));
+}
+
+// byte offset of element (row, k) of a K-major fp16 tile with 32 fp16 per
+// 64-byte row in the 64-byte swizzle layout (address bits 4-5 ^= bits 7-8)
+__device__ __forceinline__ uint32_t sw64_offset(int row, int k) {
+  int chunk = k >> 3;  // 16-byte chunk (8 fp16)
+  return (uint32_t)(row * 64 + ((chunk ^ ((row >> 1) & 3)) << 4) + ((k & 7) << 1));
 }
 
 }  // namespace tc

@@ -35,16 +35,19 @@ namespace fdi {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BK = 64;
-constexpr int STAGES = 2;
+constexpr int BK = 32;                       // fp16 K per chunk: 64-byte rows, 64-byte swizzle
+constexpr int STAGES = 4;
 constexpr int NMAX = 256;
-constexpr int A_BYTES = BM * 128;            // one fp16 half of an A chunk: 16 KB
-constexpr int B_BYTES = NMAX * 128;          // one fp16 half of a B chunk: up to 32 KB
+constexpr int ROWB = BK * 2;                 // bytes per operand row in a stage
+constexpr int A_BYTES = BM * ROWB;           // one fp16 half of an A chunk: 8 KB
+constexpr int B_BYTES = NMAX * ROWB;         // one fp16 half of a B chunk: up to 16 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int NCONV = 8;
 constexpr int THREADS = 32 * (2 + NCONV + 4);
 constexpr int TP_BYTES = 4 * 32 * 33 * 4;     // epilogue transpose tiles, one per epilogue warp
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256 + TP_BYTES;
+constexpr int BAR_BYTES = 256;
+constexpr int CS_BYTES = NMAX * 4;            // per-column unscale factors
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + BAR_BYTES + TP_BYTES + CS_BYTES;
 
 __device__ __forceinline__ float scale_from_max(float mx) {
   // power of two that maps mx into [2^14, 2^15): fp16 keeps 11 bits there and
@@ -64,15 +67,17 @@ __device__ __forceinline__ uint32_t pack_half2(__half a, __half b) {
 template <int C>
 __global__ void __launch_bounds__(THREADS, 1) k_tc_transform(const __grid_constant__ CUtensorMap tmB, TcArgs a) {
   if (a.skip && *a.skip) return;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // align by offsetting the shared array itself, so that every pointer below
+  // stays in the shared address space (shared loads/stores, no generic aliasing)
+  uint8_t* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  uint64_t* full_b = bars;        // B chunk landed (TMA transaction bytes)
-  uint64_t* conv = bars + 2;      // A chunk converted (NCONV warp arrivals)
-  uint64_t* empty = bars + 4;     // stage consumed by the MMAs (C commits)
-  uint64_t* accf = bars + 6;      // accumulator complete
-  uint64_t* acce = bars + 8;      // accumulator drained by the epilogue
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
+  uint64_t* full_b = bars;                  // B chunk landed (TMA transaction bytes)
+  uint64_t* conv = bars + STAGES;           // A chunk converted (NCONV warp arrivals)
+  uint64_t* empty = bars + 2 * STAGES;      // stage consumed by the MMAs (C commits)
+  uint64_t* accf = bars + 3 * STAGES;       // accumulator complete
+  uint64_t* acce = bars + 3 * STAGES + 2;   // accumulator drained by the epilogue
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * STAGES + 4);
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -95,6 +100,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_transform(const __grid_consta
     tc::fence_mbar_init();
   }
   if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmB);
+  float* s_cs = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + BAR_BYTES + TP_BYTES);
+  for (int k = threadIdx.x; k < N_pad; k += blockDim.x) s_cs[k] = a.col_scale[k];
   if (warp == 1) {
     tc::tmem_alloc(tmem_slot, tmem_cols);
     tc::tmem_relinquish();
@@ -115,7 +122,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_transform(const __grid_consta
   if (warp == 0) {
     // ---------------- TMA producer (B) ----------------
     if (lane == 0) {
-      const uint32_t bbytes = (uint32_t)(2 * N_pad * 128);
+      const uint32_t bbytes = (uint32_t)(2 * N_pad * ROWB);
       const int rows_per = N_pad / C;
       const int r0 = (int)rank * rows_per;
       uint32_t g = 0;
@@ -130,8 +137,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_transform(const __grid_consta
           }
           tc::mbar_expect_tx(&full_b[s], bbytes);
           uint8_t* st = smem + s * STAGE_BYTES;
-          const uint32_t dhi = tc::smem_u32(st + 2 * A_BYTES) + r0 * 128;
-          const uint32_t dlo = tc::smem_u32(st + 2 * A_BYTES + B_BYTES) + r0 * 128;
+          const uint32_t dhi = tc::smem_u32(st + 2 * A_BYTES) + r0 * ROWB;
+          const uint32_t dlo = tc::smem_u32(st + 2 * A_BYTES + B_BYTES) + r0 * ROWB;
           if (C == 1) {
             tc::tma_load_2d(dhi, &tmB, kc * BK, r0, &full_b[s]);
             tc::tma_load_2d(dlo, &tmB, kc * BK, N_pad + r0, &full_b[s]);
@@ -185,9 +192,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_transform(const __grid_consta
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint32_t off = kk * 32;
             const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
-            tc::mma_f16(d, tc::sdesc_k_sw128(ahi + off), tc::sdesc_k_sw128(bhi + off), idesc, acc);
-            tc::mma_f16(d, tc::sdesc_k_sw128(ahi + off), tc::sdesc_k_sw128(blo + off), idesc, 1u);
-            tc::mma_f16(d, tc::sdesc_k_sw128(alo + off), tc::sdesc_k_sw128(bhi + off), idesc, 1u);
+            tc::mma_f16(d, tc::sdesc_k_sw64(ahi + off), tc::sdesc_k_sw64(bhi + off), idesc, acc);
+            tc::mma_f16(d, tc::sdesc_k_sw64(ahi + off), tc::sdesc_k_sw64(blo + off), idesc, 1u);
+            tc::mma_f16(d, tc::sdesc_k_sw64(alo + off), tc::sdesc_k_sw64(bhi + off), idesc, 1u);
           }
           if (C == 1)
             tc::mma_commit(&empty[s]);
@@ -204,22 +211,22 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_transform(const __grid_consta
     }
   } else if (warp < 2 + NCONV) {
     // ---------------- converters ----------------
-    // Each thread owns 4 (row, 16-byte chunk) slots of a 128 x 64 A chunk; the
+    // Each thread owns 2 (row, 16-byte chunk) slots of a 128 x 32 A chunk; the
     // global loads of the next chunk are issued before the current one is
     // converted, so two chunks of loads are in flight per converter warp.
     const int ct = (warp - 2) * 32 + lane;  // 0..255
     const float sA = scale_from_max(a.scale_in ? *a.scale_in : 1.0f);
-    const int c8 = ct & 7;                  // 16-byte chunk within the 128-byte row
+    const int c8 = ct & 3;                  // 16-byte chunk within the 64-byte row
     const long long total = my_iters * nK;
-    auto load_chunk = [&](long long gi, float (&v)[4][8]) {
+    auto load_chunk = [&](long long gi, float (&v)[2][8]) {
       const long long it = gi / nK;
       const int kc = (int)(gi % nK);
       const long long tile = blockIdx.x + it * gridDim.x;
       const long long row0 = tile * BM;
       const int k0 = kc * BK + c8 * 8;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const long long grow = row0 + (ct >> 3) + 32 * q;
+      for (int q = 0; q < 2; ++q) {
+        const long long grow = row0 + (ct >> 2) + 64 * q;
         float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
         if (tile < num_tiles && grow < a.R) {
           const float* src = a.in + grow * (long long)a.in_pitch + k0;
@@ -228,58 +235,74 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_transform(const __grid_consta
         }
         v[q][0] = x0.x; v[q][1] = x0.y; v[q][2] = x0.z; v[q][3] = x0.w;
         v[q][4] = x1.x; v[q][5] = x1.y; v[q][6] = x1.z; v[q][7] = x1.w;
-#pragma unroll
-        for (int e = 0; e < 8; ++e)
-          if (k0 + e >= a.K) v[q][e] = 0.f;
       }
+      // nothing here may consume the loaded registers: the K-tail mask is
+      // applied at conversion time so the load latency overlaps the wait
     };
-    float v[4][8], w[4][8];
-    if (total > 0) load_chunk(0, v);
-    for (long long gi = 0; gi < total && !s_abort; ++gi) {
+    // three register buffers rotate: the loads of the next two chunks are in
+    // flight while the current one is converted
+    float v0[2][8], v1[2][8], v2[2][8];
+    auto convert_store = [&](long long gi, const float (&v)[2][8]) -> bool {
       const uint32_t g = (uint32_t)gi;
       const int s = g % STAGES;
       const uint32_t ph = (g / STAGES) & 1;
-      if (gi + 1 < total) load_chunk(gi + 1, w);
       if (!tc::mbar_wait(&empty[s], ph ^ 1, &s_abort)) {
         atomicExch(a.err, 4);
-        break;
+        return false;
       }
       uint8_t* st = smem + s * STAGE_BYTES;
+      const int k0 = (int)(gi % nK) * BK + c8 * 8;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int row = (ct >> 3) + 32 * q;
+      for (int q = 0; q < 2; ++q) {
+        const int row = (ct >> 2) + 64 * q;
         uint32_t hw[4], lw[4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
-          const float x0 = v[q][e] * sA, x1 = v[q][e + 1] * sA;
+          const float x0 = (k0 + e < a.K) ? v[q][e] * sA : 0.f;
+          const float x1 = (k0 + e + 1 < a.K) ? v[q][e + 1] * sA : 0.f;
           const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
           const __half l0 = __float2half_rn(x0 - __half2float(h0));
           const __half l1 = __float2half_rn(x1 - __half2float(h1));
           hw[e / 2] = pack_half2(h0, h1);
           lw[e / 2] = pack_half2(l0, l1);
         }
-        const uint32_t off = tc::sw128_offset(row, c8 * 8);
+        const uint32_t off = tc::sw64_offset(row, c8 * 8);
         *reinterpret_cast<uint4*>(st + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
         *reinterpret_cast<uint4*>(st + A_BYTES + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
       tc::fence_proxy_async_smem();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&conv[s]);
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[q][e] = w[q][e];
+      return true;
+    };
+    if (total > 0) load_chunk(0, v0);
+    if (total > 1) load_chunk(1, v1);
+    for (long long gi = 0; gi < total && !s_abort; gi += 3) {
+      if (gi + 2 < total) load_chunk(gi + 2, v2);
+      if (!convert_store(gi, v0)) break;
+      if (gi + 1 >= total) break;
+      if (gi + 3 < total) load_chunk(gi + 3, v0);
+      if (!convert_store(gi + 1, v1)) break;
+      if (gi + 2 >= total) break;
+      if (gi + 4 < total) load_chunk(gi + 4, v1);
+      if (!convert_store(gi + 2, v2)) break;
     }
   } else {
     // ---------------- epilogue ----------------
     // Each thread holds one accumulator row (TMEM lane) and 32 columns per
-    // load.  Transposed outputs (consecutive rows contiguous) are stored
-    // directly; row-major outputs go through a 32 x 33 shared tile so that each
-    // warp store covers 32 consecutive columns of one row.
+    // load.  Every 32 x 32 block goes through a shared tile (stride 33: conflict
+    // free both ways); after the transpose a lane owns 4 consecutive rows of one
+    // column (transposed outputs) or 4 consecutive columns of one row (row-major
+    // outputs) and stores them with one 16-byte access where the layout allows.
     const int q = warp & 3;  // TMEM lane quarter accessible to this warp
     const float inv_sA = 1.0f / scale_from_max(a.scale_in ? *a.scale_in : 1.0f);
-    float* tp = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256) + (warp - (2 + NCONV)) * (32 * 33);
+    float* tp = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + BAR_BYTES) + (warp - (2 + NCONV)) * (32 * 33);
     const bool rowmajor = a.mode != TC_OUT_F32 || a.col_stride == 1;
+    // vector stores need 16-byte aligned groups of 4 along the contiguous index
+    const bool vec_t = !rowmajor && a.row_stride == 1 && (a.S % 4 == 0) && (a.slab_stride % 4 == 0) &&
+                       (a.col_stride % 4 == 0);
+    const bool vec_r = rowmajor && (a.mode != TC_OUT_F32 || (a.row_stride % 4 == 0 && a.slab_stride % 4 == 0));
+    const int g8 = lane >> 3, l8 = lane & 7;  // after the transpose: group of 8 lanes, lane in group
     float vmax = 0.f;
     for (long long it = 0; it < my_iters && !s_abort; ++it) {
       const long long tile = blockIdx.x + it * gridDim.x;
@@ -290,72 +313,124 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_transform(const __grid_consta
         break;
       }
       tc::tc_fence_after();
-      const long long wrow0 = tile * BM + 32 * q;   // first row of this warp
-      const long long row = wrow0 + lane;
-      const bool vrow = tile < num_tiles && row < a.R;
+      const long long wrow0 = tile * BM + 32 * q;  // first row of this warp
+      const bool tvalid = tile < num_tiles;
+      const int nrows = tvalid ? (int)max(0LL, min((long long)32, a.R - wrow0)) : 0;
+      // output base of this lane's own row (row = wrow0 + lane)
       long long base = 0;
-      if (vrow) base = (row / a.S) * a.slab_stride + (row % a.S) * a.row_stride;
+      {
+        const long long row = wrow0 + lane;
+        if (row < a.R) base = (row / a.S) * a.slab_stride + (row % a.S) * a.row_stride;
+      }
+      // bases of the 4 rows this lane stores after a transpose (transposed outputs)
+      long long tb[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) tb[e] = __shfl_sync(0xffffffffu, base, 4 * l8 + e);
       for (int c0 = 0; c0 < N_pad; c0 += 32) {
         uint32_t r[32];
         tc::tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * N_pad + c0), r);
         tc::tmem_ld_wait();
-        if (!rowmajor) {
-          if (vrow) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int k = c0 + j;
-              if (k < a.n_out) {
-                const float val = __uint_as_float(r[j]) * inv_sA * a.col_scale[k];
-                a.out_f32[base + (long long)k * a.col_stride] = val;
-                vmax = fmaxf(vmax, fabsf(val));
+        for (int j = 0; j < 32; ++j) tp[lane * 33 + j] = __uint_as_float(r[j]);
+        __syncwarp();
+        if (!rowmajor) {
+          // lane -> column c0 + 4*qq + g8, rows 4*l8 .. 4*l8+3 of the warp block
+          const int rr = 4 * l8;
+#pragma unroll
+          for (int qq = 0; qq < 8; ++qq) {
+            const int cl = 4 * qq + g8;
+            const int k = c0 + cl;
+            if (k < a.n_out) {
+              const float cs = s_cs[k] * inv_sA;
+              float v4[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                v4[e] = tp[(rr + e) * 33 + cl] * cs;
+                if (rr + e < nrows) vmax = fmaxf(vmax, fabsf(v4[e]));
+              }
+              const long long koff = (long long)k * a.col_stride;
+              if (vec_t && rr + 3 < nrows) {
+                *reinterpret_cast<float4*>(a.out_f32 + tb[0] + koff) = make_float4(v4[0], v4[1], v4[2], v4[3]);
+              } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                  if (rr + e < nrows) a.out_f32[tb[e] + koff] = v4[e];
               }
             }
           }
         } else {
+          // lane -> row 4*qq + g8 of the warp block, columns c0 + 4*l8 .. +3
+          const int cc = 4 * l8;
+          float cs[4];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) tp[lane * 33 + j] = __uint_as_float(r[j]);
-          __syncwarp();
-          const int k = c0 + lane;
-          const bool kval = k < a.n_out;
-          const float cs = kval ? a.col_scale[k] * inv_sA : 0.f;
-          const int nrows = (int)min((long long)32, a.R - wrow0);  // rows of this warp inside the field
-          if (a.mode == TC_OUT_F32) {
-            for (int i = 0; i < 32; ++i) {
-              const long long bi = __shfl_sync(0xffffffffu, base, i);
-              if (tile < num_tiles && i < nrows && kval) {
-                const float val = tp[i * 33 + lane] * cs;
-                a.out_f32[bi + k] = val;
-                vmax = fmaxf(vmax, fabsf(val));
-              }
-            }
-          } else if (tile < num_tiles && kval) {
-            float2* xcol = a.out_df + wrow0 * (long long)a.n_out + k;
-            const long long rs = a.n_out;
-            if (a.mode == TC_OUT_DF_SET) {
-              for (int i = 0; i < nrows; ++i) xcol[i * rs] = make_float2(tp[i * 33 + lane] * cs, 0.f);
-            } else {
-              // read-modify-write of the double-float accumulator, loads batched
-              for (int i0 = 0; i0 < nrows; i0 += 8) {
-                float2 o[8];
+          for (int e = 0; e < 4; ++e) {
+            const int k = c0 + cc + e;
+            cs[e] = (k < a.n_out) ? s_cs[k] * inv_sA : 0.f;
+          }
+          const bool fullcols = c0 + cc + 3 < a.n_out;
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
-                  if (i0 + i < nrows) o[i] = xcol[(i0 + i) * rs];
+          for (int qq = 0; qq < 8; ++qq) {
+            const int rl = 4 * qq + g8;
+            const long long brow = __shfl_sync(0xffffffffu, base, rl);
+            if (rl < nrows) {
+              float v4[4];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                  if (i0 + i < nrows) {
-                    const float val = tp[(i0 + i) * 33 + lane] * cs;
-                    const float sh = o[i].x + val;
-                    const float bb = sh - o[i].x;
-                    const float er = (o[i].x - (sh - bb)) + (val - bb) + o[i].y;
-                    const float nh = sh + er;
-                    xcol[(i0 + i) * rs] = make_float2(nh, er - (nh - sh));
+              for (int e = 0; e < 4; ++e) v4[e] = tp[rl * 33 + cc + e] * cs[e];
+              const long long rr = wrow0 + rl;
+              if (a.mode == TC_OUT_F32) {
+                float* o = a.out_f32 + brow + c0 + cc;
+                if (vec_r && fullcols) {
+                  *reinterpret_cast<float4*>(o) = make_float4(v4[0], v4[1], v4[2], v4[3]);
+                } else {
+#pragma unroll
+                  for (int e = 0; e < 4; ++e)
+                    if (c0 + cc + e < a.n_out) o[e] = v4[e];
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                  if (c0 + cc + e < a.n_out) vmax = fmaxf(vmax, fabsf(v4[e]));
+              } else {
+                float2* x = a.out_df + rr * (long long)a.n_out + c0 + cc;
+                const bool v2 = fullcols && ((rr * (long long)a.n_out + c0 + cc) % 2 == 0);
+                float2 o[4];
+                if (a.mode == TC_OUT_DF_ADD) {
+                  if (v2) {
+                    const float4 p0 = reinterpret_cast<const float4*>(x)[0];
+                    const float4 p1 = reinterpret_cast<const float4*>(x)[1];
+                    o[0] = make_float2(p0.x, p0.y);
+                    o[1] = make_float2(p0.z, p0.w);
+                    o[2] = make_float2(p1.x, p1.y);
+                    o[3] = make_float2(p1.z, p1.w);
+                  } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) o[e] = (c0 + cc + e < a.n_out) ? x[e] : make_float2(0.f, 0.f);
                   }
+#pragma unroll
+                  for (int e = 0; e < 4; ++e) {
+                    const float val = v4[e];
+                    const float sh = o[e].x + val;
+                    const float bb = sh - o[e].x;
+                    const float er = (o[e].x - (sh - bb)) + (val - bb) + o[e].y;
+                    const float nh = sh + er;
+                    o[e] = make_float2(nh, er - (nh - sh));
+                  }
+                } else {
+#pragma unroll
+                  for (int e = 0; e < 4; ++e) o[e] = make_float2(v4[e], 0.f);
+                }
+                if (v2) {
+                  reinterpret_cast<float4*>(x)[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+                  reinterpret_cast<float4*>(x)[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+                } else {
+#pragma unroll
+                  for (int e = 0; e < 4; ++e)
+                    if (c0 + cc + e < a.n_out) x[e] = o[e];
                 }
               }
             }
           }
-          __syncwarp();
         }
+        __syncwarp();
       }
       tc::tc_fence_before();
       __syncwarp();
@@ -441,7 +516,7 @@ fdi_status tc_prepare_matrix(fdi_plan* p, const double* T, int n, TcMatrix* m, c
     cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)(m->N_pad / Cs[ci])};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(reinterpret_cast<CUtensorMap*>(m->tmap[ci]), CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, m->B, dims,
-                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
       set_error("cuTensorMapEncodeTiled failed for a transform matrix");
