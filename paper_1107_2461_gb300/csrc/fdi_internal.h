@@ -76,6 +76,7 @@ struct fdi_plan {
   float* d_scales = nullptr;        // per refinement round: max |field| of the pass inputs
   int* d_err = nullptr;             // nonzero: a tensor-core kernel hit a wait limit
   int tc_cluster = 1;               // CTAs sharing each transform-matrix chunk by TMA multicast
+  float2* lam_w = nullptr;          // lambda-scaled double-float flux weights [3][3][kMaxN]
   double* partials = nullptr;       // reduction partials
   int npartials = 0;
   fdi::DevStatus* d_status = nullptr;

@@ -50,6 +50,7 @@ struct ResidArgs {
   const float2* w0[3];
   const float2* m[3];
   float2 sigma, lambda;
+  int sig_mode;         // 0: sigma = 0, 1: sigma = 1, 2: general sigma
   const double* b;
   const float2* x;      // null: first pass, r = b
   float* r;
@@ -71,7 +72,35 @@ __device__ __forceinline__ df::F2 ld2(const float2* p) {
 // range of planes; each thread keeps x at k-1, k, k+1 in registers, reuses the
 // z difference of the previous plane and gets the x difference of its left
 // neighbour by shuffle.  Work per block is fixed, so the reduction order is too.
+//
+// Arithmetic: x = xh + xl (double-float).  With the flux weights already
+// multiplied by lambda (w' = lambda w, double-float), lambda L x = L'xh + L'xl;
+// L'xh is formed exactly term by term (two-difference of the float values, FMA
+// two-product with the double-float weight, two-sum accumulation with the low
+// parts deferred) and L'xl in plain FP32 (it is 2^-24 smaller).  The residual
+// is b - sigma x + lambda L x with sigma in {0, 1}.
 constexpr int kResTX = 32, kResTY = 8, kResZChunk = 16;
+
+struct Acc {
+  float h, l;  // unnormalised double-float accumulator
+};
+
+__device__ __forceinline__ void acc_add(Acc& s, float ph, float pl) {
+  const float t = s.h + ph;
+  const float bb = t - s.h;
+  s.l += ((s.h - (t - bb)) + (ph - bb)) + pl;
+  s.h = t;
+}
+
+// s += w * (a - c) for float a, c (exact difference) and double-float w
+__device__ __forceinline__ void acc_flux(Acc& s, float2 w, float a, float c) {
+  const float d = a - c;
+  const float bb = d - a;
+  const float dl = (a - (d - bb)) - (c + bb);  // a - c = d + dl exactly
+  const float p = w.x * d;
+  const float e = fmaf(w.x, d, -p) + fmaf(w.x, dl, w.y * d);
+  acc_add(s, p, e);
+}
 
 __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const int* __restrict__ skip) {
   if (skip && *skip) return;
@@ -85,65 +114,89 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const
   const int ic = min(i, nx - 1), jc = min(j, ny - 1);
   df::F2 mean = df::make(0.f, 0.f);
   if (a.sub_mean) mean = df::from_f64(a.st->mean_b);
-  const df::F2 sig = df::make(a.sigma.x, a.sigma.y), lam = df::make(a.lambda.x, a.lambda.y);
-  const df::F2 wpx = ld2(a.wp[0] + ic), wmx = ld2(a.wm[0] + ic), wpy = ld2(a.wp[1] + jc), wmy = ld2(a.wm[1] + jc);
+  const int sig_mode = a.sig_mode;  // 0: sigma = 0, 1: sigma = 1, 2: other
+  // lambda-scaled weights (see mixed_field_solve)
+  const float2 wpx = a.wp[0][ic], wmx = a.wm[0][ic], wpy = a.wp[1][jc], wmy = a.wm[1][jc];
   const df::F2 w0xy = df::add(ld2(a.w0[0] + ic), ld2(a.w0[1] + jc));
   df::F2 Vxy = df::make(0.f, 0.f);
   if (a.want_mean) Vxy = df::mul(ld2(a.m[0] + ic), ld2(a.m[1] + jc));
+  const bool hx = i + 1 < nx, lx = i > 0, hy = j + 1 < ny, ly = j > 0;
   float srr = 0.f, sbb = 0.f, rmax = 0.f;
   df::F2 svb = df::make(0.f, 0.f), sv = df::make(0.f, 0.f);
-  const df::F2 zero = df::make(0.f, 0.f);
   const long long col = (long long)jc * nx + ic;
-  df::F2 xc = zero, dzm = zero;
-  if (a.x && k0 < k1) {
-    xc = ld2(a.x + (long long)k0 * sz + col);
-    if (k0 > 0) dzm = df::sub(ld2(a.x + (long long)(k0 - 1) * sz + col), xc);
+  const float2 z2 = make_float2(0.f, 0.f);
+  // software pipeline: the loads of plane k+1 (and of x at k+2) are issued
+  // before plane k is computed
+  float2 xc = z2, xm = z2, xp = z2, xn = z2, xs = z2;
+  double bnow = 0.0;
+  if (k0 < k1) {
+    const long long p0 = (long long)k0 * sz + col;
+    xc = a.x[p0];
+    if (k0 > 0) xm = a.x[p0 - sz];
+    if (k0 + 1 < nz) xp = a.x[p0 + sz];
+    xn = hy ? a.x[p0 + sy] : xc;
+    xs = ly ? a.x[p0 - sy] : xc;
+    bnow = act ? a.b[p0] : 0.0;
   }
   for (int k = k0; k < k1; ++k) {
     const long long p = (long long)k * sz + col;
-    df::F2 bb = act ? df::from_f64(a.b[p]) : zero;
-    if (a.want_mean) {
+    float2 xp2 = z2, xn2 = z2, xs2 = z2;
+    double bnext = 0.0;
+    if (k + 1 < k1) {
+      if (k + 2 < nz) xp2 = a.x[p + 2 * sz];
+      xn2 = hy ? a.x[p + sz + sy] : xp;
+      xs2 = ly ? a.x[p + sz - sy] : xp;
+      bnext = act ? a.b[p + sz] : 0.0;
+    }
+    df::F2 bb = act ? df::from_f64(bnow) : df::make(0.f, 0.f);
+    if (a.want_mean && act) {
       const df::F2 V = df::mul(Vxy, ld2(a.m[2] + k));
-      if (act) {
-        svb = df::add(svb, df::mul(V, a.x ? xc : bb));
-        sv = df::add(sv, V);
-      }
+      svb = df::add(svb, df::mul(V, df::make(xc.x, xc.y)));
+      sv = df::add(sv, V);
     }
     if (a.sub_mean) bb = df::sub(bb, mean);
-    df::F2 r = bb;
-    if (a.x) {
-      df::F2 xp = zero;
-      if (k + 1 < nz) xp = ld2(a.x + p + sz);
-      // x direction: d+ = x[i+1] - x[i]; lane i-1's d+ is -(x[i-1] - x[i])
-      df::F2 xr;
-      xr.hi = __shfl_down_sync(0xffffffffu, xc.hi, 1);
-      xr.lo = __shfl_down_sync(0xffffffffu, xc.lo, 1);
-      if (lane == kResTX - 1 && i + 1 < nx) xr = ld2(a.x + p + 1);
-      const df::F2 dxp = (i + 1 < nx) ? df::sub(xr, xc) : zero;
-      df::F2 dxm;
-      dxm.hi = -__shfl_up_sync(0xffffffffu, dxp.hi, 1);
-      dxm.lo = -__shfl_up_sync(0xffffffffu, dxp.lo, 1);
-      if (lane == 0) dxm = (i > 0) ? df::sub(ld2(a.x + p - 1), xc) : zero;
-      df::F2 L = df::mul(df::add(w0xy, ld2(a.w0[2] + k)), xc);
-      if (i + 1 < nx) L = df::add(L, df::mul(wpx, dxp));
-      if (i > 0) L = df::add(L, df::mul(wmx, dxm));
-      if (j + 1 < ny) L = df::add(L, df::mul(wpy, df::sub(ld2(a.x + p + sy), xc)));
-      if (j > 0) L = df::add(L, df::mul(wmy, df::sub(ld2(a.x + p - sy), xc)));
-      const df::F2 dzp = (k + 1 < nz) ? df::sub(xp, xc) : zero;
-      if (k + 1 < nz) L = df::add(L, df::mul(ld2(a.wp[2] + k), dzp));
-      if (k > 0) L = df::add(L, df::mul(ld2(a.wm[2] + k), dzm));
-      r = df::add(df::sub(bb, df::mul(sig, xc)), df::mul(lam, L));
-      if (act && a.out) a.out[p] = df::to_f64(xc);
-      dzm = df::neg(dzp);
-      xc = xp;
+    // x neighbours by shuffle (lanes at the block edge load them)
+    float2 xe, xw;
+    xe.x = __shfl_down_sync(0xffffffffu, xc.x, 1);
+    xe.y = __shfl_down_sync(0xffffffffu, xc.y, 1);
+    xw.x = __shfl_up_sync(0xffffffffu, xc.x, 1);
+    xw.y = __shfl_up_sync(0xffffffffu, xc.y, 1);
+    if (lane == kResTX - 1 && hx) xe = a.x[p + 1];
+    if (lane == 0 && lx) xw = a.x[p - 1];
+    Acc S{0.f, 0.f};
+    float sl = 0.f;  // lambda L applied to the low parts, FP32
+    const float2 wpz = a.wp[2][k], wmz = a.wm[2][k];
+    if (hx) { acc_flux(S, wpx, xe.x, xc.x); sl = fmaf(wpx.x, xe.y - xc.y, sl); }
+    if (lx) { acc_flux(S, wmx, xw.x, xc.x); sl = fmaf(wmx.x, xw.y - xc.y, sl); }
+    if (hy) { acc_flux(S, wpy, xn.x, xc.x); sl = fmaf(wpy.x, xn.y - xc.y, sl); }
+    if (ly) { acc_flux(S, wmy, xs.x, xc.x); sl = fmaf(wmy.x, xs.y - xc.y, sl); }
+    if (k + 1 < nz) { acc_flux(S, wpz, xp.x, xc.x); sl = fmaf(wpz.x, xp.y - xc.y, sl); }
+    if (k > 0) { acc_flux(S, wmz, xm.x, xc.x); sl = fmaf(wmz.x, xm.y - xc.y, sl); }
+    const df::F2 w0 = df::add(w0xy, ld2(a.w0[2] + k));
+    if (w0.hi != 0.f) {  // wall term: only next to a Dirichlet wall
+      const df::F2 t = df::mul(w0, df::make(xc.x, xc.y));
+      acc_add(S, t.hi, t.lo);
     }
+    S.l += sl;
+    df::F2 r = df::add(bb, df::fast_two_sum(S.h, S.l));
+    if (sig_mode == 1)
+      r = df::sub(r, df::make(xc.x, xc.y));
+    else if (sig_mode == 2)
+      r = df::sub(r, df::mul(df::make(a.sigma.x, a.sigma.y), df::make(xc.x, xc.y)));
     if (act) {
+      if (a.out) a.out[p] = df::to_f64(df::make(xc.x, xc.y));
       const float rf = r.hi + r.lo;
       a.r[((long long)k * ny + j) * a.r_pitch + i] = rf;
       srr = fmaf(rf, rf, srr);
       sbb = fmaf(bb.hi, bb.hi, sbb);
       rmax = fmaxf(rmax, fabsf(rf));
     }
+    xm = xc;
+    xc = xp;
+    xp = xp2;
+    xn = xn2;
+    xs = xs2;
+    bnow = bnext;
   }
   double v[4] = {(double)srr, (double)sbb, df::to_f64(svb), df::to_f64(sv)};
 #pragma unroll
@@ -163,6 +216,84 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const
       for (int c = 0; c < 4; ++c) t[c] += sh[4 * q + c];
     const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     for (int c = 0; c < 4; ++c) a.partials[4 * bid + c] = t[c];
+  }
+}
+
+// r_0 = b: FP64 -> FP32 copy into the padded residual layout, ||b||^2, max |b|
+// and (singular problems) the volume-weighted sums; one warp per x-line
+__global__ void __launch_bounds__(256) k_init_rhs(ResidArgs a) {
+  __shared__ double sh[4 * 8];
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int nwarps = gridDim.x * 8;
+  float sbb = 0.f, rmax = 0.f;
+  df::F2 svb = df::make(0.f, 0.f), sv = df::make(0.f, 0.f);
+  for (int L = blockIdx.x * 8 + warp; L < ny * nz; L += nwarps) {
+    const int j = L % ny, k = L / ny;
+    const double* bl = a.b + (long long)L * nx;
+    float* rl = a.r + ((long long)k * ny + j) * a.r_pitch;
+    df::F2 Vjk = df::make(0.f, 0.f);
+    if (a.want_mean) Vjk = df::mul(ld2(a.m[1] + j), ld2(a.m[2] + k));
+    for (int i0 = 0; i0 < nx; i0 += 128) {
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * 32 + lane;
+        v[u] = i < nx ? bl[i] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * 32 + lane;
+        if (i < nx) {
+          const df::F2 bb = df::from_f64(v[u]);
+          const float rf = bb.hi + bb.lo;
+          rl[i] = rf;
+          sbb = fmaf(rf, rf, sbb);
+          rmax = fmaxf(rmax, fabsf(rf));
+          if (a.want_mean) {
+            const df::F2 V = df::mul(Vjk, ld2(a.m[0] + i));
+            svb = df::add(svb, df::mul(V, bb));
+            sv = df::add(sv, V);
+          }
+        }
+      }
+    }
+  }
+  double w[4] = {0.0, (double)sbb, df::to_f64(svb), df::to_f64(sv)};
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) w[q] += __shfl_down_sync(0xffffffffu, w[q], o);
+    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  }
+  if (lane == 0) {
+    for (int q = 0; q < 4; ++q) sh[4 * warp + q] = w[q];
+    if (rmax > 0.f) atomicMax(reinterpret_cast<unsigned int*>(a.rmax), __float_as_uint(rmax));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[4] = {0, 0, 0, 0};
+    for (int q = 0; q < 8; ++q)
+      for (int c = 0; c < 4; ++c) t[c] += sh[4 * q + c];
+    for (int c = 0; c < 4; ++c) a.partials[4 * blockIdx.x + c] = t[c];
+  }
+}
+
+// lambda-scaled double-float flux weights of the three directions
+__global__ void k_scale_weights(const float2* __restrict__ wp0, const float2* __restrict__ wm0,
+                                const float2* __restrict__ w00, int n0, const float2* __restrict__ wp1,
+                                const float2* __restrict__ wm1, const float2* __restrict__ w01, int n1,
+                                const float2* __restrict__ wp2, const float2* __restrict__ wm2,
+                                const float2* __restrict__ w02, int n2, float2 lam, float2* __restrict__ out) {
+  // out layout: [3 directions][3 kinds (p, m, 0)][kMaxN]
+  const int d = blockIdx.x / 3, kind = blockIdx.x % 3;
+  const int n = d == 0 ? n0 : (d == 1 ? n1 : n2);
+  const float2* src = d == 0 ? (kind == 0 ? wp0 : kind == 1 ? wm0 : w00)
+                             : d == 1 ? (kind == 0 ? wp1 : kind == 1 ? wm1 : w01)
+                                      : (kind == 0 ? wp2 : kind == 1 ? wm2 : w02);
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const df::F2 v = df::mul(df::make(lam.x, lam.y), ld2(src + t));
+    out[(d * 3 + kind) * kMaxN + t] = make_float2(v.hi, v.lo);
   }
 }
 
@@ -409,7 +540,7 @@ fdi_status setup_axis(fdi_plan* p, Axis* ax, cudaStream_t s) {
     const double km = (i > 0) ? ax->h_ko[i - 1] : 0.0;
     wp[i] = kp / ax->h_m[i];
     wm[i] = km / ax->h_m[i];
-    w0[i] = (ax->h_kd[i] + kp + km) / ax->h_m[i];
+    w0[i] = (i == 0 || i == n - 1) ? (ax->h_kd[i] + kp + km) / ax->h_m[i] : 0.0;
   }
   FDI_TRY(upload_df(&mx->wp, wp));
   FDI_TRY(upload_df(&mx->wm, wm));
@@ -466,6 +597,7 @@ fdi_status mixed_setup(fdi_plan* p) {
   FDI_CUDA_TRY(cudaMalloc(&p->d_scales, (size_t)(kMaxRefineCap + 2) * 4 * sizeof(float)));
   FDI_CUDA_TRY(cudaMalloc(&p->d_err, sizeof(int)));
   FDI_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
+  FDI_CUDA_TRY(cudaMalloc(&p->lam_w, (size_t)9 * kMaxN * sizeof(float2)));
   return FDI_OK;
 }
 
@@ -498,19 +630,27 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     set_error("grid too large for the reduction buffer");
     return FDI_ERR_INVALID_ARG;
   }
+  // flux weights multiplied by lambda for this solve
+  {
+    FDI_KTIMER(p, "reduce", s);
+    k_scale_weights<<<9, 256, 0, s>>>(mx->wp, mx->wm, mx->w0, nx, my->wp, my->wm, my->w0, ny, mz->wp, mz->wm, mz->w0,
+                                      nz, split_host(lambda), p->lam_w);
+    FDI_LAUNCH_CHECK(p);
+  }
   ResidArgs ra{};
   ra.nx = nx;
   ra.ny = ny;
   ra.nz = nz;
   for (int d = 0; d < 3; ++d) {
     const MixedAxis* m = static_cast<const MixedAxis*>(f.ax[d]->mixed);
-    ra.wp[d] = m->wp;
-    ra.wm[d] = m->wm;
-    ra.w0[d] = m->w0;
+    ra.wp[d] = p->lam_w + (d * 3 + 0) * kMaxN;
+    ra.wm[d] = p->lam_w + (d * 3 + 1) * kMaxN;
+    ra.w0[d] = p->lam_w + (d * 3 + 2) * kMaxN;
     ra.m[d] = m->m_df;
   }
   ra.sigma = split_host(sigma);
   ra.lambda = split_host(lambda);
+  ra.sig_mode = sigma == 0.0 ? 0 : (sigma == 1.0 ? 1 : 2);
   ra.b = b;
   ra.r = r;
   ra.r_pitch = px;
@@ -518,6 +658,7 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
   ra.partials = p->partials;
 
   // r_0 = b (and the volume-weighted mean of b for the singular problem)
+  const int iblocks = 152 * 4;
   {
     FDI_KTIMER(p, "residual_df_init", s);
     ResidArgs a0 = ra;
@@ -526,12 +667,12 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     a0.sub_mean = 0;
     a0.want_mean = singular ? 1 : 0;
     a0.rmax = p->d_scales + 0;
-    k_resid_df<<<rgrid, dim3(kResTX, kResTY), 0, s>>>(a0, nullptr);
+    k_init_rhs<<<iblocks, 256, 0, s>>>(a0);
     FDI_LAUNCH_CHECK(p);
   }
   {
     FDI_KTIMER(p, "reduce", s);
-    k_finish_mixed<<<1, 256, 0, s>>>(p->partials, rblocks, p->d_status, p->tol, 0, singular ? 1 : 0, nullptr);
+    k_finish_mixed<<<1, 256, 0, s>>>(p->partials, iblocks, p->d_status, p->tol, 0, singular ? 1 : 0, nullptr);
     FDI_LAUNCH_CHECK(p);
   }
 

@@ -123,7 +123,8 @@ fdi_status make_axis(Axis** out, const std::vector<double>& m, const std::vector
     double km = (i > 0) ? ko[i - 1] : 0.0;
     wp[i] = kp / m[i];
     wm[i] = km / m[i];
-    w0[i] = (kd[i] + kp + km) / m[i];
+    // wall term: nonzero only in the first and last cell (interior cells have none)
+    w0[i] = (i == 0 || i == n - 1) ? (kd[i] + kp + km) / m[i] : 0.0;
   }
   FDI_TRY(dev_alloc(&ax->m, n));
   FDI_TRY(dev_alloc(&ax->kd, n));
@@ -178,6 +179,7 @@ void free_plan(fdi_plan* p) {
   if (p->kpartials) cudaFree(p->kpartials);
   if (p->xdf) cudaFree(p->xdf);
   if (p->d_scales) cudaFree(p->d_scales);
+  if (p->lam_w) cudaFree(p->lam_w);
   if (p->d_err) cudaFree(p->d_err);
   if (p->partials) cudaFree(p->partials);
   if (p->d_status) cudaFree(p->d_status);

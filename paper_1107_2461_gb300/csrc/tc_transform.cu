@@ -368,16 +368,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_transform(const __grid_consta
             cs[e] = (k < a.n_out) ? s_cs[k] * inv_sA : 0.f;
           }
           const bool fullcols = c0 + cc + 3 < a.n_out;
+          if (a.mode == TC_OUT_F32) {
 #pragma unroll
-          for (int qq = 0; qq < 8; ++qq) {
-            const int rl = 4 * qq + g8;
-            const long long brow = __shfl_sync(0xffffffffu, base, rl);
-            if (rl < nrows) {
-              float v4[4];
+            for (int qq = 0; qq < 8; ++qq) {
+              const int rl = 4 * qq + g8;
+              const long long brow = __shfl_sync(0xffffffffu, base, rl);
+              if (rl < nrows) {
+                float v4[4];
 #pragma unroll
-              for (int e = 0; e < 4; ++e) v4[e] = tp[rl * 33 + cc + e] * cs[e];
-              const long long rr = wrow0 + rl;
-              if (a.mode == TC_OUT_F32) {
+                for (int e = 0; e < 4; ++e) v4[e] = tp[rl * 33 + cc + e] * cs[e];
                 float* o = a.out_f32 + brow + c0 + cc;
                 if (vec_r && fullcols) {
                   *reinterpret_cast<float4*>(o) = make_float4(v4[0], v4[1], v4[2], v4[3]);
@@ -389,42 +388,65 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_transform(const __grid_consta
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
                   if (c0 + cc + e < a.n_out) vmax = fmaxf(vmax, fabsf(v4[e]));
-              } else {
+              }
+            }
+          } else {
+            // double-float accumulator: rows in groups of 4 with the loads of a
+            // group issued before any of its updates
+            const bool evenrow = (a.n_out % 2 == 0);
+#pragma unroll
+            for (int q4 = 0; q4 < 8; q4 += 4) {
+              float2 o[4][4];
+              bool v2[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int rl = 4 * (q4 + u) + g8;
+                const long long rr = wrow0 + rl;
                 float2* x = a.out_df + rr * (long long)a.n_out + c0 + cc;
-                const bool v2 = fullcols && ((rr * (long long)a.n_out + c0 + cc) % 2 == 0);
-                float2 o[4];
-                if (a.mode == TC_OUT_DF_ADD) {
-                  if (v2) {
+                v2[u] = fullcols && evenrow;
+                if (rl < nrows && a.mode == TC_OUT_DF_ADD) {
+                  if (v2[u]) {
                     const float4 p0 = reinterpret_cast<const float4*>(x)[0];
                     const float4 p1 = reinterpret_cast<const float4*>(x)[1];
-                    o[0] = make_float2(p0.x, p0.y);
-                    o[1] = make_float2(p0.z, p0.w);
-                    o[2] = make_float2(p1.x, p1.y);
-                    o[3] = make_float2(p1.z, p1.w);
+                    o[u][0] = make_float2(p0.x, p0.y);
+                    o[u][1] = make_float2(p0.z, p0.w);
+                    o[u][2] = make_float2(p1.x, p1.y);
+                    o[u][3] = make_float2(p1.z, p1.w);
                   } else {
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) o[e] = (c0 + cc + e < a.n_out) ? x[e] : make_float2(0.f, 0.f);
-                  }
-#pragma unroll
-                  for (int e = 0; e < 4; ++e) {
-                    const float val = v4[e];
-                    const float sh = o[e].x + val;
-                    const float bb = sh - o[e].x;
-                    const float er = (o[e].x - (sh - bb)) + (val - bb) + o[e].y;
-                    const float nh = sh + er;
-                    o[e] = make_float2(nh, er - (nh - sh));
+                    for (int e = 0; e < 4; ++e) o[u][e] = (c0 + cc + e < a.n_out) ? x[e] : make_float2(0.f, 0.f);
                   }
                 } else {
 #pragma unroll
-                  for (int e = 0; e < 4; ++e) o[e] = make_float2(v4[e], 0.f);
+                  for (int e = 0; e < 4; ++e) o[u][e] = make_float2(0.f, 0.f);
                 }
-                if (v2) {
-                  reinterpret_cast<float4*>(x)[0] = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
-                  reinterpret_cast<float4*>(x)[1] = make_float4(o[2].x, o[2].y, o[3].x, o[3].y);
+              }
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const int rl = 4 * (q4 + u) + g8;
+                if (rl >= nrows) continue;
+                const long long rr = wrow0 + rl;
+                float2* x = a.out_df + rr * (long long)a.n_out + c0 + cc;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  const float val = tp[rl * 33 + cc + e] * cs[e];
+                  if (a.mode == TC_OUT_DF_ADD) {
+                    const float sh = o[u][e].x + val;
+                    const float bb = sh - o[u][e].x;
+                    const float er = (o[u][e].x - (sh - bb)) + (val - bb) + o[u][e].y;
+                    const float nh = sh + er;
+                    o[u][e] = make_float2(nh, er - (nh - sh));
+                  } else {
+                    o[u][e] = make_float2(val, 0.f);
+                  }
+                }
+                if (v2[u]) {
+                  reinterpret_cast<float4*>(x)[0] = make_float4(o[u][0].x, o[u][0].y, o[u][1].x, o[u][1].y);
+                  reinterpret_cast<float4*>(x)[1] = make_float4(o[u][2].x, o[u][2].y, o[u][3].x, o[u][3].y);
                 } else {
 #pragma unroll
                   for (int e = 0; e < 4; ++e)
-                    if (c0 + cc + e < a.n_out) x[e] = o[e];
+                    if (c0 + cc + e < a.n_out) x[e] = o[u][e];
                 }
               }
             }
