@@ -163,8 +163,9 @@ def kernel_model(name, n, steps, K):
         "transform_xb_set_tc": ("hbm", 12.0 * P, "byte", K),
         "transform_xb_add_tc": ("hbm", 20.0 * P, "byte", steps * K),
         "thomas_z_f32": ("hbm", 8.0 * P, "byte", rounds * K),
-        "residual_df": ("hbm", 28.0 * P, "byte", rounds * K),
+        "residual_df": ("hbm", 20.0 * P, "byte", rounds * K),
         "residual_df_init": ("hbm", 12.0 * P, "byte", K),
+        "finalize_out": ("hbm", 16.0 * P, "byte", K),
     }
     return t.get(name)
 

@@ -65,6 +65,42 @@ __device__ __forceinline__ double f2d(float f) {
 // hi + lo as the nearest FP64 (one FP64 add)
 __device__ __forceinline__ double to_f64(F2 a) { return f2d(a.hi) + f2d(a.lo); }
 
+// hi + lo as FP64 with integer operations only, for a normalised pair
+// (|lo| <= ulp(hi)) with hi normal: the significands are aligned at a common
+// binary point and added as 64-bit integers; bits of lo below the FP64
+// significand are truncated (error below one FP64 ulp).  Other inputs take the
+// FP64 addition.
+__device__ __forceinline__ double to_f64_bits(F2 a) {
+  const uint32_t bh = __float_as_uint(a.hi), bl = __float_as_uint(a.lo);
+  const int eh = (int)((bh >> 23) & 0xffu), el = (int)((bl >> 23) & 0xffu);
+  if (eh == 0 || eh == 255 || el == 0 || el == 255 || el > eh - 23) {
+    if ((bl & 0x7fffffffu) == 0u && eh != 0 && eh != 255) {
+      // lo = 0: exact widening of hi
+      return __longlong_as_double((long long)(((uint64_t)(bh & 0x80000000u) << 32) |
+                                              ((uint64_t)(eh - 127 + 1023) << 52) |
+                                              ((uint64_t)(bh & 0x7fffffu) << 29)));
+    }
+    return to_f64(a);
+  }
+  // hi significand with its leading bit at 2^52
+  long long T = (long long)((bh & 0x7fffffu) | 0x800000u) << 29;
+  const unsigned long long ml = (unsigned long long)((bl & 0x7fffffu) | 0x800000u);
+  const int shl = el - eh + 29;  // <= 6
+  long long L = shl >= 0 ? (long long)(ml << shl) : (shl > -40 ? (long long)(ml >> (-shl)) : 0ll);
+  if ((bh ^ bl) & 0x80000000u) L = -L;
+  T += L;
+  int e = eh;
+  if (T >= (1ll << 53)) {
+    T >>= 1;
+    e += 1;
+  } else if (T < (1ll << 52)) {
+    T <<= 1;
+    e -= 1;
+  }
+  return __longlong_as_double((long long)(((uint64_t)(bh & 0x80000000u) << 32) | ((uint64_t)(e - 127 + 1023) << 52) |
+                                          ((uint64_t)T & 0xFFFFFFFFFFFFFull)));
+}
+
 __device__ __forceinline__ float pow2f(int e) {
   // 2^e for -126 <= e <= 127
   return __uint_as_float((uint32_t)(e + 127) << 23);

@@ -69,16 +69,19 @@ __device__ __forceinline__ df::F2 ld2(const float2* p) {
 }
 
 // z-marching residual: a block covers a 32 (x) x 8 (y) tile of columns and a
-// range of planes; each thread keeps x at k-1, k, k+1 in registers, reuses the
-// z difference of the previous plane and gets the x difference of its left
-// neighbour by shuffle.  Work per block is fixed, so the reduction order is too.
+// range of planes; each thread keeps x at k-1, k, k+1 in registers (the loads
+// of the next plane are issued before the current one is computed) and reuses
+// the exact z difference of the face below from the previous plane.  Work per
+// block is fixed, so the reduction order is too.
 //
 // Arithmetic: x = xh + xl (double-float).  With the flux weights already
 // multiplied by lambda (w' = lambda w, double-float), lambda L x = L'xh + L'xl;
 // L'xh is formed exactly term by term (two-difference of the float values, FMA
-// two-product with the double-float weight, two-sum accumulation with the low
-// parts deferred) and L'xl in plain FP32 (it is 2^-24 smaller).  The residual
-// is b - sigma x + lambda L x with sigma in {0, 1}.
+// two-product with the double-float weight) and summed with two-sum, the
+// rounding errors and low parts deferred to an FP32 companion; L'xl is plain
+// FP32 (it is 2^-24 smaller).  b and -sigma x enter the same accumulator, and
+// the FP32 residual is its rounded value: r is stored in FP32, so only the
+// cancellation inside the sum needs the extra precision.
 constexpr int kResTX = 32, kResTY = 8, kResZChunk = 16;
 
 struct Acc {
@@ -92,16 +95,29 @@ __device__ __forceinline__ void acc_add(Acc& s, float ph, float pl) {
   s.h = t;
 }
 
-// s += w * (a - c) for float a, c (exact difference) and double-float w
-__device__ __forceinline__ void acc_flux(Acc& s, float2 w, float a, float c) {
+// a - c = d + dl exactly (Knuth two-difference)
+struct Diff {
+  float d, dl;
+};
+
+__device__ __forceinline__ Diff two_diff(float a, float c) {
   const float d = a - c;
   const float bb = d - a;
-  const float dl = (a - (d - bb)) - (c + bb);  // a - c = d + dl exactly
-  const float p = w.x * d;
-  const float e = fmaf(w.x, d, -p) + fmaf(w.x, dl, w.y * d);
+  return Diff{d, (a - (d - bb)) - (c + bb)};
+}
+
+// s += w * (d + dl) for a double-float weight w
+__device__ __forceinline__ void acc_flux(Acc& s, float2 w, Diff t) {
+  const float p = w.x * t.d;
+  const float e = fmaf(w.x, t.d, -p) + fmaf(w.x, t.dl, w.y * t.d);
   acc_add(s, p, e);
 }
 
+// SIG: 0 sigma = 0, 1 sigma = 1, 2 general sigma.  LO: x has a low part (false
+// after the first solve, whose output is exactly FP32).  MEAN: singular
+// problem (b minus its mean, volume-weighted sums of x).  OUT: write the FP64
+// solution.
+template <int SIG, bool LO, bool MEAN, bool OUT>
 __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const int* __restrict__ skip) {
   if (skip && *skip) return;
   __shared__ double sh[4 * kResTY];
@@ -112,101 +128,132 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const
   const int k0 = blockIdx.z * kResZChunk, k1 = min(nz, k0 + kResZChunk);
   const bool act = i < nx && j < ny;
   const int ic = min(i, nx - 1), jc = min(j, ny - 1);
-  df::F2 mean = df::make(0.f, 0.f);
-  if (a.sub_mean) mean = df::from_f64(a.st->mean_b);
-  const int sig_mode = a.sig_mode;  // 0: sigma = 0, 1: sigma = 1, 2: other
-  // lambda-scaled weights (see mixed_field_solve)
+  float mean_h = 0.f, mean_l = 0.f;
+  if (MEAN) {
+    const df::F2 mb = df::from_f64(a.st->mean_b);
+    mean_h = -mb.hi;
+    mean_l = -mb.lo;
+  }
   const float2 wpx = a.wp[0][ic], wmx = a.wm[0][ic], wpy = a.wp[1][jc], wmy = a.wm[1][jc];
-  const df::F2 w0xy = df::add(ld2(a.w0[0] + ic), ld2(a.w0[1] + jc));
+  const float2 w0x = a.w0[0][ic], w0y = a.w0[1][jc];
+  const bool wall_xy = w0x.x != 0.f || w0y.x != 0.f;
   df::F2 Vxy = df::make(0.f, 0.f);
-  if (a.want_mean) Vxy = df::mul(ld2(a.m[0] + ic), ld2(a.m[1] + jc));
+  if (MEAN) Vxy = df::mul(ld2(a.m[0] + ic), ld2(a.m[1] + jc));
   const bool hx = i + 1 < nx, lx = i > 0, hy = j + 1 < ny, ly = j > 0;
+  const bool ex = lane == kResTX - 1 && hx, wx = lane == 0 && lx;
   float srr = 0.f, sbb = 0.f, rmax = 0.f;
   df::F2 svb = df::make(0.f, 0.f), sv = df::make(0.f, 0.f);
-  const long long col = (long long)jc * nx + ic;
   const float2 z2 = make_float2(0.f, 0.f);
-  // software pipeline: the loads of plane k+1 (and of x at k+2) are issued
-  // before plane k is computed
+  const long long col = (long long)jc * nx + ic;
+  const float2* xq = a.x + (long long)k0 * sz + col;
+  const double* bq = a.b + (long long)k0 * sz + col;
+  float* rq = a.r + ((long long)k0 * ny + jc) * a.r_pitch + ic;
+  const long long rstep = (long long)ny * a.r_pitch;
+  double* oq = OUT ? a.out + (long long)k0 * sz + col : nullptr;
+  const float2* wpz = a.wp[2];
+  const float2* wmz = a.wm[2];
+  const float2* w0z = a.w0[2];
+  // pipeline registers: values of plane k and the loads of plane k+1
   float2 xc = z2, xm = z2, xp = z2, xn = z2, xs = z2;
   double bnow = 0.0;
   if (k0 < k1) {
-    const long long p0 = (long long)k0 * sz + col;
-    xc = a.x[p0];
-    if (k0 > 0) xm = a.x[p0 - sz];
-    if (k0 + 1 < nz) xp = a.x[p0 + sz];
-    xn = hy ? a.x[p0 + sy] : xc;
-    xs = ly ? a.x[p0 - sy] : xc;
-    bnow = act ? a.b[p0] : 0.0;
+    xc = xq[0];
+    if (k0 > 0) xm = xq[-sz];
+    if (k0 + 1 < nz) xp = xq[sz];
+    xn = hy ? xq[sy] : xc;
+    xs = ly ? xq[-sy] : xc;
+    bnow = bq[0];
   }
+  // exact z difference of the face below plane k (x_{k-1} - x_k)
+  Diff dzm = two_diff(xm.x, xc.x);
+#pragma unroll 2
   for (int k = k0; k < k1; ++k) {
-    const long long p = (long long)k * sz + col;
     float2 xp2 = z2, xn2 = z2, xs2 = z2;
     double bnext = 0.0;
     if (k + 1 < k1) {
-      if (k + 2 < nz) xp2 = a.x[p + 2 * sz];
-      xn2 = hy ? a.x[p + sz + sy] : xp;
-      xs2 = ly ? a.x[p + sz - sy] : xp;
-      bnext = act ? a.b[p + sz] : 0.0;
+      if (k + 2 < nz) xp2 = xq[2 * sz];
+      xn2 = hy ? xq[sz + sy] : xp;
+      xs2 = ly ? xq[sz - sy] : xp;
+      bnext = bq[sz];
     }
-    df::F2 bb = act ? df::from_f64(bnow) : df::make(0.f, 0.f);
-    if (a.want_mean && act) {
-      const df::F2 V = df::mul(Vxy, ld2(a.m[2] + k));
-      svb = df::add(svb, df::mul(V, df::make(xc.x, xc.y)));
-      sv = df::add(sv, V);
-    }
-    if (a.sub_mean) bb = df::sub(bb, mean);
-    // x neighbours by shuffle (lanes at the block edge load them)
     float2 xe, xw;
     xe.x = __shfl_down_sync(0xffffffffu, xc.x, 1);
     xe.y = __shfl_down_sync(0xffffffffu, xc.y, 1);
     xw.x = __shfl_up_sync(0xffffffffu, xc.x, 1);
     xw.y = __shfl_up_sync(0xffffffffu, xc.y, 1);
-    if (lane == kResTX - 1 && hx) xe = a.x[p + 1];
-    if (lane == 0 && lx) xw = a.x[p - 1];
-    Acc S{0.f, 0.f};
+    if (ex) xe = xq[1];
+    if (wx) xw = xq[-1];
+    const df::F2 bb = df::from_f64(bnow);
+    Acc S{bb.hi, bb.lo};
+    if (MEAN) acc_add(S, mean_h, mean_l);
+    if (MEAN && act) {
+      const df::F2 V = df::mul(Vxy, ld2(a.m[2] + k));
+      svb = df::add(svb, df::mul(V, df::make(xc.x, xc.y)));
+      sv = df::add(sv, V);
+    }
     float sl = 0.f;  // lambda L applied to the low parts, FP32
-    const float2 wpz = a.wp[2][k], wmz = a.wm[2][k];
-    if (hx) { acc_flux(S, wpx, xe.x, xc.x); sl = fmaf(wpx.x, xe.y - xc.y, sl); }
-    if (lx) { acc_flux(S, wmx, xw.x, xc.x); sl = fmaf(wmx.x, xw.y - xc.y, sl); }
-    if (hy) { acc_flux(S, wpy, xn.x, xc.x); sl = fmaf(wpy.x, xn.y - xc.y, sl); }
-    if (ly) { acc_flux(S, wmy, xs.x, xc.x); sl = fmaf(wmy.x, xs.y - xc.y, sl); }
-    if (k + 1 < nz) { acc_flux(S, wpz, xp.x, xc.x); sl = fmaf(wpz.x, xp.y - xc.y, sl); }
-    if (k > 0) { acc_flux(S, wmz, xm.x, xc.x); sl = fmaf(wmz.x, xm.y - xc.y, sl); }
-    const df::F2 w0 = df::add(w0xy, ld2(a.w0[2] + k));
-    if (w0.hi != 0.f) {  // wall term: only next to a Dirichlet wall
+    const Diff dzp = two_diff(xp.x, xc.x);
+    if (hx) acc_flux(S, wpx, two_diff(xe.x, xc.x));
+    if (lx) acc_flux(S, wmx, two_diff(xw.x, xc.x));
+    if (hy) acc_flux(S, wpy, two_diff(xn.x, xc.x));
+    if (ly) acc_flux(S, wmy, two_diff(xs.x, xc.x));
+    if (k + 1 < nz) acc_flux(S, wpz[k], dzp);
+    if (k > 0) acc_flux(S, wmz[k], dzm);
+    if (LO) {
+      if (hx) sl = fmaf(wpx.x, xe.y - xc.y, sl);
+      if (lx) sl = fmaf(wmx.x, xw.y - xc.y, sl);
+      if (hy) sl = fmaf(wpy.x, xn.y - xc.y, sl);
+      if (ly) sl = fmaf(wmy.x, xs.y - xc.y, sl);
+      if (k + 1 < nz) sl = fmaf(wpz[k].x, xp.y - xc.y, sl);
+      if (k > 0) sl = fmaf(wmz[k].x, xm.y - xc.y, sl);
+    }
+    const float2 w0k = w0z[k];
+    if (wall_xy || w0k.x != 0.f) {  // wall term: only next to a Dirichlet wall
+      const df::F2 w0 = df::add(df::add(df::make(w0x.x, w0x.y), df::make(w0y.x, w0y.y)), df::make(w0k.x, w0k.y));
       const df::F2 t = df::mul(w0, df::make(xc.x, xc.y));
       acc_add(S, t.hi, t.lo);
     }
-    S.l += sl;
-    df::F2 r = df::add(bb, df::fast_two_sum(S.h, S.l));
-    if (sig_mode == 1)
-      r = df::sub(r, df::make(xc.x, xc.y));
-    else if (sig_mode == 2)
-      r = df::sub(r, df::mul(df::make(a.sigma.x, a.sigma.y), df::make(xc.x, xc.y)));
+    if (SIG == 1) {
+      acc_add(S, -xc.x, -xc.y);
+    } else if (SIG == 2) {
+      const df::F2 t = df::mul(df::make(a.sigma.x, a.sigma.y), df::make(xc.x, xc.y));
+      acc_add(S, -t.hi, -t.lo);
+    }
+    const float rf = S.h + (S.l + sl);
     if (act) {
-      if (a.out) a.out[p] = df::to_f64(df::make(xc.x, xc.y));
-      const float rf = r.hi + r.lo;
-      a.r[((long long)k * ny + j) * a.r_pitch + i] = rf;
+      if (OUT) *oq = df::to_f64_bits(df::make(xc.x, xc.y));
+      *rq = rf;
       srr = fmaf(rf, rf, srr);
-      sbb = fmaf(bb.hi, bb.hi, sbb);
+      sbb = MEAN ? fmaf(bb.hi + mean_h, bb.hi + mean_h, sbb) : fmaf(bb.hi, bb.hi, sbb);
       rmax = fmaxf(rmax, fabsf(rf));
     }
+    dzm = Diff{-dzp.d, -dzp.dl};
     xm = xc;
     xc = xp;
     xp = xp2;
     xn = xn2;
     xs = xs2;
     bnow = bnext;
+    xq += sz;
+    bq += sz;
+    rq += rstep;
+    if (OUT) oq += sz;
   }
-  double v[4] = {(double)srr, (double)sbb, df::to_f64(svb), df::to_f64(sv)};
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+    srr += __shfl_down_sync(0xffffffffu, srr, o);
+    sbb += __shfl_down_sync(0xffffffffu, sbb, o);
     rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    if (MEAN) {
+      svb = df::add(svb, df::make(__shfl_down_sync(0xffffffffu, svb.hi, o), __shfl_down_sync(0xffffffffu, svb.lo, o)));
+      sv = df::add(sv, df::make(__shfl_down_sync(0xffffffffu, sv.hi, o), __shfl_down_sync(0xffffffffu, sv.lo, o)));
+    }
   }
   if (lane == 0) {
-    for (int q = 0; q < 4; ++q) sh[4 * wy + q] = v[q];
+    sh[4 * wy + 0] = (double)srr;
+    sh[4 * wy + 1] = (double)sbb;
+    sh[4 * wy + 2] = MEAN ? df::to_f64(svb) : 0.0;
+    sh[4 * wy + 3] = MEAN ? df::to_f64(sv) : 0.0;
     if (rmax > 0.f) atomicMax(reinterpret_cast<unsigned int*>(a.rmax), __float_as_uint(rmax));
   }
   __syncthreads();
@@ -216,6 +263,46 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const
       for (int c = 0; c < 4; ++c) t[c] += sh[4 * q + c];
     const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     for (int c = 0; c < 4; ++c) a.partials[4 * bid + c] = t[c];
+  }
+}
+
+using ResidKernel = void (*)(ResidArgs, const int*);
+
+template <int SIG, bool LO>
+ResidKernel resid_kernel_mo(bool mean, bool out) {
+  if (mean) return out ? k_resid_df<SIG, LO, true, true> : k_resid_df<SIG, LO, true, false>;
+  return out ? k_resid_df<SIG, LO, false, true> : k_resid_df<SIG, LO, false, false>;
+}
+
+ResidKernel resid_kernel(int sig_mode, bool lo, bool mean, bool out) {
+  if (sig_mode == 0) return lo ? resid_kernel_mo<0, true>(mean, out) : resid_kernel_mo<0, false>(mean, out);
+  if (sig_mode == 1) return lo ? resid_kernel_mo<1, true>(mean, out) : resid_kernel_mo<1, false>(mean, out);
+  return lo ? resid_kernel_mo<2, true>(mean, out) : resid_kernel_mo<2, false>(mean, out);
+}
+
+// FP64 solution from the double-float accumulator (minus the volume-weighted
+// mean for the zero-flux Laplace problem).  Runs only when the last residual
+// pass, which writes the output itself, was skipped (or for singular problems).
+__global__ void k_finalize_out(const float2* __restrict__ x, double* __restrict__ out, long long P,
+                               const DevStatus* __restrict__ st, int max_refine, int singular) {
+  if (!singular && st->refine_steps >= max_refine) return;
+  df::F2 mu = df::make(0.f, 0.f);
+  if (singular) mu = df::from_f64(st->scal[0]);
+  const long long stride = (long long)gridDim.x * blockDim.x * 2;
+  for (long long p = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 2; p < P; p += stride) {
+    if (p + 1 < P) {
+      const float4 v = *reinterpret_cast<const float4*>(x + p);
+      df::F2 u0 = df::make(v.x, v.y), u1 = df::make(v.z, v.w);
+      if (singular) {
+        u0 = df::sub(u0, mu);
+        u1 = df::sub(u1, mu);
+      }
+      *reinterpret_cast<double2*>(out + p) = make_double2(df::to_f64_bits(u0), df::to_f64_bits(u1));
+    } else {
+      df::F2 u0 = df::make(x[p].x, x[p].y);
+      if (singular) u0 = df::sub(u0, mu);
+      out[p] = df::to_f64_bits(u0);
+    }
   }
 }
 
@@ -342,13 +429,6 @@ __global__ void k_finish_mixed(const double* __restrict__ partials, int nblocks,
   } else {
     st->done = rel <= tol ? 1 : 0;
   }
-}
-
-// remove the volume-weighted mean of the FP64 solution (zero-flux Laplace)
-__global__ void k_sub_mean(double* __restrict__ out, long long P, const DevStatus* __restrict__ st) {
-  const double mu = st->scal[0];
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x)
-    out[p] -= mu;
 }
 
 struct Thomas32Args {
@@ -762,7 +842,8 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     t.out_df = p->xdf;
     t.scale_out = nullptr;
     FDI_TRY(launch_tc_transform(p, mx->bwd, t, round == 0 ? "transform_xb_set_tc" : "transform_xb_add_tc", s));
-    // residual of the updated solution, FP64 output, convergence check
+    // residual of the updated solution and convergence check; the pass of the
+    // last possible round also writes the FP64 solution
     {
       FDI_KTIMER(p, "residual_df", s);
       ResidArgs ak = ra;
@@ -771,7 +852,9 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
       ak.sub_mean = singular ? 1 : 0;
       ak.want_mean = singular ? 1 : 0;
       ak.rmax = sc_next + 0;
-      k_resid_df<<<rgrid, dim3(kResTX, kResTY), 0, s>>>(ak, skip);
+      const bool write_out = !singular && round == p->max_refine;
+      ResidKernel kern = resid_kernel(ra.sig_mode, round > 0, singular, write_out);
+      kern<<<rgrid, dim3(kResTX, kResTY), 0, s>>>(ak, skip);
       FDI_LAUNCH_CHECK(p);
     }
     {
@@ -781,11 +864,13 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
       FDI_LAUNCH_CHECK(p);
     }
   }
-  if (singular) {
-    // the FP32 sweep projects the null line only to single precision; the
-    // constant is outside the range of A, so shifting it leaves the residual
-    FDI_KTIMER(p, "mean_f64", s);
-    k_sub_mean<<<kBlocks, kThreads, 0, s>>>(out, f.P, p->d_status);
+  {
+    // FP64 output when the loop stopped before its last round (and, for the
+    // zero-flux Laplace problem, minus the volume-weighted mean: the FP32 sweep
+    // projects the null line only to single precision, and the constant is
+    // outside the range of A, so shifting it leaves the residual)
+    FDI_KTIMER(p, "finalize_out", s);
+    k_finalize_out<<<kBlocks, kThreads, 0, s>>>(p->xdf, out, f.P, p->d_status, p->max_refine, singular ? 1 : 0);
     FDI_LAUNCH_CHECK(p);
   }
   return FDI_OK;
