@@ -163,9 +163,11 @@ def kernel_model(name, n, steps, K):
         "transform_xb_set_tc": ("hbm", 12.0 * P, "byte", K),
         "transform_xb_add_tc": ("hbm", 20.0 * P, "byte", steps * K),
         "thomas_z_f32": ("hbm", 8.0 * P, "byte", rounds * K),
-        "residual_df": ("hbm", 20.0 * P, "byte", rounds * K),
+        # x and b read, r written; refinement-round passes also write the FP64 output
+        "residual_df": ("hbm", (20.0 + 8.0 * steps / rounds) * P, "byte", rounds * K),
         "residual_df_init": ("hbm", 12.0 * P, "byte", K),
-        "finalize_out": ("hbm", 16.0 * P, "byte", K),
+        # converts the output only when no refinement round ran
+        "finalize_out": ("hbm", 16.0 * P, "byte", K if steps == 0 else 0),
     }
     return t.get(name)
 
@@ -347,6 +349,8 @@ def main():
         if km is None:
             continue
         bound, units, kind, useful = km
+        if useful <= 0:
+            continue  # launched but returned at once
         useful = max(1, min(cnt, useful))
         avg_s = tot_ms * 1e-3 / useful
         if kind == "flop":

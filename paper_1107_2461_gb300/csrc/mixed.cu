@@ -281,11 +281,12 @@ ResidKernel resid_kernel(int sig_mode, bool lo, bool mean, bool out) {
 }
 
 // FP64 solution from the double-float accumulator (minus the volume-weighted
-// mean for the zero-flux Laplace problem).  Runs only when the last residual
-// pass, which writes the output itself, was skipped (or for singular problems).
+// mean for the zero-flux Laplace problem).
 __global__ void k_finalize_out(const float2* __restrict__ x, double* __restrict__ out, long long P,
                                const DevStatus* __restrict__ st, int max_refine, int singular) {
-  if (!singular && st->refine_steps >= max_refine) return;
+  // refinement passes write the output themselves: only convergence in round 0
+  // (no refinement step taken) and the singular problem need this pass
+  if (!singular && (st->refine_steps > 0 || max_refine == 0)) return;
   df::F2 mu = df::make(0.f, 0.f);
   if (singular) mu = df::from_f64(st->scal[0]);
   const long long stride = (long long)gridDim.x * blockDim.x * 2;
@@ -446,92 +447,138 @@ struct Thomas32Args {
   float* fmax;
 };
 
-constexpr int kTB = 16;  // Thomas checkpoint / prefetch block
+constexpr int kTB = 16;   // Thomas block of planes: c' checkpoint interval and copy group
+constexpr int kTL = 128;  // Thomas lines per CTA (one thread per line)
+constexpr int kNBR = 3;   // blocks of kTB planes in flight per line
+
+// single-instruction reciprocal (PTX rcp.approx, at most 1 ulp): the sweep
+// only needs FP32 accuracy, the refinement restores the rest
+__device__ __forceinline__ float rcp_fast(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 
 // one elimination step of the z sweep: c'_k and d'_k from c'_{k-1}, d'_{k-1}
 __device__ __forceinline__ void thomas_step(float s, float m, float lkd, float lo, float up, float f, float& cp,
                                             float& dp) {
   const float di = fmaf(s, m, -lkd);
-  const float inv = __frcp_rn(fmaf(-lo, cp, di));
+  const float inv = rcp_fast(fmaf(-lo, cp, di));
   cp = up * inv;
   dp = fmaf(m, f, -lo * dp) * inv;
 }
 
-__global__ void __launch_bounds__(128) k_thomas_f32(Thomas32Args a, const int* __restrict__ skip) {
+// per-thread asynchronous 4-byte copies global -> shared (each thread reads
+// back only its own slots, so completion is tracked per thread by groups)
+__device__ __forceinline__ void cp_async4(unsigned dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// FULL: nz is a multiple of kTB (no partial block of planes)
+template <bool FULL>
+__global__ void __launch_bounds__(kTL) k_thomas_f32(Thomas32Args a, const int* __restrict__ skip) {
   if (skip && *skip) return;
-  // coefficients of the z operator (M, lambda*K) in shared memory
+  // coefficients of the z operator in shared memory: {M_k, lambda Kd_k,
+  // lower, upper} with the off-diagonals negated (lambda-scaled), and the
+  // per-thread ring of planes in flight and c' checkpoints
+  __shared__ float4 s_co[kMaxN];
   __shared__ float s_m[kMaxN], s_lkd[kMaxN], s_lko[kMaxN + 1];
+  __shared__ float ring[kNBR * kTB][kTL];
+  __shared__ float ckp[kMaxN / kTB][kTL];
   const int nz = a.nz;
   const float lam = (float)a.lambda;
   for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+    const float lko_k = (k + 1 < nz) ? lam * a.koz[k] : 0.f;
+    const float lko_m = (k > 0) ? lam * a.koz[k - 1] : 0.f;
+    s_co[k] = make_float4(a.mz[k], lam * a.kdz[k], -lko_m, -lko_k);
     s_m[k] = a.mz[k];
     s_lkd[k] = lam * a.kdz[k];
-    s_lko[k] = (k + 1 < nz) ? lam * a.koz[k] : 0.f;
+    s_lko[k] = lko_k;
   }
   __syncthreads();
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int tid = threadIdx.x;
+  const long long t = (long long)blockIdx.x * blockDim.x + tid;
   float vmax = 0.f;
   if (t < (long long)a.nx * a.ny) {
     const int i = (int)(t / a.ny), j = (int)(t % a.ny);
-    const long long pl = a.plane;
+    const int pl = (int)a.plane;  // plane stride in elements (< 2^31 / kMaxN)
     const double lab = a.lamx[i] + a.lamy[j];
     const float s = (float)(a.sigma - a.lambda * lab);
     float* f = a.f + (long long)i * a.pitch + j;
     if (!(a.singular_possible && lab == 0.0)) {
-      // forward elimination in blocks of kTB: loads of a block issued together,
-      // d'_k stored in place, c'_{k0-1} kept at each block start (checkpoint)
-      float ckp[kMaxN / kTB];
-      float cp = 0.f, dp = 0.f;
       const int nb = (nz + kTB - 1) / kTB;
-      for (int b = 0; b < nb; ++b) {
-        const int k0 = b * kTB;
-        ckp[b] = cp;
-        float fv[kTB];
+      const unsigned ring0 = (unsigned)__cvta_generic_to_shared(&ring[0][tid]);
+      // request block b of planes into its ring slot (one copy group per block)
+      auto fetch = [&](int b) {
+        if (b >= 0 && b < nb) {
+          const unsigned dst = ring0 + (unsigned)((b % kNBR) * kTB * kTL * 4);
+          const float* src = f + (long long)b * kTB * pl;
+          const int cnt = FULL ? kTB : min(kTB, nz - b * kTB);
 #pragma unroll
-        for (int e = 0; e < kTB; ++e) fv[e] = (k0 + e < nz) ? f[(k0 + e) * pl] : 0.f;
+          for (int e = 0; e < kTB; ++e)
+            if (FULL || e < cnt) cp_async4(dst + e * kTL * 4, src + e * pl);
+        }
+        cp_async_commit();
+      };
+      // forward elimination: d'_k stored in place, c'_{k-1} kept at each block start
+      for (int q = 0; q < kNBR - 1; ++q) fetch(q);
+      float cp = 0.f, dp = 0.f;
+      for (int b = 0; b < nb; ++b) {
+        fetch(b + kNBR - 1);
+        cp_async_wait<kNBR - 1>();
+        ckp[b][tid] = cp;
+        const float* rs = &ring[(b % kNBR) * kTB][tid];
+        float* fo = f + (long long)b * kTB * pl;
+        const int k0 = b * kTB;
 #pragma unroll
         for (int e = 0; e < kTB; ++e) {
-          const int k = k0 + e;
-          if (k < nz) {
-            const float lo = k > 0 ? -s_lko[k - 1] : 0.f;
-            thomas_step(s, s_m[k], s_lkd[k], lo, -s_lko[k], fv[e], cp, dp);
-            fv[e] = dp;
+          if (FULL || k0 + e < nz) {
+            const float4 co = s_co[k0 + e];
+            const float inv = rcp_fast(fmaf(-co.z, cp, fmaf(s, co.x, -co.y)));
+            cp = co.w * inv;
+            dp = fmaf(co.x, rs[e * kTL], -co.z * dp) * inv;
+            fo[e * pl] = dp;
           }
         }
-#pragma unroll
-        for (int e = 0; e < kTB; ++e)
-          if (k0 + e < nz) f[(k0 + e) * pl] = fv[e];
       }
-      // back substitution block by block from the top, c'_k recomputed from
-      // the checkpoint with the same operations (bit-identical)
+      cp_async_wait<0>();
+      // back substitution from the top, streaming d' block by block in
+      // reverse; c'_k is recomputed from the checkpoint with the same
+      // operations (bit-identical).  The top plane has c' = 0 (no upper
+      // neighbour), so u_{nz-1} = d'_{nz-1} falls out of the same update.
+      for (int q = 0; q < kNBR - 1; ++q) fetch(nb - 1 - q);
       float u = 0.f;
       for (int b = nb - 1; b >= 0; --b) {
+        fetch(b - (kNBR - 1));
         const int k0 = b * kTB;
-        float cpb[kTB], dv[kTB];
-        float c = ckp[b], d = 0.f;
+        float cpb[kTB];
+        float c = ckp[b][tid];
 #pragma unroll
         for (int e = 0; e < kTB; ++e) {
-          const int k = k0 + e;
-          dv[e] = (k < nz) ? f[k * pl] : 0.f;
-          if (k < nz) {
-            const float lo = k > 0 ? -s_lko[k - 1] : 0.f;
-            thomas_step(s, s_m[k], s_lkd[k], lo, -s_lko[k], 0.f, c, d);
+          if (FULL || k0 + e < nz) {
+            const float4 co = s_co[k0 + e];
+            c = co.w * rcp_fast(fmaf(-co.z, c, fmaf(s, co.x, -co.y)));
           }
           cpb[e] = c;
         }
+        cp_async_wait<kNBR - 1>();
+        const float* rs = &ring[(b % kNBR) * kTB][tid];
+        float* fo = f + (long long)k0 * pl;
 #pragma unroll
         for (int e = kTB - 1; e >= 0; --e) {
-          const int k = k0 + e;
-          if (k < nz) {
-            u = (k == nz - 1) ? dv[e] : fmaf(-cpb[e], u, dv[e]);
-            dv[e] = u;
+          if (FULL || k0 + e < nz) {
+            u = fmaf(-cpb[e], u, rs[e * kTL]);
+            fo[e * pl] = u;
             vmax = fmaxf(vmax, fabsf(u));
           }
         }
-#pragma unroll
-        for (int e = 0; e < kTB; ++e)
-          if (k0 + e < nz) f[(k0 + e) * pl] = dv[e];
       }
+      cp_async_wait<0>();
     } else {
       // singular line of the zero-flux Laplacian: project, pin u_0 = 0, solve, re-centre
       float* cs = a.cs + (long long)i * a.pitch + j;
@@ -813,7 +860,10 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
       ta.singular_possible = singular ? 1 : 0;
       ta.fmax = sc + 2;
       const long long lines = (long long)nx * ny;
-      k_thomas_f32<<<(unsigned)((lines + 127) / 128), 128, 0, s>>>(ta, skip);
+      if (nz % kTB == 0)
+        k_thomas_f32<true><<<(unsigned)((lines + kTL - 1) / kTL), kTL, 0, s>>>(ta, skip);
+      else
+        k_thomas_f32<false><<<(unsigned)((lines + kTL - 1) / kTL), kTL, 0, s>>>(ta, skip);
       FDI_LAUNCH_CHECK(p);
     }
     // back y: F2 [z][i][j] -> F4 [z][y][i]
@@ -852,7 +902,10 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
       ak.sub_mean = singular ? 1 : 0;
       ak.want_mean = singular ? 1 : 0;
       ak.rmax = sc_next + 0;
-      const bool write_out = !singular && round == p->max_refine;
+      // the FP64 solution is written by every refinement-round pass (the first
+      // solve alone essentially never meets the tolerance); the finalize pass
+      // covers convergence in round 0 and the zero-flux Laplace problem
+      const bool write_out = !singular && (round > 0 || p->max_refine == 0);
       ResidKernel kern = resid_kernel(ra.sig_mode, round > 0, singular, write_out);
       kern<<<rgrid, dim3(kResTX, kResTY), 0, s>>>(ak, skip);
       FDI_LAUNCH_CHECK(p);
