@@ -17,13 +17,16 @@
 // [2*N_pad][K_pad] (row k scaled by its own power of two, undone per output
 // column in the epilogue) and streamed by TMA.
 //
-// Warp roles of the persistent CTA (one per SM, 448 threads):
+// Warp roles of the persistent CTA (one per SM, 480 threads):
 //   warp 0      TMA producer of the B chunks
 //   warp 1      TMEM allocator and single-thread MMA issuer
-//   warps 2-9   converters: load FP32 rows of A, scale, split to fp16 hi/lo,
-//               store them in the 128-byte swizzled K-major layout
+//   warps 2-9   converters: read FP32 rows of A from shared memory, scale,
+//               split to fp16 hi/lo, store them in the 64-byte swizzled
+//               K-major layout of the MMA stage
 //   warps 10-13 epilogue: TMEM -> registers -> unscale -> global store
-// Two shared-memory stages of K = 64, two TMEM accumulators of N_pad columns.
+//   warp 14     TMA producer of the FP32 A chunks (128 rows x 32 columns)
+// Three MMA stages of K = 32, four FP32 A slots ahead of them (64 KB of input
+// in flight per SM), two TMEM accumulators of N_pad columns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -36,18 +39,26 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 32;                       // fp16 K per chunk: 64-byte rows, 64-byte swizzle
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;
+constexpr int NA32 = 4;                      // FP32 A slots (TMA, 128-byte swizzle)
 constexpr int NMAX = 256;
 constexpr int ROWB = BK * 2;                 // bytes per operand row in a stage
 constexpr int A_BYTES = BM * ROWB;           // one fp16 half of an A chunk: 8 KB
 constexpr int B_BYTES = NMAX * ROWB;         // one fp16 half of a B chunk: up to 16 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr int A32_BYTES = BM * BK * 4;      // 16 KB
 constexpr int NCONV = 8;
-constexpr int THREADS = 32 * (2 + NCONV + 4);
+constexpr int WARP_A = 2 + NCONV + 4;         // A producer warp
+constexpr int THREADS = 32 * (WARP_A + 1);
 constexpr int TP_BYTES = 4 * 32 * 33 * 4;     // epilogue transpose tiles, one per epilogue warp
 constexpr int BAR_BYTES = 256;
 constexpr int CS_BYTES = NMAX * 4;            // per-column unscale factors
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + BAR_BYTES + TP_BYTES + CS_BYTES;
+constexpr int A32_OFF = STAGES * STAGE_BYTES;
+constexpr int BAR_OFF = A32_OFF + NA32 * A32_BYTES;
+// the dynamic block starts 1024-byte aligned (the static block is padded to
+// 1024 bytes by the alignment of the extern declaration; checked at run time)
+constexpr int SMEM_BYTES = BAR_OFF + BAR_BYTES + TP_BYTES + CS_BYTES;
+static_assert(SMEM_BYTES + 1024 <= 232448, "shared memory budget");
 
 __device__ __forceinline__ float scale_from_max(float mx) {
   // power of two that maps mx into [2^14, 2^15): fp16 keeps 11 bits there and
@@ -65,19 +76,26 @@ __device__ __forceinline__ uint32_t pack_half2(__half a, __half b) {
 }
 
 template <int C>
-__global__ void __launch_bounds__(THREADS, 1) k_tc_transform(const __grid_constant__ CUtensorMap tmB, TcArgs a) {
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc_transform(const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmA, TcArgs a) {
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
-  // align by offsetting the shared array itself, so that every pointer below
-  // stays in the shared address space (shared loads/stores, no generic aliasing)
-  uint8_t* smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  // the swizzled layouts need a 1024-byte aligned base; the launch reserves no
+  // slack for re-alignment, so a misaligned block reports an error instead
+  if ((tc::smem_u32(smem_raw) & 1023u) != 0u) {
+    if (threadIdx.x == 0) atomicExch(a.err, 7);
+    return;
+  }
+  uint8_t* smem = smem_raw;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + BAR_OFF);
   uint64_t* full_b = bars;                  // B chunk landed (TMA transaction bytes)
   uint64_t* conv = bars + STAGES;           // A chunk converted (NCONV warp arrivals)
   uint64_t* empty = bars + 2 * STAGES;      // stage consumed by the MMAs (C commits)
   uint64_t* accf = bars + 3 * STAGES;       // accumulator complete
   uint64_t* acce = bars + 3 * STAGES + 2;   // accumulator drained by the epilogue
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * STAGES + 4);
+  uint64_t* a_full = bars + 3 * STAGES + 4;          // FP32 A chunk landed (TMA bytes)
+  uint64_t* a_empty = bars + 3 * STAGES + 4 + NA32;  // FP32 A chunk read (NCONV warp arrivals)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * STAGES + 4 + 2 * NA32);
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -96,11 +114,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_transform(const __grid_consta
       tc::mbar_init(&accf[b], 1);
       tc::mbar_init(&acce[b], 4);
     }
+    for (int b = 0; b < NA32; ++b) {
+      tc::mbar_init(&a_full[b], 1);
+      tc::mbar_init(&a_empty[b], NCONV);
+    }
     s_abort = 0;
     tc::fence_mbar_init();
   }
   if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmB);
-  float* s_cs = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + BAR_BYTES + TP_BYTES);
+  if (warp == WARP_A && lane == 0) tc::prefetch_tmap(&tmA);
+  float* s_cs = reinterpret_cast<float*>(smem + BAR_OFF + BAR_BYTES + TP_BYTES);
   for (int k = threadIdx.x; k < N_pad; k += blockDim.x) s_cs[k] = a.col_scale[k];
   if (warp == 1) {
     tc::tmem_alloc(tmem_slot, tmem_cols);
@@ -211,47 +234,41 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_transform(const __grid_consta
     }
   } else if (warp < 2 + NCONV) {
     // ---------------- converters ----------------
-    // Each thread owns 2 (row, 16-byte chunk) slots of a 128 x 32 A chunk; the
-    // global loads of the next chunk are issued before the current one is
-    // converted, so two chunks of loads are in flight per converter warp.
+    // Each thread owns 2 (row, 32-byte) slots of a 128 x 32 A chunk: it reads
+    // the FP32 values from the TMA slot (128-byte swizzle: 16-byte unit u of
+    // row r sits at unit u ^ (r & 7), conflict free), scales, splits and stores
+    // 16 fp16 hi and lo values into the MMA stage.
     const int ct = (warp - 2) * 32 + lane;  // 0..255
     const float sA = scale_from_max(a.scale_in ? *a.scale_in : 1.0f);
-    const int c8 = ct & 3;                  // 16-byte chunk within the 64-byte row
+    const int c8 = ct & 3;                  // 32-byte group within the 128-byte row
     const long long total = my_iters * nK;
-    auto load_chunk = [&](long long gi, float (&v)[2][8]) {
-      const long long it = gi / nK;
-      const int kc = (int)(gi % nK);
-      const long long tile = blockIdx.x + it * gridDim.x;
-      const long long row0 = tile * BM;
-      const int k0 = kc * BK + c8 * 8;
+    int kc = 0;
+    for (long long gi = 0; gi < total && !s_abort; ++gi) {
+      const uint32_t g = (uint32_t)gi;
+      const int sa = g % NA32;
+      const uint32_t pa = (g / NA32) & 1;
+      const int s = g % STAGES;
+      const uint32_t ph = (g / STAGES) & 1;
+      if (!tc::mbar_wait(&a_full[sa], pa, &s_abort)) {
+        atomicExch(a.err, 4);
+        break;
+      }
+      const uint8_t* src = smem + A32_OFF + sa * A32_BYTES;
+      float v[2][8];
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        const long long grow = row0 + (ct >> 2) + 64 * q;
-        float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f), x1 = x0;
-        if (tile < num_tiles && grow < a.R) {
-          const float* src = a.in + grow * (long long)a.in_pitch + k0;
-          if (k0 < a.in_pitch) x0 = __ldg(reinterpret_cast<const float4*>(src));
-          if (k0 + 4 < a.in_pitch) x1 = __ldg(reinterpret_cast<const float4*>(src + 4));
-        }
+        const int row = (ct >> 2) + 64 * q;
+        const float4 x0 = *reinterpret_cast<const float4*>(src + row * 128 + (((2 * c8) ^ (row & 7)) << 4));
+        const float4 x1 = *reinterpret_cast<const float4*>(src + row * 128 + (((2 * c8 + 1) ^ (row & 7)) << 4));
         v[q][0] = x0.x; v[q][1] = x0.y; v[q][2] = x0.z; v[q][3] = x0.w;
         v[q][4] = x1.x; v[q][5] = x1.y; v[q][6] = x1.z; v[q][7] = x1.w;
       }
-      // nothing here may consume the loaded registers: the K-tail mask is
-      // applied at conversion time so the load latency overlaps the wait
-    };
-    // three register buffers rotate: the loads of the next two chunks are in
-    // flight while the current one is converted
-    float v0[2][8], v1[2][8], v2[2][8];
-    auto convert_store = [&](long long gi, const float (&v)[2][8]) -> bool {
-      const uint32_t g = (uint32_t)gi;
-      const int s = g % STAGES;
-      const uint32_t ph = (g / STAGES) & 1;
       if (!tc::mbar_wait(&empty[s], ph ^ 1, &s_abort)) {
         atomicExch(a.err, 4);
-        return false;
+        break;
       }
       uint8_t* st = smem + s * STAGE_BYTES;
-      const int k0 = (int)(gi % nK) * BK + c8 * 8;
+      const int k0 = kc * BK + c8 * 8;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const int row = (ct >> 2) + 64 * q;
@@ -270,22 +287,34 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_transform(const __grid_consta
         *reinterpret_cast<uint4*>(st + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
         *reinterpret_cast<uint4*>(st + A_BYTES + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
+      // the FP32 values were consumed above: the slot may be refilled
       tc::fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&conv[s]);
-      return true;
-    };
-    if (total > 0) load_chunk(0, v0);
-    if (total > 1) load_chunk(1, v1);
-    for (long long gi = 0; gi < total && !s_abort; gi += 3) {
-      if (gi + 2 < total) load_chunk(gi + 2, v2);
-      if (!convert_store(gi, v0)) break;
-      if (gi + 1 >= total) break;
-      if (gi + 3 < total) load_chunk(gi + 3, v0);
-      if (!convert_store(gi + 1, v1)) break;
-      if (gi + 2 >= total) break;
-      if (gi + 4 < total) load_chunk(gi + 4, v1);
-      if (!convert_store(gi + 2, v2)) break;
+      if (lane == 0) {
+        tc::mbar_arrive(&a_empty[sa]);
+        tc::mbar_arrive(&conv[s]);
+      }
+      if (++kc == nK) kc = 0;
+    }
+  } else if (warp == WARP_A) {
+    // ---------------- TMA producer (FP32 A) ----------------
+    if (lane == 0) {
+      uint32_t g = 0;
+      for (long long it = 0; it < my_iters && !s_abort; ++it) {
+        const long long tile = blockIdx.x + it * gridDim.x;
+        const int row0 = (int)(tile * BM);
+        for (int kc = 0; kc < nK; ++kc, ++g) {
+          const int sa = g % NA32;
+          const uint32_t pa = (g / NA32) & 1;
+          if (!tc::mbar_wait(&a_empty[sa], pa ^ 1, &s_abort)) {
+            s_abort = 1;
+            atomicExch(a.err, 6);
+            break;
+          }
+          tc::mbar_expect_tx(&a_full[sa], (uint32_t)A32_BYTES);
+          tc::tma_load_2d(tc::smem_u32(smem + A32_OFF + sa * A32_BYTES), &tmA, kc * BK, row0, &a_full[sa]);
+        }
+      }
     }
   } else {
     // ---------------- epilogue ----------------
@@ -296,7 +325,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_transform(const __grid_consta
     // outputs) and stores them with one 16-byte access where the layout allows.
     const int q = warp & 3;  // TMEM lane quarter accessible to this warp
     const float inv_sA = 1.0f / scale_from_max(a.scale_in ? *a.scale_in : 1.0f);
-    float* tp = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + BAR_BYTES) + (warp - (2 + NCONV)) * (32 * 33);
+    float* tp = reinterpret_cast<float*>(smem + BAR_OFF + BAR_BYTES) + (warp - (2 + NCONV)) * (32 * 33);
     const bool rowmajor = a.mode != TC_OUT_F32 || a.col_stride == 1;
     // vector stores need 16-byte aligned groups of 4 along the contiguous index
     const bool vec_t = !rowmajor && a.row_stride == 1 && (a.S % 4 == 0) && (a.slab_stride % 4 == 0) &&
@@ -556,7 +585,8 @@ void tc_free_matrix(TcMatrix* m) {
 }
 
 template <int C>
-fdi_status launch_cluster(fdi_plan* p, const TcMatrix& m, const TcArgs& args, long long tiles, cudaStream_t s) {
+fdi_status launch_cluster(fdi_plan* p, const TcMatrix& m, const CUtensorMap& mapA, const TcArgs& args, long long tiles,
+                          cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
     FDI_CUDA_TRY(cudaFuncSetAttribute(k_tc_transform<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
@@ -581,7 +611,7 @@ fdi_status launch_cluster(fdi_plan* p, const TcMatrix& m, const TcArgs& args, lo
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  FDI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_transform<C>, map, args));
+  FDI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_transform<C>, map, mapA, args));
   FDI_LAUNCH_CHECK(p);
   return FDI_OK;
 }
@@ -592,10 +622,35 @@ fdi_status launch_tc_transform(fdi_plan* p, const TcMatrix& m, TcArgs args, cons
   args.nK = (args.K + BK - 1) / BK;
   args.col_scale = m.col_scale;
   const long long tiles = (args.R + BM - 1) / BM;
+  if (args.R > 0x7fffffffLL - BM || args.in_pitch % 4 != 0 || (reinterpret_cast<uintptr_t>(args.in) & 15u) != 0) {
+    set_error("transform input must be 16-byte aligned with a pitch multiple of 4 and fewer than 2^31 rows");
+    return FDI_ERR_INVALID_ARG;
+  }
+  // FP32 input rows as a 2D tensor [R][in_pitch]; 32 x 128 boxes, 128-byte swizzle;
+  // rows past R and columns past the pitch read as zero
+  auto enc = encode_fn();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled entry point unavailable");
+    return FDI_ERR_CUDA;
+  }
+  CUtensorMap mapA;
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)args.in_pitch, (cuuint64_t)args.R};
+    cuuint64_t strides[1] = {(cuuint64_t)args.in_pitch * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&mapA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(args.in), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      set_error("cuTensorMapEncodeTiled failed for a transform input");
+      return FDI_ERR_CUDA;
+    }
+  }
   switch (p->tc_cluster) {
-    case 2: return launch_cluster<2>(p, m, args, tiles, s);
-    case 4: return launch_cluster<4>(p, m, args, tiles, s);
-    default: return launch_cluster<1>(p, m, args, tiles, s);
+    case 2: return launch_cluster<2>(p, m, mapA, args, tiles, s);
+    case 4: return launch_cluster<4>(p, m, mapA, args, tiles, s);
+    default: return launch_cluster<1>(p, m, mapA, args, tiles, s);
   }
 }
 
