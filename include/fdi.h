@@ -199,6 +199,15 @@ fdi_status fdi_plan_set_transform_config(fdi_plan* plan, int cluster);
 fdi_status fdi_eigen_noalloc(const double* faces, int n, int face_kind, fdi_bc bc_lo, fdi_bc bc_hi, double* lam,
                              double* E, double* Einv, int* converged, fdi_stream_t stream);
 
+/* CUDA-graph replay of field solves (default on).  A Helmholtz / Laplace /
+ * field solve whose arguments (field, sigma, lambda, rhs, out, stream) repeat
+ * those of the previous call on this plan is captured into a CUDA graph on its
+ * second occurrence and replayed as one graph launch from then on; results are
+ * identical to the eager launch sequence.  The legacy default stream and plans
+ * with timing on always run eagerly.  Changing tolerances or the transform
+ * configuration drops the captured graph.  on: 0 off, nonzero on. */
+fdi_status fdi_plan_set_graphs(fdi_plan* plan, int on);
+
 /* Per-kernel device timing: with timing on, every kernel launch of this plan is
  * bracketed by a CUDA event pair on the launching stream. */
 fdi_status fdi_plan_enable_timing(fdi_plan* plan, int on);

@@ -99,6 +99,21 @@ struct fdi_plan {
   double last_res = 0.0;
   long long launches = 0;
   bool status_valid = false;
+  // CUDA graph of the field solve: a call that repeats the previous call's
+  // arguments (field, sigma, lambda, arrays, stream) is captured once and then
+  // replayed with a single graph launch
+  bool use_graphs = true;
+  struct GraphKey {
+    int field = -1;
+    double sigma = 0.0, lambda = 0.0;
+    const double* rhs = nullptr;
+    double* out = nullptr;
+    cudaStream_t s = nullptr;
+  };
+  GraphKey gkey;
+  bool gkey_valid = false;
+  cudaGraphExec_t gexec = nullptr;
+  long long glaunches = 0;
   // optional per-kernel device timing (CUDA events around each launch)
   bool timing = false;
   struct TimedLaunch { const char* name; cudaEvent_t e0, e1; };
@@ -141,6 +156,9 @@ struct KTimer {
   ~KTimer();
 };
 #define FDI_KTIMER(plan, name, stream) ::fdi::KTimer _kt_##__LINE__((plan), (name), (stream))
+
+// drop the captured solve graph (arguments or controls changed)
+void invalidate_graph(fdi_plan* p);
 
 // plan-time eigen decomposition of the symmetric tridiagonal M^{-1/2} K M^{-1/2}
 fdi_status eigen_decompose_all(const std::vector<Axis*>& axes, cudaStream_t s, int* d_err);

@@ -969,5 +969,6 @@ extern "C" fdi_status fdi_apply_transform(fdi_plan* plan, fdi_field field, int d
 extern "C" fdi_status fdi_plan_set_transform_config(fdi_plan* plan, int cluster) {
   if (!plan || (cluster != 1 && cluster != 2 && cluster != 4)) return FDI_ERR_INVALID_ARG;
   plan->tc_cluster = cluster;
+  fdi::invalidate_graph(plan);
   return FDI_OK;
 }

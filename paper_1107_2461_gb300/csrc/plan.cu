@@ -156,6 +156,7 @@ void free_axis(Axis* ax) {
 }
 
 void free_plan(fdi_plan* p) {
+  invalidate_graph(p);
   if (!p) return;
   for (auto& t : p->pending) {
     cudaEventDestroy(t.e0);
@@ -381,6 +382,7 @@ fdi_status fdi_plan_set_tolerances(fdi_plan* plan, double tol, int max_refine, d
       max_iters < 1)
     return FDI_ERR_INVALID_ARG;
   plan->tol = tol;
+  invalidate_graph(plan);
   plan->max_refine = max_refine;
   plan->ktol = krylov_tol;
   plan->kmaxit = max_iters;

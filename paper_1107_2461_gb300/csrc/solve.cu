@@ -101,6 +101,82 @@ fdi_status field_solve(fdi_plan* p, int field, double sigma, double lambda, cons
   return FDI_OK;
 }
 
+void invalidate_graph(fdi_plan* p) {
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  p->gexec = nullptr;
+  p->gkey_valid = false;
+  p->glaunches = 0;
+}
+
+namespace {
+
+bool same_key(const fdi_plan::GraphKey& a, const fdi_plan::GraphKey& b) {
+  return a.field == b.field && a.sigma == b.sigma && a.lambda == b.lambda && a.rhs == b.rhs && a.out == b.out &&
+         a.s == b.s;
+}
+
+// Field solve through the graph cache: the first call with new arguments runs
+// eagerly, the second identical call is captured (stream capture of the same
+// launch sequence) and every later identical call is one graph launch.  The
+// legacy default stream cannot be captured and timed plans need their events,
+// so both run eagerly.
+fdi_status field_solve_entry(fdi_plan* p, int field, double sigma, double lambda, const double* rhs, double* out,
+                             cudaStream_t s) {
+  if (!p) return FDI_ERR_INVALID_ARG;
+  p->launches = 0;
+  if (!p->use_graphs || p->timing || s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread)
+    return field_solve(p, field, sigma, lambda, rhs, out, s);
+  fdi_plan::GraphKey key;
+  key.field = field;
+  key.sigma = sigma;
+  key.lambda = lambda;
+  key.rhs = rhs;
+  key.out = out;
+  key.s = s;
+  if (p->gkey_valid && same_key(key, p->gkey) && p->gexec) {
+    FDI_CUDA_TRY(cudaGraphLaunch(p->gexec, s));
+    p->launches = p->glaunches;
+    return FDI_OK;
+  }
+  if (!p->gkey_valid || !same_key(key, p->gkey)) {
+    invalidate_graph(p);
+    fdi_status st = field_solve(p, field, sigma, lambda, rhs, out, s);
+    if (st == FDI_OK) {
+      p->gkey = key;
+      p->gkey_valid = true;
+    }
+    return st;
+  }
+  // second call with these arguments: capture, instantiate, launch
+  FDI_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  fdi_status st = field_solve(p, field, sigma, lambda, rhs, out, s);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (st != FDI_OK || e != cudaSuccess || g == nullptr) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    invalidate_graph(p);
+    if (st != FDI_OK) return st;
+    return field_solve(p, field, sigma, lambda, rhs, out, s);  // capture refused: eager
+  }
+  const long long n_launch = p->launches;
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    invalidate_graph(p);
+    return field_solve(p, field, sigma, lambda, rhs, out, s);
+  }
+  p->gexec = ex;
+  p->glaunches = n_launch;
+  FDI_CUDA_TRY(cudaGraphLaunch(p->gexec, s));
+  p->launches = n_launch;
+  return FDI_OK;
+}
+
+}  // namespace
+
 }  // namespace fdi
 
 using namespace fdi;
@@ -109,19 +185,22 @@ extern "C" {
 
 fdi_status fdi_field_solve(fdi_plan* plan, fdi_field field, double sigma, double lambda, const double* rhs,
                            double* out, fdi_stream_t stream) {
-  if (plan) plan->launches = 0;
-  return field_solve(plan, (int)field, sigma, lambda, rhs, out, (cudaStream_t)stream);
+  fdi_status st = validate_field_args(plan, (int)field, sigma, lambda);
+  if (st != FDI_OK) return st;
+  return field_solve_entry(plan, (int)field, sigma, lambda, rhs, out, (cudaStream_t)stream);
 }
 
 fdi_status fdi_helmholtz_solve(fdi_plan* plan, double lambda, const double* rhs, double* out,
                                fdi_stream_t stream) {
-  if (plan) plan->launches = 0;
-  return field_solve(plan, FDI_FIELD_CELL, 1.0, lambda, rhs, out, (cudaStream_t)stream);
+  fdi_status st = validate_field_args(plan, FDI_FIELD_CELL, 1.0, lambda);
+  if (st != FDI_OK) return st;
+  return field_solve_entry(plan, FDI_FIELD_CELL, 1.0, lambda, rhs, out, (cudaStream_t)stream);
 }
 
 fdi_status fdi_laplace_solve(fdi_plan* plan, const double* rhs, double* out, fdi_stream_t stream) {
-  if (plan) plan->launches = 0;
-  return field_solve(plan, FDI_FIELD_CELL, 0.0, 1.0, rhs, out, (cudaStream_t)stream);
+  fdi_status st = validate_field_args(plan, FDI_FIELD_CELL, 0.0, 1.0);
+  if (st != FDI_OK) return st;
+  return field_solve_entry(plan, FDI_FIELD_CELL, 0.0, 1.0, rhs, out, (cudaStream_t)stream);
 }
 
 fdi_status fdi_helmholtz_solve_batched(fdi_plan* const* plans, const double* lambdas, const double* const* rhs,
@@ -132,11 +211,18 @@ fdi_status fdi_helmholtz_solve_batched(fdi_plan* const* plans, const double* lam
     if (st != FDI_OK) return st;
     if (!rhs[i] || !out[i]) return FDI_ERR_INVALID_ARG;
   }
-  for (int i = 0; i < count; ++i) plans[i]->launches = 0;
   for (int i = 0; i < count; ++i) {
-    fdi_status st = field_solve(plans[i], FDI_FIELD_CELL, 1.0, lambdas[i], rhs[i], out[i], (cudaStream_t)stream);
+    fdi_status st = field_solve_entry(plans[i], FDI_FIELD_CELL, 1.0, lambdas[i], rhs[i], out[i],
+                                      (cudaStream_t)stream);
     if (st != FDI_OK) return st;
   }
+  return FDI_OK;
+}
+
+fdi_status fdi_plan_set_graphs(fdi_plan* plan, int on) {
+  if (!plan) return FDI_ERR_INVALID_ARG;
+  plan->use_graphs = on != 0;
+  invalidate_graph(plan);
   return FDI_OK;
 }
 

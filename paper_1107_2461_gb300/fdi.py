@@ -43,6 +43,7 @@ SIGNATURES = {
     "fdi_plan_set_transform_config": (_i, [_vp, _i]),
     "fdi_plan_set_stokes_preconditioner": (_i, [_vp, _i]),
     "fdi_eigen_noalloc": (_i, [C.POINTER(_d), _i, _i, _i, _i, _vp, _vp, _vp, C.POINTER(_i), _vp]),
+    "fdi_plan_set_graphs": (_i, [_vp, _i]),
     "fdi_plan_enable_timing": (_i, [_vp, _i]),
     "fdi_plan_kernel_times": (_i, [_vp, _i, C.POINTER(C.c_char_p), C.POINTER(_d), C.POINTER(C.c_longlong),
                                    C.POINTER(_i)]),
@@ -239,6 +240,11 @@ def set_stokes_preconditioner(plan: Plan, mode: int):
 
 def set_transform_config(plan: Plan, cluster: int):
     _check(load().fdi_plan_set_transform_config(plan.handle, int(cluster)), "fdi_plan_set_transform_config")
+
+
+def set_graphs(plan: Plan, on=True):
+    """Enable / disable CUDA-graph replay of repeated field solves on this plan."""
+    _check(load().fdi_plan_set_graphs(plan.handle, 1 if on else 0), "fdi_plan_set_graphs")
 
 
 def enable_timing(plan: Plan, on=True):
