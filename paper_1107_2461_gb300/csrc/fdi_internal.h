@@ -72,7 +72,7 @@ struct fdi_plan {
   double* ws[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   // mixed-path workspace: FP32 buffers + double-float pairs
   float* wf[4] = {nullptr, nullptr, nullptr, nullptr};
-  float2* xdf = nullptr;            // solution accumulator (hi, lo)
+  float2* xdf = nullptr;            // mixed solution planes H and L (2 x Pmax floats)
   float* d_scales = nullptr;        // per refinement round: max |field| of the pass inputs
   int* d_err = nullptr;             // nonzero: a tensor-core kernel hit a wait limit
   int tc_cluster = 1;               // CTAs sharing each transform-matrix chunk by TMA multicast

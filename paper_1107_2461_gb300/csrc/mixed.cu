@@ -9,12 +9,17 @@
 //   F1   [z][i][y]   after E_x^{-1}   (i: x mode)
 //   F2   [z][i][j]   after E_y^{-1}   (j: y mode); the Thomas sweep runs in place
 //   F4   [z][y][i]   after E_y
-//   x    [z][y][x]   solution accumulator, double-float (hi, lo)
+//   H, L [z][y][x]   solution x = H + L in two FP32 planes: after the first
+//                    solve H holds its output (exactly FP32); the first
+//                    correction is stored as L (the pair is then exact, not
+//                    renormalised); later corrections are added in
+//                    double-float with renormalisation
 // Rows are padded to a multiple of 4 floats (16-byte rows for vector loads).
 //
 // Refinement (the tensor-core solve is accurate to about 1e-6 relative):
-//   r_0 = b;  x_1 = S(r_0);  r_k = b - A x_k (double-float, flux form);
-//   x_{k+1} = x_k + S(r_k)   until ||r_k|| / ||b|| <= tol.
+//   r_0 = b;  H = S(r_0);  r_1 = b - A H;  L = S(r_1);
+//   r_k = b - A (H + L) (double-float, flux form);  (H, L) += S(r_k)
+//   until ||r_k|| / ||b|| <= tol.
 // Every refinement-round kernel reads the device "done" flag and returns at
 // once after convergence, so the solve is enqueued without host round trips.
 #include <cmath>
@@ -52,7 +57,8 @@ struct ResidArgs {
   float2 sigma, lambda;
   int sig_mode;         // 0: sigma = 0, 1: sigma = 1, 2: general sigma
   const double* b;
-  const float2* x;      // null: first pass, r = b
+  const float* xh;      // solution planes H and L (L read only when LO)
+  const float* xl;
   float* r;
   int r_pitch;
   double* out;          // FP64 solution output (null: not written)
@@ -145,7 +151,15 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const
   df::F2 svb = df::make(0.f, 0.f), sv = df::make(0.f, 0.f);
   const float2 z2 = make_float2(0.f, 0.f);
   const long long col = (long long)jc * nx + ic;
-  const float2* xq = a.x + (long long)k0 * sz + col;
+  const float* hq = a.xh + (long long)k0 * sz + col;
+  const float* lq = LO ? a.xl + (long long)k0 * sz + col : nullptr;
+  // x = H + L at an offset from the current point, renormalised to a
+  // double-float pair (L may be far above the rounding level of H)
+  auto ldx = [&](long long o) {
+    if (!LO) return make_float2(hq[o], 0.f);
+    const df::F2 v = df::two_sum(hq[o], lq[o]);
+    return make_float2(v.hi, v.lo);
+  };
   const double* bq = a.b + (long long)k0 * sz + col;
   float* rq = a.r + ((long long)k0 * ny + jc) * a.r_pitch + ic;
   const long long rstep = (long long)ny * a.r_pitch;
@@ -157,11 +171,11 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const
   float2 xc = z2, xm = z2, xp = z2, xn = z2, xs = z2;
   double bnow = 0.0;
   if (k0 < k1) {
-    xc = xq[0];
-    if (k0 > 0) xm = xq[-sz];
-    if (k0 + 1 < nz) xp = xq[sz];
-    xn = hy ? xq[sy] : xc;
-    xs = ly ? xq[-sy] : xc;
+    xc = ldx(0);
+    if (k0 > 0) xm = ldx(-sz);
+    if (k0 + 1 < nz) xp = ldx(sz);
+    xn = hy ? ldx(sy) : xc;
+    xs = ly ? ldx(-sy) : xc;
     bnow = bq[0];
   }
   // exact z difference of the face below plane k (x_{k-1} - x_k)
@@ -171,9 +185,9 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const
     float2 xp2 = z2, xn2 = z2, xs2 = z2;
     double bnext = 0.0;
     if (k + 1 < k1) {
-      if (k + 2 < nz) xp2 = xq[2 * sz];
-      xn2 = hy ? xq[sz + sy] : xp;
-      xs2 = ly ? xq[sz - sy] : xp;
+      if (k + 2 < nz) xp2 = ldx(2 * sz);
+      xn2 = hy ? ldx(sz + sy) : xp;
+      xs2 = ly ? ldx(sz - sy) : xp;
       bnext = bq[sz];
     }
     float2 xe, xw;
@@ -181,8 +195,8 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const
     xe.y = __shfl_down_sync(0xffffffffu, xc.y, 1);
     xw.x = __shfl_up_sync(0xffffffffu, xc.x, 1);
     xw.y = __shfl_up_sync(0xffffffffu, xc.y, 1);
-    if (ex) xe = xq[1];
-    if (wx) xw = xq[-1];
+    if (ex) xe = ldx(1);
+    if (wx) xw = ldx(-1);
     const df::F2 bb = df::from_f64(bnow);
     Acc S{bb.hi, bb.lo};
     if (MEAN) acc_add(S, mean_h, mean_l);
@@ -234,7 +248,8 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const
     xn = xn2;
     xs = xs2;
     bnow = bnext;
-    xq += sz;
+    hq += sz;
+    if (LO) lq += sz;
     bq += sz;
     rq += rstep;
     if (OUT) oq += sz;
@@ -282,28 +297,19 @@ ResidKernel resid_kernel(int sig_mode, bool lo, bool mean, bool out) {
 
 // FP64 solution from the double-float accumulator (minus the volume-weighted
 // mean for the zero-flux Laplace problem).
-__global__ void k_finalize_out(const float2* __restrict__ x, double* __restrict__ out, long long P,
-                               const DevStatus* __restrict__ st, int max_refine, int singular) {
+__global__ void k_finalize_out(const float* __restrict__ xh, const float* __restrict__ xl, double* __restrict__ out,
+                               long long P, const DevStatus* __restrict__ st, int max_refine, int singular) {
   // refinement passes write the output themselves: only convergence in round 0
-  // (no refinement step taken) and the singular problem need this pass
+  // (no refinement step taken, L = 0) and the singular problem need this pass
   if (!singular && (st->refine_steps > 0 || max_refine == 0)) return;
+  const bool has_l = st->refine_steps > 0;
   df::F2 mu = df::make(0.f, 0.f);
   if (singular) mu = df::from_f64(st->scal[0]);
-  const long long stride = (long long)gridDim.x * blockDim.x * 2;
-  for (long long p = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 2; p < P; p += stride) {
-    if (p + 1 < P) {
-      const float4 v = *reinterpret_cast<const float4*>(x + p);
-      df::F2 u0 = df::make(v.x, v.y), u1 = df::make(v.z, v.w);
-      if (singular) {
-        u0 = df::sub(u0, mu);
-        u1 = df::sub(u1, mu);
-      }
-      *reinterpret_cast<double2*>(out + p) = make_double2(df::to_f64_bits(u0), df::to_f64_bits(u1));
-    } else {
-      df::F2 u0 = df::make(x[p].x, x[p].y);
-      if (singular) u0 = df::sub(u0, mu);
-      out[p] = df::to_f64_bits(u0);
-    }
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
+    df::F2 u = df::two_sum(xh[p], has_l ? xl[p] : 0.f);
+    if (singular) u = df::sub(u, mu);
+    out[p] = df::to_f64_bits(u);
   }
 }
 
@@ -720,7 +726,7 @@ fdi_status mixed_setup(fdi_plan* p) {
   FDI_CUDA_TRY(cudaMalloc(&p->wf[1], szf * sizeof(float)));   // F1
   FDI_CUDA_TRY(cudaMalloc(&p->wf[2], szf * sizeof(float)));   // F2 / F3
   FDI_CUDA_TRY(cudaMalloc(&p->wf[3], szf * sizeof(float)));   // Thomas scratch
-  FDI_CUDA_TRY(cudaMalloc(&p->xdf, (size_t)p->Pmax * sizeof(float2)));
+  FDI_CUDA_TRY(cudaMalloc(&p->xdf, (size_t)p->Pmax * sizeof(float2)));  // planes H and L
   FDI_CUDA_TRY(cudaMalloc(&p->d_scales, (size_t)(kMaxRefineCap + 2) * 4 * sizeof(float)));
   FDI_CUDA_TRY(cudaMalloc(&p->d_err, sizeof(int)));
   FDI_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
@@ -749,6 +755,8 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
   float* F2 = p->wf[2];
   float* CS = p->wf[3];
   float* F4 = p->wf[0];
+  float* xH = reinterpret_cast<float*>(p->xdf);
+  float* xL = xH + f.P;
   const int* done = &p->d_status->done;
 
   const dim3 rgrid = resid_grid(nx, ny, nz);
@@ -789,7 +797,8 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
   {
     FDI_KTIMER(p, "residual_df_init", s);
     ResidArgs a0 = ra;
-    a0.x = nullptr;
+    a0.xh = nullptr;
+    a0.xl = nullptr;
     a0.out = nullptr;
     a0.sub_mean = 0;
     a0.want_mean = singular ? 1 : 0;
@@ -880,24 +889,31 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     t.col_stride = px;
     t.scale_out = sc + 3;
     FDI_TRY(launch_tc_transform(p, my->bwd, t, "transform_yb_tc", s));
-    // back x: F4 [z][y][i] -> x (double-float) [z][y][x]
+    // back x: F4 [z][y][i] -> H (first solve), L (first correction) or L += (later ones), [z][y][x]
     t.in = F4;
     t.R = (long long)nz * ny;
     t.K = nx;
     t.in_pitch = px;
     t.scale_in = sc + 3;
-    t.mode = round == 0 ? TC_OUT_DF_SET : TC_OUT_DF_ADD;
+    t.mode = round <= 1 ? TC_OUT_F32 : TC_OUT_DF_ADD;
     t.n_out = nx;
-    t.out_f32 = nullptr;
-    t.out_df = p->xdf;
+    t.out_f32 = round == 0 ? xH : (round == 1 ? xL : xH);
+    t.out_lo = xL;
+    t.S = t.R;
+    t.slab_stride = 0;
+    t.row_stride = nx;
+    t.col_stride = 1;
     t.scale_out = nullptr;
-    FDI_TRY(launch_tc_transform(p, mx->bwd, t, round == 0 ? "transform_xb_set_tc" : "transform_xb_add_tc", s));
+    FDI_TRY(launch_tc_transform(p, mx->bwd, t,
+                                round == 0 ? "transform_xb_set_tc" : (round == 1 ? "transform_xb_corr_tc" : "transform_xb_add_tc"),
+                                s));
     // residual of the updated solution and convergence check; the pass of the
     // last possible round also writes the FP64 solution
     {
       FDI_KTIMER(p, "residual_df", s);
       ResidArgs ak = ra;
-      ak.x = p->xdf;
+      ak.xh = xH;
+      ak.xl = xL;
       ak.out = out;
       ak.sub_mean = singular ? 1 : 0;
       ak.want_mean = singular ? 1 : 0;
@@ -923,7 +939,7 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     // projects the null line only to single precision, and the constant is
     // outside the range of A, so shifting it leaves the residual)
     FDI_KTIMER(p, "finalize_out", s);
-    k_finalize_out<<<kBlocks, kThreads, 0, s>>>(p->xdf, out, f.P, p->d_status, p->max_refine, singular ? 1 : 0);
+    k_finalize_out<<<kBlocks, kThreads, 0, s>>>(xH, xL, out, f.P, p->d_status, p->max_refine, singular ? 1 : 0);
     FDI_LAUNCH_CHECK(p);
   }
   return FDI_OK;

@@ -326,11 +326,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int q = warp & 3;  // TMEM lane quarter accessible to this warp
     const float inv_sA = 1.0f / scale_from_max(a.scale_in ? *a.scale_in : 1.0f);
     float* tp = reinterpret_cast<float*>(smem + BAR_OFF + BAR_BYTES) + (warp - (2 + NCONV)) * (32 * 33);
-    const bool rowmajor = a.mode != TC_OUT_F32 || a.col_stride == 1;
+    const bool rowmajor = a.col_stride == 1;
     // vector stores need 16-byte aligned groups of 4 along the contiguous index
     const bool vec_t = !rowmajor && a.row_stride == 1 && (a.S % 4 == 0) && (a.slab_stride % 4 == 0) &&
                        (a.col_stride % 4 == 0);
-    const bool vec_r = rowmajor && (a.mode != TC_OUT_F32 || (a.row_stride % 4 == 0 && a.slab_stride % 4 == 0));
+    const bool vec_r = rowmajor && a.row_stride % 4 == 0 && a.slab_stride % 4 == 0 &&
+                       (reinterpret_cast<uintptr_t>(a.out_f32) & 15u) == 0;
     const int g8 = lane >> 3, l8 = lane & 7;  // after the transpose: group of 8 lanes, lane in group
     float vmax = 0.f;
     for (long long it = 0; it < my_iters && !s_abort; ++it) {
@@ -420,62 +421,55 @@ __global__ void __launch_bounds__(THREADS, 1)
               }
             }
           } else {
-            // double-float accumulator: rows in groups of 4 with the loads of a
-            // group issued before any of its updates
-            const bool evenrow = (a.n_out % 2 == 0);
+            // double-float accumulation into the (out_f32, out_lo) planes: rows in
+            // groups of 4 with the loads of a group issued before any update
 #pragma unroll
             for (int q4 = 0; q4 < 8; q4 += 4) {
-              float2 o[4][4];
-              bool v2[4];
+              float oh[4][4], ol[4][4];
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
                 const int rl = 4 * (q4 + u) + g8;
-                const long long rr = wrow0 + rl;
-                float2* x = a.out_df + rr * (long long)a.n_out + c0 + cc;
-                v2[u] = fullcols && evenrow;
-                if (rl < nrows && a.mode == TC_OUT_DF_ADD) {
-                  if (v2[u]) {
-                    const float4 p0 = reinterpret_cast<const float4*>(x)[0];
-                    const float4 p1 = reinterpret_cast<const float4*>(x)[1];
-                    o[u][0] = make_float2(p0.x, p0.y);
-                    o[u][1] = make_float2(p0.z, p0.w);
-                    o[u][2] = make_float2(p1.x, p1.y);
-                    o[u][3] = make_float2(p1.z, p1.w);
-                  } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) o[u][e] = (c0 + cc + e < a.n_out) ? x[e] : make_float2(0.f, 0.f);
-                  }
+                const long long brow = __shfl_sync(0xffffffffu, base, rl) + c0 + cc;
+                if (rl < nrows && vec_r && fullcols) {
+                  const float4 h = *reinterpret_cast<const float4*>(a.out_f32 + brow);
+                  const float4 l = *reinterpret_cast<const float4*>(a.out_lo + brow);
+                  oh[u][0] = h.x; oh[u][1] = h.y; oh[u][2] = h.z; oh[u][3] = h.w;
+                  ol[u][0] = l.x; ol[u][1] = l.y; ol[u][2] = l.z; ol[u][3] = l.w;
                 } else {
 #pragma unroll
-                  for (int e = 0; e < 4; ++e) o[u][e] = make_float2(0.f, 0.f);
+                  for (int e = 0; e < 4; ++e) {
+                    const bool ok = rl < nrows && c0 + cc + e < a.n_out;
+                    oh[u][e] = ok ? a.out_f32[brow + e] : 0.f;
+                    ol[u][e] = ok ? a.out_lo[brow + e] : 0.f;
+                  }
                 }
               }
 #pragma unroll
               for (int u = 0; u < 4; ++u) {
                 const int rl = 4 * (q4 + u) + g8;
+                const long long brow = __shfl_sync(0xffffffffu, base, rl) + c0 + cc;
                 if (rl >= nrows) continue;
-                const long long rr = wrow0 + rl;
-                float2* x = a.out_df + rr * (long long)a.n_out + c0 + cc;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
+                  // (oh, ol) + val: two-sum of the high parts, low parts added, fast renormalisation
                   const float val = tp[rl * 33 + cc + e] * cs[e];
-                  if (a.mode == TC_OUT_DF_ADD) {
-                    const float sh = o[u][e].x + val;
-                    const float bb = sh - o[u][e].x;
-                    const float er = (o[u][e].x - (sh - bb)) + (val - bb) + o[u][e].y;
-                    const float nh = sh + er;
-                    o[u][e] = make_float2(nh, er - (nh - sh));
-                  } else {
-                    o[u][e] = make_float2(val, 0.f);
-                  }
+                  const float sh = oh[u][e] + val;
+                  const float bb = sh - oh[u][e];
+                  const float er = (oh[u][e] - (sh - bb)) + (val - bb) + ol[u][e];
+                  const float nh = sh + er;
+                  oh[u][e] = nh;
+                  ol[u][e] = er - (nh - sh);
                 }
-                if (v2[u]) {
-                  reinterpret_cast<float4*>(x)[0] = make_float4(o[u][0].x, o[u][0].y, o[u][1].x, o[u][1].y);
-                  reinterpret_cast<float4*>(x)[1] = make_float4(o[u][2].x, o[u][2].y, o[u][3].x, o[u][3].y);
+                if (vec_r && fullcols) {
+                  *reinterpret_cast<float4*>(a.out_f32 + brow) = make_float4(oh[u][0], oh[u][1], oh[u][2], oh[u][3]);
+                  *reinterpret_cast<float4*>(a.out_lo + brow) = make_float4(ol[u][0], ol[u][1], ol[u][2], ol[u][3]);
                 } else {
 #pragma unroll
                   for (int e = 0; e < 4; ++e)
-                    if (c0 + cc + e < a.n_out) x[e] = o[u][e];
+                    if (c0 + cc + e < a.n_out) {
+                      a.out_f32[brow + e] = oh[u][e];
+                      a.out_lo[brow + e] = ol[u][e];
+                    }
                 }
               }
             }

@@ -6,7 +6,10 @@
 
 namespace fdi {
 
-enum { TC_OUT_F32 = 0, TC_OUT_DF_SET = 1, TC_OUT_DF_ADD = 2 };
+// TC_OUT_F32: out = T x.  TC_OUT_DF_ADD: (out, out_lo) += T x, the two FP32
+// planes holding one double-float value per element, renormalised on store
+// (row-major outputs only)
+enum { TC_OUT_F32 = 0, TC_OUT_DF_ADD = 1 };
 
 // A transform matrix T (n x n, output index k, input index j) prepared for the
 // tensor cores: B = [hi; lo] fp16 [2*N_pad][K_pad], per-row power-of-two scale
@@ -32,11 +35,10 @@ struct TcArgs {
   const float* scale_in = nullptr;  // device: max |in| (sets the fp16 scaling)
   // output: element (r, k) of an FP32 field at
   //   (r / S) * slab_stride + (r % S) * row_stride + k * col_stride
-  // or the double-float accumulator out_df[r * n_out + k]
   int mode = TC_OUT_F32;
   int n_out = 0;
   float* out_f32 = nullptr;
-  float2* out_df = nullptr;
+  float* out_lo = nullptr;          // TC_OUT_DF_ADD: low plane, same layout as out_f32
   long long S = 1, slab_stride = 0, row_stride = 0, col_stride = 1;
   float* scale_out = nullptr;       // device: atomic max |out| (next pass's scaling)
   const int* skip = nullptr;
