@@ -164,9 +164,10 @@ def kernel_model(name, n, steps, K):
         "transform_xb_corr_tc": ("hbm", 8.0 * P, "byte", min(steps, 1) * K),
         "transform_xb_add_tc": ("hbm", 12.0 * P, "byte", max(steps - 1, 0) * K),
         "thomas_z_f32": ("hbm", 8.0 * P, "byte", rounds * K),
-        # H (and L after the first round) and b read, r written; refinement-round
-        # passes also write the FP64 output
-        "residual_df": ("hbm", (16.0 + 12.0 * steps) / rounds * P, "byte", rounds * K),
+        # first check r_1 = b - A H: H and b read, r_1 written as two FP32 planes
+        "residual_df": ("hbm", 20.0 * P, "byte", K),
+        # later checks r = r_1 - A L: r_1 planes, L and H read, r and the FP64 output written
+        "residual_corr": ("hbm", 28.0 * P, "byte", steps * K),
         "residual_df_init": ("hbm", 12.0 * P, "byte", K),
         # converts the output only when no refinement round ran
         "finalize_out": ("hbm", 12.0 * P, "byte", K if steps == 0 else 0),

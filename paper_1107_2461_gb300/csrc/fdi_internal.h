@@ -72,7 +72,9 @@ struct fdi_plan {
   double* ws[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   // mixed-path workspace: FP32 buffers + double-float pairs
   float* wf[4] = {nullptr, nullptr, nullptr, nullptr};
-  float2* xdf = nullptr;            // mixed solution planes H and L (2 x Pmax floats)
+  float2* xdf = nullptr;            // mixed solution planes H, L, low part of L (3 x Pmax floats)
+  float* wr1 = nullptr;             // mixed: first residual r_1 as (hi, lo) FP32 planes
+  long long wr1_plane = 0;
   float* d_scales = nullptr;        // per refinement round: max |field| of the pass inputs
   int* d_err = nullptr;             // nonzero: a tensor-core kernel hit a wait limit
   int tc_cluster = 1;               // CTAs sharing each transform-matrix chunk by TMA multicast

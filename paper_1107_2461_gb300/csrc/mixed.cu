@@ -57,9 +57,13 @@ struct ResidArgs {
   float2 sigma, lambda;
   int sig_mode;         // 0: sigma = 0, 1: sigma = 1, 2: general sigma
   const double* b;
-  const float* xh;      // solution planes H and L (L read only when LO)
+  const float* xh;      // solution planes: H, L (= Lh) and the low plane of L
   const float* xl;
-  float* r;
+  const float* xll;
+  const float* r1;      // r_1 as a double-float pair of planes (MODE 1 input)
+  const float* r1_lo;
+  float* r;             // FP32 residual (the next solve's input)
+  float* r_lo;          // MODE 0: low plane of r_1
   int r_pitch;
   double* out;          // FP64 solution output (null: not written)
   float* rmax;          // atomic max |r|
@@ -119,11 +123,18 @@ __device__ __forceinline__ void acc_flux(Acc& s, float2 w, Diff t) {
   acc_add(s, p, e);
 }
 
-// SIG: 0 sigma = 0, 1 sigma = 1, 2 general sigma.  LO: x has a low part (false
-// after the first solve, whose output is exactly FP32).  MEAN: singular
-// problem (b minus its mean, volume-weighted sums of x).  OUT: write the FP64
-// solution.
-template <int SIG, bool LO, bool MEAN, bool OUT>
+// Two residual passes share this body.
+//   MODE 0 (after the first solve):  r_1 = b - A H, with H exactly FP32; the
+//     result is stored as a double-float pair (r_hi, r_lo) of FP32 planes and
+//     r_hi is the next solve's input.
+//   MODE 1 (after every correction): r = r_1 - A L, with L = Lh (+ Ll when LO)
+//     the accumulated corrections; A is linear, so this equals b - A (H + L)
+//     exactly, and only the small field L passes through the stencil.
+// SIG: 0 sigma = 0, 1 sigma = 1, 2 general sigma.  MEAN: zero-flux Laplace
+// problem (MODE 0 subtracts the volume-weighted mean of b; volume-weighted
+// sums of the solution H (+ L) are reduced).  OUT: write the FP64 solution
+// H + L.
+template <int MODE, int SIG, bool LO, bool MEAN, bool OUT>
 __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const int* __restrict__ skip) {
   if (skip && *skip) return;
   __shared__ double sh[4 * kResTY];
@@ -135,7 +146,7 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const
   const bool act = i < nx && j < ny;
   const int ic = min(i, nx - 1), jc = min(j, ny - 1);
   float mean_h = 0.f, mean_l = 0.f;
-  if (MEAN) {
+  if (MODE == 0 && MEAN) {
     const df::F2 mb = df::from_f64(a.st->mean_b);
     mean_h = -mb.hi;
     mean_l = -mb.lo;
@@ -151,17 +162,17 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const
   df::F2 svb = df::make(0.f, 0.f), sv = df::make(0.f, 0.f);
   const float2 z2 = make_float2(0.f, 0.f);
   const long long col = (long long)jc * nx + ic;
-  const float* hq = a.xh + (long long)k0 * sz + col;
-  const float* lq = LO ? a.xl + (long long)k0 * sz + col : nullptr;
-  // x = H + L at an offset from the current point, renormalised to a
-  // double-float pair (L may be far above the rounding level of H)
-  auto ldx = [&](long long o) {
-    if (!LO) return make_float2(hq[o], 0.f);
-    const df::F2 v = df::two_sum(hq[o], lq[o]);
-    return make_float2(v.hi, v.lo);
-  };
-  const double* bq = a.b + (long long)k0 * sz + col;
-  float* rq = a.r + ((long long)k0 * ny + jc) * a.r_pitch + ic;
+  // the field the stencil acts on: H (MODE 0) or L (MODE 1), as (hi, lo)
+  const float* uq = (MODE == 0 ? a.xh : a.xl) + (long long)k0 * sz + col;
+  const float* uql = (MODE == 1 && LO) ? a.xll + (long long)k0 * sz + col : nullptr;
+  auto ldu = [&](long long o) { return make_float2(uq[o], (MODE == 1 && LO) ? uql[o] : 0.f); };
+  const float* hq = (MODE == 1 && (OUT || MEAN)) ? a.xh + (long long)k0 * sz + col : nullptr;
+  const double* bq = MODE == 0 ? a.b + (long long)k0 * sz + col : nullptr;
+  const long long rp0 = ((long long)k0 * ny + jc) * a.r_pitch + ic;
+  const float* r1h = MODE == 1 ? a.r1 + rp0 : nullptr;
+  const float* r1l = MODE == 1 ? a.r1_lo + rp0 : nullptr;
+  float* rq = a.r + rp0;
+  float* rql = MODE == 0 ? a.r_lo + rp0 : nullptr;
   const long long rstep = (long long)ny * a.r_pitch;
   double* oq = OUT ? a.out + (long long)k0 * sz + col : nullptr;
   const float2* wpz = a.wp[2];
@@ -170,39 +181,57 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const
   // pipeline registers: values of plane k and the loads of plane k+1
   float2 xc = z2, xm = z2, xp = z2, xn = z2, xs = z2;
   double bnow = 0.0;
+  float2 rnow = z2;
+  float hnow = 0.f;
   if (k0 < k1) {
-    xc = ldx(0);
-    if (k0 > 0) xm = ldx(-sz);
-    if (k0 + 1 < nz) xp = ldx(sz);
-    xn = hy ? ldx(sy) : xc;
-    xs = ly ? ldx(-sy) : xc;
-    bnow = bq[0];
+    xc = ldu(0);
+    if (k0 > 0) xm = ldu(-sz);
+    if (k0 + 1 < nz) xp = ldu(sz);
+    xn = hy ? ldu(sy) : xc;
+    xs = ly ? ldu(-sy) : xc;
+    if (MODE == 0) bnow = bq[0];
+    if (MODE == 1) rnow = make_float2(r1h[0], r1l[0]);
+    if (MODE == 1 && (OUT || MEAN)) hnow = hq[0];
   }
-  // exact z difference of the face below plane k (x_{k-1} - x_k)
+  // exact z difference of the face below plane k (u_{k-1} - u_k)
   Diff dzm = two_diff(xm.x, xc.x);
 #pragma unroll 2
   for (int k = k0; k < k1; ++k) {
-    float2 xp2 = z2, xn2 = z2, xs2 = z2;
+    float2 xp2 = z2, xn2 = z2, xs2 = z2, rnext = z2;
     double bnext = 0.0;
+    float hnext = 0.f;
     if (k + 1 < k1) {
-      if (k + 2 < nz) xp2 = ldx(2 * sz);
-      xn2 = hy ? ldx(sz + sy) : xp;
-      xs2 = ly ? ldx(sz - sy) : xp;
-      bnext = bq[sz];
+      if (k + 2 < nz) xp2 = ldu(2 * sz);
+      xn2 = hy ? ldu(sz + sy) : xp;
+      xs2 = ly ? ldu(sz - sy) : xp;
+      if (MODE == 0) bnext = bq[sz];
+      if (MODE == 1) rnext = make_float2(r1h[rstep], r1l[rstep]);
+      if (MODE == 1 && (OUT || MEAN)) hnext = hq[sz];
     }
     float2 xe, xw;
     xe.x = __shfl_down_sync(0xffffffffu, xc.x, 1);
     xe.y = __shfl_down_sync(0xffffffffu, xc.y, 1);
     xw.x = __shfl_up_sync(0xffffffffu, xc.x, 1);
     xw.y = __shfl_up_sync(0xffffffffu, xc.y, 1);
-    if (ex) xe = ldx(1);
-    if (wx) xw = ldx(-1);
-    const df::F2 bb = df::from_f64(bnow);
-    Acc S{bb.hi, bb.lo};
-    if (MEAN) acc_add(S, mean_h, mean_l);
+    if (ex) xe = ldu(1);
+    if (wx) xw = ldu(-1);
+    Acc S;
+    df::F2 bb = df::make(0.f, 0.f);
+    if (MODE == 0) {
+      bb = df::from_f64(bnow);
+      S = Acc{bb.hi, bb.lo};
+      if (MEAN) acc_add(S, mean_h, mean_l);
+    } else {
+      S = Acc{rnow.x, rnow.y};
+    }
     if (MEAN && act) {
       const df::F2 V = df::mul(Vxy, ld2(a.m[2] + k));
-      svb = df::add(svb, df::mul(V, df::make(xc.x, xc.y)));
+      df::F2 xv = df::make(xc.x, 0.f);
+      if (MODE == 1) {
+        xv = df::two_sum(hnow, xc.x);
+        xv = df::fast_two_sum(xv.hi, xv.lo + xc.y);
+      }
+      svb = df::add(svb, df::mul(V, xv));
       sv = df::add(sv, V);
     }
     float sl = 0.f;  // lambda L applied to the low parts, FP32
@@ -213,7 +242,7 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const
     if (ly) acc_flux(S, wmy, two_diff(xs.x, xc.x));
     if (k + 1 < nz) acc_flux(S, wpz[k], dzp);
     if (k > 0) acc_flux(S, wmz[k], dzm);
-    if (LO) {
+    if (MODE == 1 && LO) {
       if (hx) sl = fmaf(wpx.x, xe.y - xc.y, sl);
       if (lx) sl = fmaf(wmx.x, xw.y - xc.y, sl);
       if (hy) sl = fmaf(wpy.x, xn.y - xc.y, sl);
@@ -233,13 +262,20 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const
       const df::F2 t = df::mul(df::make(a.sigma.x, a.sigma.y), df::make(xc.x, xc.y));
       acc_add(S, -t.hi, -t.lo);
     }
-    const float rf = S.h + (S.l + sl);
+    // S.h + S.l: the rounding errors in S.l may exceed the cancelled S.h, so
+    // the pair is rounded with a full two-sum
+    const df::F2 rr = df::two_sum(S.h, S.l + sl);
     if (act) {
-      if (OUT) *oq = df::to_f64_bits(df::make(xc.x, xc.y));
-      *rq = rf;
-      srr = fmaf(rf, rf, srr);
-      sbb = MEAN ? fmaf(bb.hi + mean_h, bb.hi + mean_h, sbb) : fmaf(bb.hi, bb.hi, sbb);
-      rmax = fmaxf(rmax, fabsf(rf));
+      if (OUT) {
+        df::F2 u = df::two_sum(hnow, xc.x);
+        u = df::fast_two_sum(u.hi, u.lo + xc.y);
+        *oq = df::to_f64_bits(u);
+      }
+      *rq = rr.hi;
+      if (MODE == 0) *rql = rr.lo;
+      srr = fmaf(rr.hi, rr.hi, srr);
+      if (MODE == 0) sbb = MEAN ? fmaf(bb.hi + mean_h, bb.hi + mean_h, sbb) : fmaf(bb.hi, bb.hi, sbb);
+      rmax = fmaxf(rmax, fabsf(rr.hi));
     }
     dzm = Diff{-dzp.d, -dzp.dl};
     xm = xc;
@@ -248,10 +284,18 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const
     xn = xn2;
     xs = xs2;
     bnow = bnext;
-    hq += sz;
-    if (LO) lq += sz;
-    bq += sz;
+    rnow = rnext;
+    hnow = hnext;
+    uq += sz;
+    if (MODE == 1 && LO) uql += sz;
+    if (MODE == 1 && (OUT || MEAN)) hq += sz;
+    if (MODE == 0) bq += sz;
+    if (MODE == 1) {
+      r1h += rstep;
+      r1l += rstep;
+    }
     rq += rstep;
+    if (MODE == 0) rql += rstep;
     if (OUT) oq += sz;
   }
 #pragma unroll
@@ -283,31 +327,36 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const
 
 using ResidKernel = void (*)(ResidArgs, const int*);
 
-template <int SIG, bool LO>
-ResidKernel resid_kernel_mo(bool mean, bool out) {
-  if (mean) return out ? k_resid_df<SIG, LO, true, true> : k_resid_df<SIG, LO, true, false>;
-  return out ? k_resid_df<SIG, LO, false, true> : k_resid_df<SIG, LO, false, false>;
+template <int SIG>
+ResidKernel resid_kernel_s(int mode, bool lo, bool mean, bool out) {
+  if (mode == 0) return mean ? k_resid_df<0, SIG, false, true, false> : k_resid_df<0, SIG, false, false, false>;
+  if (mean) return lo ? k_resid_df<1, SIG, true, true, false> : k_resid_df<1, SIG, false, true, false>;
+  if (out) return lo ? k_resid_df<1, SIG, true, false, true> : k_resid_df<1, SIG, false, false, true>;
+  return lo ? k_resid_df<1, SIG, true, false, false> : k_resid_df<1, SIG, false, false, false>;
 }
 
-ResidKernel resid_kernel(int sig_mode, bool lo, bool mean, bool out) {
-  if (sig_mode == 0) return lo ? resid_kernel_mo<0, true>(mean, out) : resid_kernel_mo<0, false>(mean, out);
-  if (sig_mode == 1) return lo ? resid_kernel_mo<1, true>(mean, out) : resid_kernel_mo<1, false>(mean, out);
-  return lo ? resid_kernel_mo<2, true>(mean, out) : resid_kernel_mo<2, false>(mean, out);
+// mode 0: r_1 = b - A H;  mode 1: r = r_1 - A L (lo: L has a low plane)
+ResidKernel resid_kernel(int sig_mode, int mode, bool lo, bool mean, bool out) {
+  if (sig_mode == 0) return resid_kernel_s<0>(mode, lo, mean, out);
+  if (sig_mode == 1) return resid_kernel_s<1>(mode, lo, mean, out);
+  return resid_kernel_s<2>(mode, lo, mean, out);
 }
 
 // FP64 solution from the double-float accumulator (minus the volume-weighted
 // mean for the zero-flux Laplace problem).
-__global__ void k_finalize_out(const float* __restrict__ xh, const float* __restrict__ xl, double* __restrict__ out,
-                               long long P, const DevStatus* __restrict__ st, int max_refine, int singular) {
+__global__ void k_finalize_out(const float* __restrict__ xh, const float* __restrict__ xl,
+                               const float* __restrict__ xll, double* __restrict__ out, long long P,
+                               const DevStatus* __restrict__ st, int max_refine, int singular) {
   // refinement passes write the output themselves: only convergence in round 0
   // (no refinement step taken, L = 0) and the singular problem need this pass
   if (!singular && (st->refine_steps > 0 || max_refine == 0)) return;
-  const bool has_l = st->refine_steps > 0;
+  const bool has_l = st->refine_steps > 0, has_ll = st->refine_steps > 1;
   df::F2 mu = df::make(0.f, 0.f);
   if (singular) mu = df::from_f64(st->scal[0]);
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
     df::F2 u = df::two_sum(xh[p], has_l ? xl[p] : 0.f);
+    if (has_ll) u = df::fast_two_sum(u.hi, u.lo + xll[p]);
     if (singular) u = df::sub(u, mu);
     out[p] = df::to_f64_bits(u);
   }
@@ -422,14 +471,16 @@ __global__ void k_finish_mixed(const double* __restrict__ partials, int nblocks,
     st->done = 0;
     return;
   }
-  const double rel = t[1] > 0.0 ? sqrt(t[0] / t[1]) : sqrt(t[0]);
+  // the first check (r_1 = b - A H) also measures ||b||; later checks reuse it
+  const double bn2 = kind == 1 ? t[1] : st->bnorm2;
+  const double rel = bn2 > 0.0 ? sqrt(t[0] / bn2) : sqrt(t[0]);
   if (kind == 1)
     st->refine_steps = 0;
   else
     st->refine_steps += 1;
   if (want_mean) st->scal[0] = t[2] / t[3];  // volume-weighted mean of the current solution
   st->rel_res = rel;
-  st->bnorm2 = t[1];
+  st->bnorm2 = bn2;
   if (!isfinite(rel)) {
     st->error = 1;
     st->done = 1;
@@ -726,7 +777,9 @@ fdi_status mixed_setup(fdi_plan* p) {
   FDI_CUDA_TRY(cudaMalloc(&p->wf[1], szf * sizeof(float)));   // F1
   FDI_CUDA_TRY(cudaMalloc(&p->wf[2], szf * sizeof(float)));   // F2 / F3
   FDI_CUDA_TRY(cudaMalloc(&p->wf[3], szf * sizeof(float)));   // Thomas scratch
-  FDI_CUDA_TRY(cudaMalloc(&p->xdf, (size_t)p->Pmax * sizeof(float2)));  // planes H and L
+  FDI_CUDA_TRY(cudaMalloc(&p->xdf, (size_t)p->Pmax * 3 * sizeof(float)));  // planes H, L, low part of L
+  FDI_CUDA_TRY(cudaMalloc(&p->wr1, szr * 2 * sizeof(float)));              // r_1 as (hi, lo) planes
+  p->wr1_plane = (long long)szr;
   FDI_CUDA_TRY(cudaMalloc(&p->d_scales, (size_t)(kMaxRefineCap + 2) * 4 * sizeof(float)));
   FDI_CUDA_TRY(cudaMalloc(&p->d_err, sizeof(int)));
   FDI_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
@@ -757,6 +810,9 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
   float* F4 = p->wf[0];
   float* xH = reinterpret_cast<float*>(p->xdf);
   float* xL = xH + f.P;
+  float* xLL = xL + f.P;
+  float* r1h = p->wr1;
+  float* r1l = p->wr1 + p->wr1_plane;
   const int* done = &p->d_status->done;
 
   const dim3 rgrid = resid_grid(nx, ny, nz);
@@ -816,11 +872,11 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     const int* skip = round == 0 ? nullptr : done;
     float* sc = p->d_scales + 4 * round;
     float* sc_next = p->d_scales + 4 * (round + 1);
-    // forward x: r [z][y][x] -> F1 [z][i][y]
+    // forward x: r [z][y][x] -> F1 [z][i][y] (round 1 reads r_1 from its own planes)
     TcArgs t{};
     t.skip = skip;
     t.err = p->d_err;
-    t.in = r;
+    t.in = round == 1 ? r1h : r;
     t.R = (long long)nz * ny;
     t.K = nx;
     t.in_pitch = px;
@@ -897,8 +953,9 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     t.scale_in = sc + 3;
     t.mode = round <= 1 ? TC_OUT_F32 : TC_OUT_DF_ADD;
     t.n_out = nx;
-    t.out_f32 = round == 0 ? xH : (round == 1 ? xL : xH);
-    t.out_lo = xL;
+    t.out_f32 = round == 0 ? xH : xL;
+    t.out_lo = xLL;
+    t.lo_valid = round >= 3 ? 1 : 0;
     t.S = t.R;
     t.slab_stride = 0;
     t.row_stride = nx;
@@ -907,22 +964,22 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     FDI_TRY(launch_tc_transform(p, mx->bwd, t,
                                 round == 0 ? "transform_xb_set_tc" : (round == 1 ? "transform_xb_corr_tc" : "transform_xb_add_tc"),
                                 s));
-    // residual of the updated solution and convergence check; the pass of the
-    // last possible round also writes the FP64 solution
+    // residual and convergence check: r_1 = b - A H after the first solve,
+    // r = r_1 - A L after each correction (which also writes the FP64 solution)
     {
-      FDI_KTIMER(p, "residual_df", s);
+      FDI_KTIMER(p, round == 0 ? "residual_df" : "residual_corr", s);
       ResidArgs ak = ra;
       ak.xh = xH;
       ak.xl = xL;
+      ak.xll = xLL;
+      ak.r1 = r1h;
+      ak.r1_lo = r1l;
+      ak.r = round == 0 ? r1h : r;
+      ak.r_lo = r1l;
       ak.out = out;
-      ak.sub_mean = singular ? 1 : 0;
-      ak.want_mean = singular ? 1 : 0;
       ak.rmax = sc_next + 0;
-      // the FP64 solution is written by every refinement-round pass (the first
-      // solve alone essentially never meets the tolerance); the finalize pass
-      // covers convergence in round 0 and the zero-flux Laplace problem
-      const bool write_out = !singular && (round > 0 || p->max_refine == 0);
-      ResidKernel kern = resid_kernel(ra.sig_mode, round > 0, singular, write_out);
+      const bool write_out = !singular && round > 0;
+      ResidKernel kern = resid_kernel(ra.sig_mode, round == 0 ? 0 : 1, round >= 2, singular, write_out);
       kern<<<rgrid, dim3(kResTX, kResTY), 0, s>>>(ak, skip);
       FDI_LAUNCH_CHECK(p);
     }
@@ -939,7 +996,8 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     // projects the null line only to single precision, and the constant is
     // outside the range of A, so shifting it leaves the residual)
     FDI_KTIMER(p, "finalize_out", s);
-    k_finalize_out<<<kBlocks, kThreads, 0, s>>>(xH, xL, out, f.P, p->d_status, p->max_refine, singular ? 1 : 0);
+    k_finalize_out<<<kBlocks, kThreads, 0, s>>>(xH, xL, xLL, out, f.P, p->d_status, p->max_refine,
+                                                singular ? 1 : 0);
     FDI_LAUNCH_CHECK(p);
   }
   return FDI_OK;

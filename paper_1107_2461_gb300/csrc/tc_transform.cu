@@ -432,7 +432,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const long long brow = __shfl_sync(0xffffffffu, base, rl) + c0 + cc;
                 if (rl < nrows && vec_r && fullcols) {
                   const float4 h = *reinterpret_cast<const float4*>(a.out_f32 + brow);
-                  const float4 l = *reinterpret_cast<const float4*>(a.out_lo + brow);
+                  const float4 l = a.lo_valid ? *reinterpret_cast<const float4*>(a.out_lo + brow)
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
                   oh[u][0] = h.x; oh[u][1] = h.y; oh[u][2] = h.z; oh[u][3] = h.w;
                   ol[u][0] = l.x; ol[u][1] = l.y; ol[u][2] = l.z; ol[u][3] = l.w;
                 } else {
@@ -440,7 +441,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                   for (int e = 0; e < 4; ++e) {
                     const bool ok = rl < nrows && c0 + cc + e < a.n_out;
                     oh[u][e] = ok ? a.out_f32[brow + e] : 0.f;
-                    ol[u][e] = ok ? a.out_lo[brow + e] : 0.f;
+                    ol[u][e] = (ok && a.lo_valid) ? a.out_lo[brow + e] : 0.f;
                   }
                 }
               }

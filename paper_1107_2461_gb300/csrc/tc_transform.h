@@ -39,6 +39,7 @@ struct TcArgs {
   int n_out = 0;
   float* out_f32 = nullptr;
   float* out_lo = nullptr;          // TC_OUT_DF_ADD: low plane, same layout as out_f32
+  int lo_valid = 1;                 // TC_OUT_DF_ADD: 0 = the low plane holds no value yet (read as 0)
   long long S = 1, slab_stride = 0, row_stride = 0, col_stride = 1;
   float* scale_out = nullptr;       // device: atomic max |out| (next pass's scaling)
   const int* skip = nullptr;
