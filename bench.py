@@ -23,6 +23,7 @@ the same workload instead.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -53,6 +54,25 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def dram_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/dram_traffic_256cube.json), or None when there is no entry or the
+    kernel's sources changed since the counters were taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic_256cube.json")) as fh:
+            table = json.load(fh)
+        e = table[kernel]
+        h = hashlib.sha256()
+        for f in e["sources"]:
+            with open(os.path.join(ROOT, "paper_1107_2461_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest() != e["sha256"]:
+            return None
+        return float(e["dram_read_bytes"] + e["dram_write_bytes"])
+    except Exception:
+        return None
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -69,7 +89,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "25"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
@@ -272,7 +292,7 @@ def run_stokes(fdi, torch, prec, n, reps, warm, stream):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fdi", choices=["fdi", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
@@ -379,6 +399,8 @@ def main():
         per_kernel[name] = e
     if per_kernel:
         roof = dict(max(per_kernel.values(), key=lambda e: e["total_ms"]))
+        if tuple(n) == (256, 256, 256):
+            roof["traffic"] = dram_traffic(roof["kernel"])
     stokes = None
     if args.stokes_n > 0:
         stokes = {}

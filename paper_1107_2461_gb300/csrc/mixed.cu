@@ -134,10 +134,11 @@ __device__ __forceinline__ void acc_flux(Acc& s, float2 w, Diff t) {
 // problem (MODE 0 subtracts the volume-weighted mean of b; volume-weighted
 // sums of the solution H (+ L) are reduced).  OUT: write the FP64 solution
 // H + L.
-template <int MODE, int SIG, bool LO, bool MEAN, bool OUT>
-__global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const int* __restrict__ skip) {
-  if (skip && *skip) return;
-  __shared__ double sh[4 * kResTY];
+// INT: every column of the block has both x and both y neighbours and no
+// x / y wall term (blocks away from the side walls), so the per-column
+// neighbour tests drop out.
+template <int MODE, int SIG, bool LO, bool MEAN, bool OUT, bool INT>
+__device__ __forceinline__ void resid_body(const ResidArgs& a, double* sh) {
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const long long sy = nx, sz = (long long)nx * ny;
   const int lane = threadIdx.x, wy = threadIdx.y;
@@ -153,10 +154,10 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const
   }
   const float2 wpx = a.wp[0][ic], wmx = a.wm[0][ic], wpy = a.wp[1][jc], wmy = a.wm[1][jc];
   const float2 w0x = a.w0[0][ic], w0y = a.w0[1][jc];
-  const bool wall_xy = w0x.x != 0.f || w0y.x != 0.f;
+  const bool wall_xy = !INT && (w0x.x != 0.f || w0y.x != 0.f);
   df::F2 Vxy = df::make(0.f, 0.f);
   if (MEAN) Vxy = df::mul(ld2(a.m[0] + ic), ld2(a.m[1] + jc));
-  const bool hx = i + 1 < nx, lx = i > 0, hy = j + 1 < ny, ly = j > 0;
+  const bool hx = INT || i + 1 < nx, lx = INT || i > 0, hy = INT || j + 1 < ny, ly = INT || j > 0;
   const bool ex = lane == kResTX - 1 && hx, wx = lane == 0 && lx;
   float srr = 0.f, sbb = 0.f, rmax = 0.f;
   df::F2 svb = df::make(0.f, 0.f), sv = df::make(0.f, 0.f);
@@ -323,6 +324,18 @@ __global__ void __launch_bounds__(kResTX * kResTY) k_resid_df(ResidArgs a, const
     const long long bid = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     for (int c = 0; c < 4; ++c) a.partials[4 * bid + c] = t[c];
   }
+}
+
+template <int MODE, int SIG, bool LO, bool MEAN, bool OUT>
+__global__ void __launch_bounds__(kResTX * kResTY, 4) k_resid_df(ResidArgs a, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ double sh[4 * kResTY];
+  const bool interior = blockIdx.x > 0 && (int)(blockIdx.x + 1) * kResTX < a.nx && blockIdx.y > 0 &&
+                        (int)(blockIdx.y + 1) * kResTY < a.ny;
+  if (interior)
+    resid_body<MODE, SIG, LO, MEAN, OUT, true>(a, sh);
+  else
+    resid_body<MODE, SIG, LO, MEAN, OUT, false>(a, sh);
 }
 
 using ResidKernel = void (*)(ResidArgs, const int*);

@@ -40,7 +40,7 @@ namespace {
 constexpr int BM = 128;
 constexpr int BK = 32;                       // fp16 K per chunk: 64-byte rows, 64-byte swizzle
 constexpr int STAGES = 3;
-constexpr int NA32 = 4;                      // FP32 A slots (TMA, 128-byte swizzle)
+constexpr int NA32 = 3;                      // FP32 A slots (TMA, 128-byte swizzle)
 constexpr int NMAX = 256;
 constexpr int ROWB = BK * 2;                 // bytes per operand row in a stage
 constexpr int A_BYTES = BM * ROWB;           // one fp16 half of an A chunk: 8 KB
@@ -50,14 +50,17 @@ constexpr int A32_BYTES = BM * BK * 4;      // 16 KB
 constexpr int NCONV = 8;
 constexpr int WARP_A = 2 + NCONV + 4;         // A producer warp
 constexpr int THREADS = 32 * (WARP_A + 1);
-constexpr int TP_BYTES = 4 * 32 * 33 * 4;     // epilogue transpose tiles, one per epilogue warp
+constexpr bool kTmaTransposed = false;
+constexpr int EPI_WARP_BYTES = 5 * 1024;      // per epilogue warp: transpose tile (32 x 33) or TMA staging (32 x 32)
+constexpr int TP_BYTES = 4 * EPI_WARP_BYTES;
 constexpr int BAR_BYTES = 256;
 constexpr int CS_BYTES = NMAX * 4;            // per-column unscale factors
 constexpr int A32_OFF = STAGES * STAGE_BYTES;
-constexpr int BAR_OFF = A32_OFF + NA32 * A32_BYTES;
+constexpr int EPI_OFF = A32_OFF + NA32 * A32_BYTES;  // 1024-byte aligned
+constexpr int BAR_OFF = EPI_OFF + TP_BYTES;
 // the dynamic block starts 1024-byte aligned (the static block is padded to
 // 1024 bytes by the alignment of the extern declaration; checked at run time)
-constexpr int SMEM_BYTES = BAR_OFF + BAR_BYTES + TP_BYTES + CS_BYTES;
+constexpr int SMEM_BYTES = BAR_OFF + BAR_BYTES + CS_BYTES;
 static_assert(SMEM_BYTES + 1024 <= 232448, "shared memory budget");
 
 __device__ __forceinline__ float scale_from_max(float mx) {
@@ -77,7 +80,8 @@ __device__ __forceinline__ uint32_t pack_half2(__half a, __half b) {
 
 template <int C>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_tc_transform(const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmA, TcArgs a) {
+    k_tc_transform(const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmA,
+                   const __grid_constant__ CUtensorMap tmO, TcArgs a) {
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // the swizzled layouts need a 1024-byte aligned base; the launch reserves no
@@ -123,7 +127,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmB);
   if (warp == WARP_A && lane == 0) tc::prefetch_tmap(&tmA);
-  float* s_cs = reinterpret_cast<float*>(smem + BAR_OFF + BAR_BYTES + TP_BYTES);
+  float* s_cs = reinterpret_cast<float*>(smem + BAR_OFF + BAR_BYTES);
   for (int k = threadIdx.x; k < N_pad; k += blockDim.x) s_cs[k] = a.col_scale[k];
   if (warp == 1) {
     tc::tmem_alloc(tmem_slot, tmem_cols);
@@ -325,7 +329,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     // outputs) and stores them with one 16-byte access where the layout allows.
     const int q = warp & 3;  // TMEM lane quarter accessible to this warp
     const float inv_sA = 1.0f / scale_from_max(a.scale_in ? *a.scale_in : 1.0f);
-    float* tp = reinterpret_cast<float*>(smem + BAR_OFF + BAR_BYTES) + (warp - (2 + NCONV)) * (32 * 33);
+    float* tp = reinterpret_cast<float*>(smem + EPI_OFF + (warp - (2 + NCONV)) * EPI_WARP_BYTES);
+    const uint32_t stg_u32 = tc::smem_u32(tp);  // TMA staging (1024-byte aligned)
     const bool rowmajor = a.col_stride == 1;
     // vector stores need 16-byte aligned groups of 4 along the contiguous index
     const bool vec_t = !rowmajor && a.row_stride == 1 && (a.S % 4 == 0) && (a.slab_stride % 4 == 0) &&
@@ -360,6 +365,46 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint32_t r[32];
         tc::tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * N_pad + c0), r);
         tc::tmem_ld_wait();
+        if (a.tma_store) {
+          // unscale into the staging tile and hand it to a TMA store; rows past
+          // R and columns past n_out hold zeros (zero-filled A rows, zero B
+          // rows) and are clipped by the store
+          if (lane == 0) tc::bulk_wait_read_all();  // the previous store has read the tile
+          __syncwarp();
+          if (a.tma_store == 1) {
+            // staging [column][row]: 32 rows of one column are 128 contiguous bytes
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const float v = __uint_as_float(r[j]) * s_cs[c0 + j] * inv_sA;
+              vmax = fmaxf(vmax, fabsf(v));
+              tp[j * 32 + lane] = v;
+            }
+          } else {
+            // staging [row][column] in the 128-byte swizzle (16-byte unit u of row
+            // `lane` at unit u ^ (lane & 7))
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              float v4[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                v4[e] = __uint_as_float(r[4 * u + e]) * s_cs[c0 + 4 * u + e] * inv_sA;
+                vmax = fmaxf(vmax, fabsf(v4[e]));
+              }
+              *reinterpret_cast<float4*>(tp + lane * 32 + ((u ^ (lane & 7)) << 2)) =
+                  make_float4(v4[0], v4[1], v4[2], v4[3]);
+            }
+          }
+          tc::fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0 && nrows > 0) {
+            if (a.tma_store == 1)
+              tc::tma_store_3d(&tmO, stg_u32, (int)(wrow0 % a.S), c0, (int)(wrow0 / a.S));
+            else
+              tc::tma_store_2d(&tmO, stg_u32, c0, (int)wrow0);
+            tc::bulk_commit();
+          }
+          continue;
+        }
 #pragma unroll
         for (int j = 0; j < 32; ++j) tp[lane * 33 + j] = __uint_as_float(r[j]);
         __syncwarp();
@@ -482,6 +527,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&acce[buf]);
     }
+    if (a.tma_store && lane == 0) tc::bulk_wait_all();
     if (a.scale_out) {
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
@@ -580,8 +626,8 @@ void tc_free_matrix(TcMatrix* m) {
 }
 
 template <int C>
-fdi_status launch_cluster(fdi_plan* p, const TcMatrix& m, const CUtensorMap& mapA, const TcArgs& args, long long tiles,
-                          cudaStream_t s) {
+fdi_status launch_cluster(fdi_plan* p, const TcMatrix& m, const CUtensorMap& mapA, const CUtensorMap& mapO,
+                          const TcArgs& args, long long tiles, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
     FDI_CUDA_TRY(cudaFuncSetAttribute(k_tc_transform<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
@@ -606,7 +652,7 @@ fdi_status launch_cluster(fdi_plan* p, const TcMatrix& m, const CUtensorMap& map
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  FDI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_transform<C>, map, mapA, args));
+  FDI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_transform<C>, map, mapA, mapO, args));
   FDI_LAUNCH_CHECK(p);
   return FDI_OK;
 }
@@ -642,10 +688,40 @@ fdi_status launch_tc_transform(fdi_plan* p, const TcMatrix& m, TcArgs args, cons
       return FDI_ERR_CUDA;
     }
   }
+  // output through TMA stores where the layout allows: 16-byte aligned base and
+  // strides, and (transposed outputs) slabs made of whole 32-row warp blocks
+  CUtensorMap mapO;
+  memset(&mapO, 0, sizeof(mapO));
+  args.tma_store = 0;
+  const bool out_aligned = (reinterpret_cast<uintptr_t>(args.out_f32) & 15u) == 0;
+  if (args.mode == TC_OUT_F32 && out_aligned && args.n_out > 0) {
+    cuuint32_t estr[3] = {1, 1, 1};
+    // transposed outputs keep the thread stores (16-byte row groups after an
+    // in-shared transpose), which measured faster than 32 x 32 TMA boxes of
+    // 128-byte column segments; kTmaTransposed enables the TMA variant
+    if (kTmaTransposed && args.row_stride == 1 && args.S % 32 == 0 && args.R % args.S == 0 &&
+        args.col_stride % 4 == 0 && args.slab_stride % 4 == 0 && args.R / args.S < 0x7fffffffLL) {
+      cuuint64_t dims[3] = {(cuuint64_t)args.S, (cuuint64_t)args.n_out, (cuuint64_t)(args.R / args.S)};
+      cuuint64_t strides[2] = {(cuuint64_t)args.col_stride * sizeof(float), (cuuint64_t)args.slab_stride * sizeof(float)};
+      cuuint32_t box[3] = {32, 32, 1};
+      if (enc(&mapO, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, args.out_f32, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+        args.tma_store = 1;
+    } else if (args.col_stride == 1 && args.S == args.R && args.row_stride % 4 == 0 && args.row_stride >= args.n_out) {
+      cuuint64_t dims[2] = {(cuuint64_t)args.n_out, (cuuint64_t)args.R};
+      cuuint64_t strides[1] = {(cuuint64_t)args.row_stride * sizeof(float)};
+      cuuint32_t box[2] = {32, 32};
+      if (enc(&mapO, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, args.out_f32, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+        args.tma_store = 2;
+    }
+  }
   switch (p->tc_cluster) {
-    case 2: return launch_cluster<2>(p, m, mapA, args, tiles, s);
-    case 4: return launch_cluster<4>(p, m, mapA, args, tiles, s);
-    default: return launch_cluster<1>(p, m, mapA, args, tiles, s);
+    case 2: return launch_cluster<2>(p, m, mapA, mapO, args, tiles, s);
+    case 4: return launch_cluster<4>(p, m, mapA, mapO, args, tiles, s);
+    default: return launch_cluster<1>(p, m, mapA, mapO, args, tiles, s);
   }
 }
 

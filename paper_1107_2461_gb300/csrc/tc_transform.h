@@ -42,6 +42,10 @@ struct TcArgs {
   int lo_valid = 1;                 // TC_OUT_DF_ADD: 0 = the low plane holds no value yet (read as 0)
   long long S = 1, slab_stride = 0, row_stride = 0, col_stride = 1;
   float* scale_out = nullptr;       // device: atomic max |out| (next pass's scaling)
+  // set by the launcher: 0 thread stores; 1 TMA stores of a transposed output
+  // (3D map over (row in slab, column, slab)); 2 TMA stores of a row-major
+  // output (2D map over (column, row))
+  int tma_store = 0;
   const int* skip = nullptr;
   int* err = nullptr;
   // filled by the launcher
