@@ -268,9 +268,10 @@ __device__ __forceinline__ void resid_body(const ResidArgs& a, double* sh) {
     const df::F2 rr = df::two_sum(S.h, S.l + sl);
     if (act) {
       if (OUT) {
-        df::F2 u = df::two_sum(hnow, xc.x);
-        u = df::fast_two_sum(u.hi, u.lo + xc.y);
-        *oq = df::to_f64_bits(u);
+        // H + L in FP64: one FP64 addition (exact while the exponents of H and
+        // L differ by at most 29) on integer-built operands; the FP64 pipe is
+        // otherwise idle here
+        *oq = df::f2d(hnow) + (LO ? df::to_f64(df::make(xc.x, xc.y)) : df::f2d(xc.x));
       }
       *rq = rr.hi;
       if (MODE == 0) *rql = rr.lo;
@@ -432,6 +433,64 @@ __global__ void __launch_bounds__(256) k_init_rhs(ResidArgs a) {
     for (int q = 0; q < 8; ++q)
       for (int c = 0; c < 4; ++c) t[c] += sh[4 * q + c];
     for (int c = 0; c < 4; ++c) a.partials[4 * blockIdx.x + c] = t[c];
+  }
+}
+
+// r_0 = b for unpadded fields without the mean (nx a multiple of 4): flat
+// stream, 8 values per thread and iteration (four 16-byte loads in flight),
+// ||b||^2 and max |b|
+__global__ void __launch_bounds__(256) k_init_rhs_flat(ResidArgs a, long long P) {
+  __shared__ double sh[8];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  float sbb = 0.f, rmax = 0.f;
+  const long long stride = (long long)gridDim.x * blockDim.x * 8;
+  for (long long p0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 8; p0 < P; p0 += stride) {
+    double v[8];
+    if (p0 + 8 <= P) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const double2 t = *reinterpret_cast<const double2*>(a.b + p0 + 2 * u);
+        v[2 * u] = t.x;
+        v[2 * u + 1] = t.y;
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = p0 + u < P ? a.b[p0 + u] : 0.0;
+    }
+    float f[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const df::F2 bb = df::from_f64(v[u]);
+      f[u] = bb.hi + bb.lo;
+      sbb = fmaf(f[u], f[u], sbb);
+      rmax = fmaxf(rmax, fabsf(f[u]));
+    }
+    if (p0 + 8 <= P) {
+      *reinterpret_cast<float4*>(a.r + p0) = make_float4(f[0], f[1], f[2], f[3]);
+      *reinterpret_cast<float4*>(a.r + p0 + 4) = make_float4(f[4], f[5], f[6], f[7]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (p0 + u < P) a.r[p0 + u] = f[u];
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sbb += __shfl_down_sync(0xffffffffu, sbb, o);
+    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  }
+  if (lane == 0) {
+    sh[warp] = (double)sbb;
+    if (rmax > 0.f) atomicMax(reinterpret_cast<unsigned int*>(a.rmax), __float_as_uint(rmax));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += sh[q];
+    a.partials[4 * blockIdx.x + 0] = 0.0;
+    a.partials[4 * blockIdx.x + 1] = t;
+    a.partials[4 * blockIdx.x + 2] = 0.0;
+    a.partials[4 * blockIdx.x + 3] = 0.0;
   }
 }
 
@@ -862,7 +921,7 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
   ra.partials = p->partials;
 
   // r_0 = b (and the volume-weighted mean of b for the singular problem)
-  const int iblocks = 152 * 4;
+  const int iblocks = 152 * 8;
   {
     FDI_KTIMER(p, "residual_df_init", s);
     ResidArgs a0 = ra;
@@ -872,7 +931,10 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     a0.sub_mean = 0;
     a0.want_mean = singular ? 1 : 0;
     a0.rmax = p->d_scales + 0;
-    k_init_rhs<<<iblocks, 256, 0, s>>>(a0);
+    if (px == nx && !singular && (reinterpret_cast<uintptr_t>(b) & 15u) == 0)
+      k_init_rhs_flat<<<iblocks, 256, 0, s>>>(a0, f.P);
+    else
+      k_init_rhs<<<iblocks, 256, 0, s>>>(a0);
     FDI_LAUNCH_CHECK(p);
   }
   {
