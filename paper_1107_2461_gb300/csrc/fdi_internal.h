@@ -116,6 +116,13 @@ struct fdi_plan {
   bool gkey_valid = false;
   cudaGraphExec_t gexec = nullptr;
   long long glaunches = 0;
+  // CUDA graph of one BiCGstab iteration of the Stokes inverse (every
+  // iteration after the first enqueues the same launches on plan workspace)
+  cudaGraphExec_t kgraph = nullptr;
+  double kgraph_lambda = 0.0;
+  int kgraph_precond = -1;
+  cudaStream_t kgraph_stream = nullptr;
+  long long kgraph_launches = 0;
   // optional per-kernel device timing (CUDA events around each launch)
   bool timing = false;
   struct TimedLaunch { const char* name; cudaEvent_t e0, e1; };

@@ -106,6 +106,9 @@ void invalidate_graph(fdi_plan* p) {
   p->gexec = nullptr;
   p->gkey_valid = false;
   p->glaunches = 0;
+  if (p->kgraph) cudaGraphExecDestroy(p->kgraph);
+  p->kgraph = nullptr;
+  p->kgraph_precond = -1;
 }
 
 namespace {

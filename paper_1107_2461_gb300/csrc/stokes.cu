@@ -405,8 +405,8 @@ fdi_status stokes_solve(fdi_plan* p, double dt, double Re, const double* const f
   FDI_LAUNCH_CHECK(p);
   FDI_TRY(dots(p, b, b, nullptr, nullptr, Pc, KF_INIT, s));
   // step 2: BiCGstab on C q = b, right-preconditioned by L_p^{-1}
-  for (int it = 0; it < p->kmaxit; ++it) {
-    k_bicg_p<<<vb, vt, 0, s>>>(p->d_kry, pv, r, v, Pc, it == 0 ? 1 : 0);
+  auto iteration = [&](int first) -> fdi_status {
+    k_bicg_p<<<vb, vt, 0, s>>>(p->d_kry, pv, r, v, Pc, first);
     FDI_LAUNCH_CHECK(p);
     // y = (-L_p)^{-1} p (+ lambda p) = -phat ; v = C phat
     FDI_TRY(field_solve(p, FDI_FIELD_CELL, 0.0, 1.0, pv, y, s));
@@ -431,6 +431,46 @@ fdi_status stokes_solve(fdi_plan* p, double dt, double Re, const double* const f
       FDI_LAUNCH_CHECK(p);
       k_kry_finish<<<1, kDotThreads, 0, s>>>(p->kpartials, p->d_kry, KF_ITER);
       FDI_LAUNCH_CHECK(p);
+    }
+    return FDI_OK;
+  };
+  // iterations after the first replay one captured graph of the iteration
+  // (plan workspace only, so the launches are identical); the legacy stream
+  // and timed plans run eagerly
+  const bool graphs = p->use_graphs && !p->timing && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+  for (int it = 0; it < p->kmaxit; ++it) {
+    if (it == 0 || !graphs) {
+      FDI_TRY(iteration(it == 0 ? 1 : 0));
+    } else {
+      if (!p->kgraph || p->kgraph_lambda != lambda || p->kgraph_precond != p->stokes_precond ||
+          p->kgraph_stream != s) {
+        if (p->kgraph) cudaGraphExecDestroy(p->kgraph);
+        p->kgraph = nullptr;
+        const long long before = p->launches;
+        FDI_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        fdi_status st = iteration(0);
+        cudaGraph_t gr = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &gr);
+        if (st != FDI_OK || e != cudaSuccess || gr == nullptr) {
+          if (gr) cudaGraphDestroy(gr);
+          if (st != FDI_OK) return st;
+          FDI_CUDA_TRY(e);
+          set_error("stream capture of the BiCGstab iteration failed");
+          return FDI_ERR_CUDA;
+        }
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, gr, 0);
+        cudaGraphDestroy(gr);
+        FDI_CUDA_TRY(e);
+        p->kgraph = ex;
+        p->kgraph_lambda = lambda;
+        p->kgraph_precond = p->stokes_precond;
+        p->kgraph_stream = s;
+        p->kgraph_launches = p->launches - before;
+        p->launches = before;
+      }
+      FDI_CUDA_TRY(cudaGraphLaunch(p->kgraph, s));
+      p->launches += p->kgraph_launches;
     }
     FDI_CUDA_TRY(cudaMemcpyAsync(p->h_flag, &p->d_kry->done, sizeof(int), cudaMemcpyDeviceToHost, s));
     FDI_CUDA_TRY(cudaStreamSynchronize(s));
