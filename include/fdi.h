@@ -171,8 +171,8 @@ fdi_status fdi_apply_transform(fdi_plan* plan, fdi_field field, int d, int inver
 /* Launch shape of the tensor-core transforms of a mixed plan: `cluster` CTAs
  * (1, 2 or 4) form a thread-block cluster and share each chunk of the
  * transform matrix through TMA multicast, dividing its L2 reads by `cluster`.
- * A tuning knob (see the autotuner in the Python package); results do not
- * depend on it beyond FP32 rounding order.  Default 1. */
+ * A tuning knob (see fdi_plan_autotune); results are bitwise identical for
+ * every value.  Default 1. */
 fdi_status fdi_plan_set_transform_config(fdi_plan* plan, int cluster);
 
 /* Allocation-free eigen decomposition of one 1D operator (the same kernel as
@@ -198,6 +198,22 @@ fdi_status fdi_plan_set_transform_config(fdi_plan* plan, int cluster);
  * cleared per call): calls that overlap on the GPU, on any stream, race. */
 fdi_status fdi_eigen_noalloc(const double* faces, int n, int face_kind, fdi_bc bc_lo, fdi_bc bc_hi, double* lam,
                              double* E, double* Einv, int* converged, fdi_stream_t stream);
+
+/* FP32 Thomas sweep of mixed plans: lines (threads) per CTA, 64 or 128
+ * (default 128).  A tuning knob: results are bitwise identical. */
+fdi_status fdi_plan_set_thomas_config(fdi_plan* plan, int lines_per_cta);
+
+/* Autotuner for mixed plans: times `reps` complete Helmholtz solves
+ * (sigma = 1, `lambda`, rhs -> out on `stream`, after one warm-up solve each)
+ * for every transform cluster size (1, 2, 4) and Thomas CTA size (64, 128),
+ * keeps the fastest on the plan and records it for the plan's grid shape:
+ * plans created later with the same shape and precision start with it.  Every
+ * configuration computes bitwise-identical results.  rhs and out: device FP64
+ * fields of the plan's cell shape, distinct; out is overwritten.  The chosen
+ * values are written to *cluster_out and *thomas_tl_out (host, may be NULL).
+ * Synchronises `stream`.  FP64 plans have nothing to tune (returns OK). */
+fdi_status fdi_plan_autotune(fdi_plan* plan, double lambda, const double* rhs, double* out, int reps,
+                             int* cluster_out, int* thomas_tl_out, fdi_stream_t stream);
 
 /* CUDA-graph replay of field solves (default on).  A Helmholtz / Laplace /
  * field solve whose arguments (field, sigma, lambda, rhs, out, stream) repeat

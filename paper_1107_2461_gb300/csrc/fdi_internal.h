@@ -78,6 +78,7 @@ struct fdi_plan {
   float* d_scales = nullptr;        // per refinement round: max |field| of the pass inputs
   int* d_err = nullptr;             // nonzero: a tensor-core kernel hit a wait limit
   int tc_cluster = 1;               // CTAs sharing each transform-matrix chunk by TMA multicast
+  int thomas_tl = 128;              // FP32 Thomas lines per CTA (64 or 128)
   float2* lam_w = nullptr;          // lambda-scaled double-float flux weights [3][3][kMaxN]
   double* partials = nullptr;       // reduction partials
   int npartials = 0;
@@ -168,6 +169,16 @@ struct KTimer {
 
 // drop the captured solve graph (arguments or controls changed)
 void invalidate_graph(fdi_plan* p);
+
+// autotuned configurations per grid shape (fdi_plan_autotune records, plan
+// creation applies)
+void remember_tuning(const fdi_plan* p);
+void apply_tuning(fdi_plan* p);
+
+// independent Helmholtz solves of several plans: concurrent on a stream pool,
+// one CUDA graph when the same batch repeats
+fdi_status batch_solve(fdi_plan* const* plans, const double* lambdas, const double* const* rhs, double* const* out,
+                       int count, cudaStream_t s);
 
 // plan-time eigen decomposition of the symmetric tridiagonal M^{-1/2} K M^{-1/2}
 fdi_status eigen_decompose_all(const std::vector<Axis*>& axes, cudaStream_t s, int* d_err);

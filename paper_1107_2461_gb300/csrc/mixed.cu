@@ -577,7 +577,6 @@ struct Thomas32Args {
 };
 
 constexpr int kTB = 16;   // Thomas block of planes: c' checkpoint interval and copy group
-constexpr int kTL = 128;  // Thomas lines per CTA (one thread per line)
 constexpr int kNBR = 3;   // blocks of kTB planes in flight per line
 
 // single-instruction reciprocal (PTX rcp.approx, at most 1 ulp): the sweep
@@ -608,9 +607,11 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// FULL: nz is a multiple of kTB (no partial block of planes)
-template <bool FULL>
-__global__ void __launch_bounds__(kTL) k_thomas_f32(Thomas32Args a, const int* __restrict__ skip) {
+// TL: lines per CTA (one thread per line; a tuning knob).  FULL: nz is a
+// multiple of kTB (no partial block of planes)
+template <int TL, bool FULL>
+__global__ void __launch_bounds__(TL) k_thomas_f32(Thomas32Args a, const int* __restrict__ skip) {
+  constexpr int kTL = TL;
   if (skip && *skip) return;
   // coefficients of the z operator in shared memory: {M_k, lambda Kd_k,
   // lower, upper} with the off-diagonals negated (lambda-scaled), and the
@@ -1000,10 +1001,20 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
       ta.singular_possible = singular ? 1 : 0;
       ta.fmax = sc + 2;
       const long long lines = (long long)nx * ny;
-      if (nz % kTB == 0)
-        k_thomas_f32<true><<<(unsigned)((lines + kTL - 1) / kTL), kTL, 0, s>>>(ta, skip);
-      else
-        k_thomas_f32<false><<<(unsigned)((lines + kTL - 1) / kTL), kTL, 0, s>>>(ta, skip);
+      const bool full = nz % kTB == 0;
+      if (p->thomas_tl == 64) {
+        const unsigned g = (unsigned)((lines + 63) / 64);
+        if (full)
+          k_thomas_f32<64, true><<<g, 64, 0, s>>>(ta, skip);
+        else
+          k_thomas_f32<64, false><<<g, 64, 0, s>>>(ta, skip);
+      } else {
+        const unsigned g = (unsigned)((lines + 127) / 128);
+        if (full)
+          k_thomas_f32<128, true><<<g, 128, 0, s>>>(ta, skip);
+        else
+          k_thomas_f32<128, false><<<g, 128, 0, s>>>(ta, skip);
+      }
       FDI_LAUNCH_CHECK(p);
     }
     // back y: F2 [z][i][j] -> F4 [z][y][i]

@@ -366,6 +366,7 @@ fdi_status fdi_plan_create(const double* const faces[3], const int n[3], const f
     free_plan(p);
     return st;
   }
+  apply_tuning(p);  // a configuration autotuned earlier for this grid shape
   *out = p;
   return FDI_OK;
 }

@@ -12,6 +12,10 @@
 // reads a device "done" flag and returns at once when the previous check has
 // converged, so the whole solve is enqueued without a host round trip.
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "fdi_internal.h"
 
@@ -101,6 +105,36 @@ fdi_status field_solve(fdi_plan* p, int field, double sigma, double lambda, cons
   return FDI_OK;
 }
 
+// Autotuned transform / Thomas configurations per (grid shape, precision),
+// applied to plans created later with the same shape.
+namespace {
+struct TuneKey {
+  int n0, n1, n2, prec, grid;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(n0, n1, n2, prec, grid) < std::tie(o.n0, o.n1, o.n2, o.prec, o.grid);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune;
+TuneKey tune_key(const fdi_plan* p) { return TuneKey{p->n[0], p->n[1], p->n[2], (int)p->prec, (int)p->grid}; }
+}  // namespace
+
+void forget_batch_graph(const fdi_plan* p);
+
+void remember_tuning(const fdi_plan* p) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[tune_key(p)] = {p->tc_cluster, p->thomas_tl};
+}
+
+void apply_tuning(fdi_plan* p) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(tune_key(p));
+  if (it != g_tune.end()) {
+    p->tc_cluster = it->second.first;
+    p->thomas_tl = it->second.second;
+  }
+}
+
 void invalidate_graph(fdi_plan* p) {
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   p->gexec = nullptr;
@@ -109,6 +143,7 @@ void invalidate_graph(fdi_plan* p) {
   if (p->kgraph) cudaGraphExecDestroy(p->kgraph);
   p->kgraph = nullptr;
   p->kgraph_precond = -1;
+  forget_batch_graph(p);
 }
 
 namespace {
@@ -178,7 +213,161 @@ fdi_status field_solve_entry(fdi_plan* p, int field, double sigma, double lambda
   return FDI_OK;
 }
 
+// ---- batched solves: independent plans run concurrently on a pool of streams ----
+
+constexpr int kBatchStreams = 8;
+
+struct StreamPool {
+  cudaStream_t st[kBatchStreams] = {};
+  cudaEvent_t done[kBatchStreams] = {};
+  cudaEvent_t fork = nullptr;
+  bool ok = false;
+};
+
+std::mutex g_pool_mu;
+std::map<int, StreamPool> g_pools;
+
+StreamPool* stream_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  StreamPool& sp = g_pools[dev];
+  if (!sp.ok) {
+    for (int k = 0; k < kBatchStreams; ++k) {
+      if (cudaStreamCreateWithFlags(&sp.st[k], cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+      if (cudaEventCreateWithFlags(&sp.done[k], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    }
+    if (cudaEventCreateWithFlags(&sp.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    sp.ok = true;
+  }
+  return &sp;
+}
+
+// Fork from s onto the pool, one stream per distinct plan (a plan appearing
+// twice keeps one stream, so its workspace is used in order), join back on s.
+fdi_status enqueue_batch(StreamPool* sp, fdi_plan* const* plans, const double* lambdas, const double* const* rhs,
+                         double* const* out, int count, cudaStream_t s) {
+  FDI_CUDA_TRY(cudaEventRecord(sp->fork, s));
+  std::vector<int> lane(count, -1);
+  bool used[kBatchStreams] = {false};
+  int next = 0;
+  for (int i = 0; i < count; ++i) {
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) {
+        lane[i] = lane[j];
+        break;
+      }
+    if (lane[i] < 0) lane[i] = (next++) % kBatchStreams;
+    const int k = lane[i];
+    if (!used[k]) {
+      FDI_CUDA_TRY(cudaStreamWaitEvent(sp->st[k], sp->fork, 0));
+      used[k] = true;
+    }
+    plans[i]->launches = 0;
+    FDI_TRY(field_solve(plans[i], FDI_FIELD_CELL, 1.0, lambdas[i], rhs[i], out[i], sp->st[k]));
+  }
+  for (int k = 0; k < kBatchStreams; ++k)
+    if (used[k]) {
+      FDI_CUDA_TRY(cudaEventRecord(sp->done[k], sp->st[k]));
+      FDI_CUDA_TRY(cudaStreamWaitEvent(s, sp->done[k], 0));
+    }
+  return FDI_OK;
+}
+
+// Graph of a whole batch: captured on the second call with identical
+// arguments, then replayed as one launch.
+struct BatchGraph {
+  std::vector<fdi_plan*> plans;
+  std::vector<double> lambdas;
+  std::vector<const double*> rhs;
+  std::vector<double*> out;
+  cudaStream_t s = nullptr;
+  bool seen = false;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<long long> launches;
+};
+
+std::mutex g_batch_mu;
+BatchGraph g_batch;
+
+bool same_batch(const BatchGraph& g, fdi_plan* const* plans, const double* lambdas, const double* const* rhs,
+                double* const* out, int count, cudaStream_t s) {
+  if ((int)g.plans.size() != count || g.s != s) return false;
+  for (int i = 0; i < count; ++i)
+    if (g.plans[i] != plans[i] || g.lambdas[i] != lambdas[i] || g.rhs[i] != rhs[i] || g.out[i] != out[i]) return false;
+  return true;
+}
+
 }  // namespace
+
+// drop the batch graph if it involves this plan (plan destroyed or changed)
+void forget_batch_graph(const fdi_plan* p) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (fdi_plan* q : g_batch.plans)
+    if (q == p) {
+      if (g_batch.exec) cudaGraphExecDestroy(g_batch.exec);
+      g_batch = BatchGraph();
+      return;
+    }
+}
+
+fdi_status batch_solve(fdi_plan* const* plans, const double* lambdas, const double* const* rhs, double* const* out,
+                       int count, cudaStream_t s) {
+  StreamPool* sp = stream_pool();
+  if (!sp) {
+    set_error("could not create the batch stream pool");
+    return FDI_ERR_CUDA;
+  }
+  bool graphs = s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+  for (int i = 0; i < count; ++i) graphs = graphs && plans[i]->use_graphs && !plans[i]->timing;
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  if (!graphs) return enqueue_batch(sp, plans, lambdas, rhs, out, count, s);
+  if (same_batch(g_batch, plans, lambdas, rhs, out, count, s)) {
+    if (g_batch.exec) {
+      FDI_CUDA_TRY(cudaGraphLaunch(g_batch.exec, s));
+      for (int i = 0; i < count; ++i) plans[i]->launches = g_batch.launches[i];
+      return FDI_OK;
+    }
+    // second identical call: capture the fork / solves / join
+    FDI_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    fdi_status st = enqueue_batch(sp, plans, lambdas, rhs, out, count, s);
+    cudaGraph_t gr = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &gr);
+    if (st != FDI_OK || e != cudaSuccess || !gr) {
+      if (gr) cudaGraphDestroy(gr);
+      cudaGetLastError();
+      g_batch = BatchGraph();
+      if (st != FDI_OK) return st;
+      return enqueue_batch(sp, plans, lambdas, rhs, out, count, s);
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      g_batch = BatchGraph();
+      return enqueue_batch(sp, plans, lambdas, rhs, out, count, s);
+    }
+    g_batch.exec = ex;
+    g_batch.launches.assign(count, 0);
+    for (int i = 0; i < count; ++i) g_batch.launches[i] = plans[i]->launches;
+    FDI_CUDA_TRY(cudaGraphLaunch(ex, s));
+    return FDI_OK;
+  }
+  // new arguments: run eagerly and remember them
+  if (g_batch.exec) cudaGraphExecDestroy(g_batch.exec);
+  g_batch = BatchGraph();
+  fdi_status st = enqueue_batch(sp, plans, lambdas, rhs, out, count, s);
+  if (st == FDI_OK) {
+    g_batch.plans.assign(plans, plans + count);
+    g_batch.lambdas.assign(lambdas, lambdas + count);
+    g_batch.rhs.assign(rhs, rhs + count);
+    g_batch.out.assign(out, out + count);
+    g_batch.s = s;
+    g_batch.seen = true;
+  }
+  return st;
+}
 
 }  // namespace fdi
 
@@ -214,11 +403,67 @@ fdi_status fdi_helmholtz_solve_batched(fdi_plan* const* plans, const double* lam
     if (st != FDI_OK) return st;
     if (!rhs[i] || !out[i]) return FDI_ERR_INVALID_ARG;
   }
-  for (int i = 0; i < count; ++i) {
-    fdi_status st = field_solve_entry(plans[i], FDI_FIELD_CELL, 1.0, lambdas[i], rhs[i], out[i],
-                                      (cudaStream_t)stream);
+  if (count == 0) return FDI_OK;
+  return batch_solve(plans, lambdas, rhs, out, count, (cudaStream_t)stream);
+}
+
+fdi_status fdi_plan_set_thomas_config(fdi_plan* plan, int lines_per_cta) {
+  if (!plan || (lines_per_cta != 64 && lines_per_cta != 128)) return FDI_ERR_INVALID_ARG;
+  plan->thomas_tl = lines_per_cta;
+  invalidate_graph(plan);
+  return FDI_OK;
+}
+
+fdi_status fdi_plan_autotune(fdi_plan* plan, double lambda, const double* rhs, double* out, int reps,
+                             int* cluster_out, int* thomas_tl_out, fdi_stream_t stream) {
+  fdi_status st = validate_field_args(plan, FDI_FIELD_CELL, 1.0, lambda);
+  if (st != FDI_OK) return st;
+  if (!rhs || !out || rhs == out || reps < 1 || reps > 1000) return FDI_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (plan->prec != FDI_PREC_FP64) {
+    const int clusters[3] = {1, 2, 4};
+    const int tls[2] = {64, 128};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    FDI_CUDA_TRY(cudaEventCreate(&e0));
+    FDI_CUDA_TRY(cudaEventCreate(&e1));
+    float best = 0.f;
+    int best_c = plan->tc_cluster, best_t = plan->thomas_tl;
+    const bool timing = plan->timing;
+    plan->timing = false;
+    for (int ci = 0; ci < 3 && st == FDI_OK; ++ci) {
+      for (int ti = 0; ti < 2 && st == FDI_OK; ++ti) {
+        plan->tc_cluster = clusters[ci];
+        plan->thomas_tl = tls[ti];
+        st = field_solve(plan, FDI_FIELD_CELL, 1.0, lambda, rhs, out, s);  // warm-up
+        if (st != FDI_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == FDI_OK; ++r) st = field_solve(plan, FDI_FIELD_CELL, 1.0, lambda, rhs, out, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+          set_error("autotune: timing event failed");
+          st = FDI_ERR_CUDA;
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best == 0.f || ms < best) {
+          best = ms;
+          best_c = clusters[ci];
+          best_t = tls[ti];
+        }
+      }
+    }
+    plan->timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    plan->tc_cluster = best_c;
+    plan->thomas_tl = best_t;
+    invalidate_graph(plan);
     if (st != FDI_OK) return st;
+    remember_tuning(plan);
   }
+  if (cluster_out) *cluster_out = plan->tc_cluster;
+  if (thomas_tl_out) *thomas_tl_out = plan->thomas_tl;
   return FDI_OK;
 }
 

@@ -44,6 +44,8 @@ SIGNATURES = {
     "fdi_plan_set_stokes_preconditioner": (_i, [_vp, _i]),
     "fdi_eigen_noalloc": (_i, [C.POINTER(_d), _i, _i, _i, _i, _vp, _vp, _vp, C.POINTER(_i), _vp]),
     "fdi_plan_set_graphs": (_i, [_vp, _i]),
+    "fdi_plan_set_thomas_config": (_i, [_vp, _i]),
+    "fdi_plan_autotune": (_i, [_vp, _d, _vp, _vp, _i, C.POINTER(_i), C.POINTER(_i), _vp]),
     "fdi_plan_enable_timing": (_i, [_vp, _i]),
     "fdi_plan_kernel_times": (_i, [_vp, _i, C.POINTER(C.c_char_p), C.POINTER(_d), C.POINTER(C.c_longlong),
                                    C.POINTER(_i)]),
@@ -240,6 +242,19 @@ def set_stokes_preconditioner(plan: Plan, mode: int):
 
 def set_transform_config(plan: Plan, cluster: int):
     _check(load().fdi_plan_set_transform_config(plan.handle, int(cluster)), "fdi_plan_set_transform_config")
+
+
+def set_thomas_config(plan: Plan, lines_per_cta: int):
+    _check(load().fdi_plan_set_thomas_config(plan.handle, int(lines_per_cta)), "fdi_plan_set_thomas_config")
+
+
+def autotune(plan: Plan, lam, rhs, out, reps=3, stream=None):
+    """Time the transform / Thomas configurations on this plan, keep the fastest;
+    returns (cluster, thomas_lines_per_cta)."""
+    c, t = C.c_int(0), C.c_int(0)
+    _check(load().fdi_plan_autotune(plan.handle, float(lam), _ptr(rhs), _ptr(out), int(reps), C.byref(c), C.byref(t),
+                                    _stream(stream)), "fdi_plan_autotune")
+    return c.value, t.value
 
 
 def set_graphs(plan: Plan, on=True):
