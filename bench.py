@@ -289,6 +289,40 @@ def run_stokes(fdi, torch, prec, n, reps, warm, stream):
     return out
 
 
+def run_batch(fdi, torch, prec, count, reps, stream):
+    """Batched Helmholtz solves over uneven stretched grids (shapes from
+    {32..160} with aspect up to 1:4, beta ~ U[1,2], lambda log-uniform in
+    [1e-4, 1], seed 0; RHS seeds 1..count): grid-points/s of whole batches
+    (concurrent plans, one graph launch per batch after the first two calls)."""
+    probs = workloads.mixed_shape_batch(count, 0)
+    plans, lams, rhs, outs = [], [], [], []
+    for q, (nn, beta, lam) in enumerate(probs):
+        faces = [workloads.tanh_faces(nn[d], beta) for d in range(3)]
+        plans.append(fdi.plan_create(faces, nn, prec=prec))
+        rhs.append(torch.from_numpy(workloads.rhs_uniform(nn[::-1], q + 1)).cuda())
+        outs.append(torch.empty_like(rhs[-1]))
+        lams.append(lam)
+    pts = float(sum(np.prod(nn) for nn, _, _ in probs))
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            fdi.helmholtz_solve_batched(plans, lams, rhs, outs, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(reps):
+            fdi.helmholtz_solve_batched(plans, lams, rhs, outs, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    worst = max(fdi.last_result(pl)[2] for pl in plans)
+    ok = all(fdi.last_result(pl)[3] == 0 for pl in plans)
+    for pl in plans:
+        pl.destroy()
+    return {"value": pts / (ms * 1e-3), "unit": "grid-pts/s", "ms_per_batch": ms, "solves": count,
+            "points": pts, "worst_rel_residual": worst, "all_converged": ok, "reps": reps}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -301,6 +335,7 @@ def main():
     ap.add_argument("--cluster", type=int, default=None, help="tensor-core transform cluster size (1, 2, 4)")
     ap.add_argument("--stokes-n", type=int, default=64, help="Stokes latency grid (0: skip)")
     ap.add_argument("--stokes-reps", type=int, default=10)
+    ap.add_argument("--batch", type=int, default=64, help="batched uneven-grid solves per batch (0: skip)")
     args = ap.parse_args()
     n = (args.n, args.n, args.n)
     P = n[0] * n[1] * n[2]
@@ -410,6 +445,15 @@ def main():
                 stokes[name] = run_stokes(fdi, torch, prec, args.stokes_n, args.stokes_reps, 2, stream)
             except fdi.FdiError as e:
                 stokes[name] = {"error": str(e)}
+    batch = None
+    if args.batch > 0:
+        batch = {"config": f"{args.batch} Helmholtz solves, grids from {{32,48,64,96,128,160}}^3 with aspect <= 4, "
+                           "beta ~ U[1,2], lambda log-uniform [1e-4, 1], seed 0"}
+        for name in args.arms.split(","):
+            try:
+                batch[name] = run_batch(fdi, torch, precs[name][0], args.batch, 5, stream)
+            except fdi.FdiError as e:
+                batch[name] = {"error": str(e)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t = oracle_tpt_time(n)
@@ -430,6 +474,7 @@ def main():
         "clocks": best["clocks"],
         "stokes_latency": ({"config": f"MAC {args.stokes_n}^3, tanh {BETA}, no-slip, Re 1000, Gaussian forcing",
                             **stokes} if stokes is not None else None),
+        "batched": batch,
         "kernels": {k: {kk: round(vv, 4) if isinstance(vv, float) else vv for kk, vv in e.items()
                         if kk in ("achieved", "unit", "frac", "avg_launch_ms", "launches", "tensor_frac")}
                     for k, e in per_kernel.items()},

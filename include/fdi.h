@@ -246,6 +246,82 @@ const char* fdi_last_error_message(void);
 
 const char* fdi_status_string(fdi_status s);
 
+/* ---------------------------------------------------------------------------
+ * Serving runtime (no counterpart in the paper, which applies the inverses
+ * inside its own time stepper): a request loop for the Stokes-inverse
+ * applications that time-stepper-based Newton and Arnoldi iterations issue
+ * (Sec. 1-2), with uneven grids and differing dt / Re.  Plans and eigenbases
+ * stay resident in a cache keyed by (n, beta, precision); requests are
+ * admitted in FIFO order when their footprint (plan, if not cached, plus
+ * fields) fits the device-memory budget, idle plans being evicted least
+ * recently used; `slots` worker threads with one CUDA stream each run admitted
+ * requests concurrently (continuous batching: a request arriving while others
+ * run starts as soon as a slot and memory free up).  Each request is solved
+ * exactly as a lone fdi_stokes_solve on a plan of its grid, so its result does
+ * not depend on the mix.
+ * ------------------------------------------------------------------------- */
+typedef struct fdi_server fdi_server;
+
+/* One Stokes-inverse request on the no-slip unit box with n[d] cells per
+ * direction (2 <= n[d] <= 256), faces x_i = (1 + tanh(beta (2i/n - 1)) /
+ * tanh(beta)) / 2 in every direction (beta = 0: uniform), the staggered MAC
+ * unknowns of fdi_stokes_solve, time step dt > 0, Reynolds number Re > 0,
+ * precision FDI_PREC_FP64 or FDI_PREC_MIXED_F16.  f, u, p are HOST arrays in
+ * the MAC shapes (u: (n_x-1) n_y n_z, v: n_x (n_y-1) n_z, w: n_x n_y (n_z-1),
+ * p: n_x n_y n_z; x fastest), owned by the caller and left untouched (f) /
+ * written (u, p) until the request is done. */
+typedef struct {
+  int n[3];
+  double beta;
+  double dt, Re;
+  fdi_precision prec;
+  const double* f[3];
+  double* u[3];
+  double* p;
+} fdi_stokes_request;
+
+typedef struct {
+  int state;            /* 0 queued, 1 running, 2 done */
+  fdi_status status;    /* of the solve (valid when done) */
+  int iters;            /* BiCGstab iterations */
+  double rel_residual;  /* relative residual of the pressure system */
+  double queue_ms;      /* submission -> start */
+  double latency_ms;    /* submission -> completion (when done) */
+} fdi_stokes_result;
+
+typedef struct {
+  long long completed;
+  double p50_ms, p99_ms;    /* latency percentiles over completed requests */
+  double throughput_rps;    /* completed / (last completion - first submission) */
+  size_t peak_bytes, bytes_in_use;
+  long long plans_created, plans_evicted, plans_cached;
+} fdi_server_report;
+
+/* Device bytes a MAC Stokes plan of this size allocates (upper estimate used
+ * for admission); prec: an fdi_precision value. */
+size_t fdi_stokes_plan_bytes_estimate(const int n[3], int prec);
+
+/* Start `slots` (1..64) workers on the current device with a device-memory
+ * budget in bytes for plans plus request fields. */
+fdi_status fdi_server_create(size_t hbm_budget_bytes, int slots, fdi_server** out);
+
+/* Queue a request (returns at once).  FDI_ERR_OUT_OF_MEMORY if its footprint
+ * alone exceeds the budget; FDI_ERR_INVALID_ARG / FDI_ERR_UNSUPPORTED for bad
+ * fields.  *ticket identifies it. */
+fdi_status fdi_server_submit(fdi_server* server, const fdi_stokes_request* req, long long* ticket);
+
+/* State and result of a request; wait != 0 blocks until it is done. */
+fdi_status fdi_server_poll(fdi_server* server, long long ticket, int wait, fdi_stokes_result* res);
+
+/* Block until every submitted request is done. */
+fdi_status fdi_server_drain(fdi_server* server);
+
+/* Latency percentiles, throughput, memory and plan-cache counters. */
+fdi_status fdi_server_stats(fdi_server* server, fdi_server_report* out);
+
+/* Finish queued requests, stop the workers, free every cached plan. */
+fdi_status fdi_server_destroy(fdi_server* server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -7,11 +7,12 @@ of include/fdi.h); `fdi` is its thin ctypes binding.
 from . import fdi  # noqa: F401
 from .fdi import (  # noqa: F401
     BC_DIRICHLET, BC_NEUMANN, FIELD_CELL, FIELD_U, FIELD_V, FIELD_W, GRID_CELL, GRID_MAC, PREC_FP64,
-    PREC_MIXED_BF16, PREC_MIXED_F16, PREC_MIXED_TF32, FdiError, Plan, apply_transform, autotune, enable_timing,
+    PREC_MIXED_BF16, PREC_MIXED_F16, PREC_MIXED_TF32, FdiError, Plan, Server, apply_transform, autotune,
+    enable_timing,
     field_solve,
     helmholtz_solve, helmholtz_solve_batched, kernel_times, laplace_solve, last_launch_count, last_result,
     plan_create, plan_destroy, reset_kernel_times, set_graphs, set_stokes_preconditioner, set_thomas_config,
     set_transform_config,
-    status_string,
+    status_string, stokes_plan_bytes_estimate,
     stokes_solve,
 )

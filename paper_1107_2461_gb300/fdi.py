@@ -22,6 +22,25 @@ GRID_CELL, GRID_MAC = 0, 1
 PREC_FP64, PREC_MIXED_TF32, PREC_MIXED_BF16, PREC_MIXED_F16 = 0, 1, 2, 3
 FIELD_CELL, FIELD_U, FIELD_V, FIELD_W = 0, 1, 2, 3
 
+class StokesRequest(C.Structure):
+    """fdi_stokes_request (host arrays in the MAC shapes)."""
+    _fields_ = [("n", C.c_int * 3), ("beta", C.c_double), ("dt", C.c_double), ("Re", C.c_double),
+                ("prec", C.c_int), ("f", C.c_void_p * 3), ("u", C.c_void_p * 3), ("p", C.c_void_p)]
+
+
+class StokesResult(C.Structure):
+    """fdi_stokes_result."""
+    _fields_ = [("state", C.c_int), ("status", C.c_int), ("iters", C.c_int), ("rel_residual", C.c_double),
+                ("queue_ms", C.c_double), ("latency_ms", C.c_double)]
+
+
+class ServerReport(C.Structure):
+    """fdi_server_report."""
+    _fields_ = [("completed", C.c_longlong), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("throughput_rps", C.c_double), ("peak_bytes", C.c_size_t), ("bytes_in_use", C.c_size_t),
+                ("plans_created", C.c_longlong), ("plans_evicted", C.c_longlong), ("plans_cached", C.c_longlong)]
+
+
 # every function declared in include/fdi.h: name -> (restype, argtypes)
 _vp = C.c_void_p
 _i = C.c_int
@@ -50,6 +69,13 @@ SIGNATURES = {
     "fdi_plan_kernel_times": (_i, [_vp, _i, C.POINTER(C.c_char_p), C.POINTER(_d), C.POINTER(C.c_longlong),
                                    C.POINTER(_i)]),
     "fdi_plan_reset_kernel_times": (_i, [_vp]),
+    "fdi_stokes_plan_bytes_estimate": (C.c_size_t, [C.POINTER(_i), _i]),
+    "fdi_server_create": (_i, [C.c_size_t, _i, C.POINTER(_vp)]),
+    "fdi_server_submit": (_i, [_vp, C.POINTER(StokesRequest), C.POINTER(C.c_longlong)]),
+    "fdi_server_poll": (_i, [_vp, C.c_longlong, _i, C.POINTER(StokesResult)]),
+    "fdi_server_drain": (_i, [_vp]),
+    "fdi_server_stats": (_i, [_vp, C.POINTER(ServerReport)]),
+    "fdi_server_destroy": (_i, [_vp]),
     "fdi_last_error_message": (C.c_char_p, []),
     "fdi_status_string": (C.c_char_p, [_i]),
 }
@@ -283,3 +309,64 @@ def reset_kernel_times(plan: Plan):
 
 def status_string(s: int) -> str:
     return load().fdi_status_string(int(s)).decode()
+
+
+class Server:
+    """Stokes-inverse serving loop (fdi_server_*): resident plan cache, admission
+    by device-memory footprint, `slots` concurrent workers.  Requests take host
+    NumPy arrays; the arrays are kept referenced until the request is done."""
+
+    def __init__(self, budget_bytes, slots=4):
+        h = C.c_void_p()
+        _check(load().fdi_server_create(int(budget_bytes), int(slots), C.byref(h)), "fdi_server_create")
+        self.handle = h.value
+        self._keep = {}
+
+    def submit(self, n, beta, dt, Re, f, u, p, prec=PREC_MIXED_F16):
+        """n: (nx, ny, nz); f, u: three contiguous float64 arrays (MAC shapes); p: cell array."""
+        for a in list(f) + list(u) + [p]:
+            if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]):
+                raise ValueError("server requests take contiguous float64 NumPy arrays")
+        r = StokesRequest()
+        r.n = (C.c_int * 3)(*[int(v) for v in n])
+        r.beta, r.dt, r.Re, r.prec = float(beta), float(dt), float(Re), int(prec)
+        r.f = (C.c_void_p * 3)(*[a.ctypes.data for a in f])
+        r.u = (C.c_void_p * 3)(*[a.ctypes.data for a in u])
+        r.p = p.ctypes.data
+        t = C.c_longlong()
+        _check(load().fdi_server_submit(self.handle, C.byref(r), C.byref(t)), "fdi_server_submit")
+        self._keep[t.value] = (f, u, p)
+        return t.value
+
+    def poll(self, ticket, wait=False):
+        res = StokesResult()
+        _check(load().fdi_server_poll(self.handle, int(ticket), 1 if wait else 0, C.byref(res)), "fdi_server_poll")
+        if res.state == 2:
+            self._keep.pop(ticket, None)
+        return {"state": res.state, "status": res.status, "iters": res.iters, "rel_residual": res.rel_residual,
+                "queue_ms": res.queue_ms, "latency_ms": res.latency_ms}
+
+    def drain(self):
+        _check(load().fdi_server_drain(self.handle), "fdi_server_drain")
+
+    def stats(self):
+        r = ServerReport()
+        _check(load().fdi_server_stats(self.handle, C.byref(r)), "fdi_server_stats")
+        return {k: getattr(r, k) for k, _ in ServerReport._fields_}
+
+    def close(self):
+        if self.handle:
+            _check(load().fdi_server_destroy(self.handle), "fdi_server_destroy")
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def stokes_plan_bytes_estimate(n, prec=PREC_MIXED_F16) -> int:
+    arr = (C.c_int * 3)(*[int(v) for v in n])
+    return int(load().fdi_stokes_plan_bytes_estimate(arr, int(prec)))
