@@ -323,6 +323,45 @@ def run_batch(fdi, torch, prec, count, reps, stream):
             "points": pts, "worst_rel_residual": worst, "all_converged": ok, "reps": reps}
 
 
+def run_serving(fdi, prec, count, rate_hz, max_n, slots):
+    """Serving trace: Poisson arrivals (rate_hz, seed 0) of Stokes-inverse
+    requests on stretched no-slip boxes (beta 1.5), cubic n uniform over
+    {48, 64, 96, 128, 160, 192, 256} up to max_n, dt log-uniform in [1e-2, 1e3],
+    Re in {100, 1000, 5000}, Gaussian forcing; host arrays in and out.  Requests
+    are submitted at their arrival times into a server with `slots` workers and
+    a 64 GB device budget; p50 / p99 latency (arrival to completion) and
+    throughput."""
+    rng = np.random.default_rng(0)
+    sizes = [v for v in (48, 64, 96, 128, 160, 192, 256) if v <= max_n]
+    arrivals = workloads.poisson_arrivals(count, rate_hz, 0)
+    reqs = []
+    for q in range(count):
+        nn = int(rng.choice(sizes))
+        dt = float(10.0 ** rng.uniform(-2.0, 3.0))
+        Re = float(rng.choice([100.0, 1000.0, 5000.0]))
+        sh = workloads.mac_shapes((nn, nn, nn))
+        f = [np.ascontiguousarray(workloads.rhs_gaussian(sh[c], 3 * q + i)) for i, c in enumerate("uvw")]
+        u = [np.zeros(sh[c]) for c in "uvw"]
+        p = np.zeros(sh["p"])
+        reqs.append(((nn, nn, nn), dt, Re, f, u, p))
+    srv = fdi.Server(64 << 30, slots)
+    t0 = time.perf_counter()
+    tickets = []
+    for q, (nn, dt, Re, f, u, p) in enumerate(reqs):
+        wait = arrivals[q] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        tickets.append(srv.submit(nn, 1.5, dt, Re, f, u, p, prec=prec))
+    srv.drain()
+    res = [srv.poll(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    return {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "throughput_rps": st["throughput_rps"],
+            "completed": st["completed"], "all_converged": all(r["status"] == 0 for r in res),
+            "worst_rel_residual": max(r["rel_residual"] for r in res), "plans_created": st["plans_created"],
+            "peak_gb": st["peak_bytes"] / 1e9}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -336,6 +375,9 @@ def main():
     ap.add_argument("--stokes-n", type=int, default=64, help="Stokes latency grid (0: skip)")
     ap.add_argument("--stokes-reps", type=int, default=10)
     ap.add_argument("--batch", type=int, default=64, help="batched uneven-grid solves per batch (0: skip)")
+    ap.add_argument("--serve", type=int, default=40, help="serving-trace requests (0: skip)")
+    ap.add_argument("--serve-max-n", type=int, default=128, help="largest cubic grid in the serving sample")
+    ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
     n = (args.n, args.n, args.n)
     P = n[0] * n[1] * n[2]
@@ -454,6 +496,17 @@ def main():
                 batch[name] = run_batch(fdi, torch, precs[name][0], args.batch, 5, stream)
             except fdi.FdiError as e:
                 batch[name] = {"error": str(e)}
+    serving = None
+    if args.serve > 0:
+        serving = {"config": f"{args.serve} Stokes-inverse requests, Poisson arrivals at 200/s (seed 0), cubic n "
+                             f"from {{48..256}} up to {args.serve_max_n}, dt log-uniform [1e-2,1e3], "
+                             f"Re in {{100,1000,5000}}, beta 1.5, {args.serve_slots} slots, 64 GB budget"}
+        for name in args.arms.split(","):
+            try:
+                serving[name] = run_serving(fdi, precs[name][0], args.serve, 200.0, args.serve_max_n,
+                                            args.serve_slots)
+            except fdi.FdiError as e:
+                serving[name] = {"error": str(e)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t = oracle_tpt_time(n)
@@ -475,6 +528,7 @@ def main():
         "stokes_latency": ({"config": f"MAC {args.stokes_n}^3, tanh {BETA}, no-slip, Re 1000, Gaussian forcing",
                             **stokes} if stokes is not None else None),
         "batched": batch,
+        "serving": serving,
         "kernels": {k: {kk: round(vv, 4) if isinstance(vv, float) else vv for kk, vv in e.items()
                         if kk in ("achieved", "unit", "frac", "avg_launch_ms", "launches", "tensor_frac")}
                     for k, e in per_kernel.items()},
