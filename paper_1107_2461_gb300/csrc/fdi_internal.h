@@ -80,6 +80,7 @@ struct fdi_plan {
   int tc_cluster = 1;               // CTAs sharing each transform-matrix chunk by TMA multicast
   int thomas_tl = 128;              // FP32 Thomas lines per CTA (64 or 128)
   float2* lam_w = nullptr;          // lambda-scaled double-float flux weights [3][3][kMaxN]
+  unsigned* d_counter = nullptr;    // ticket counter of the fused last-block reductions (zero between launches)
   double* partials = nullptr;       // reduction partials
   int npartials = 0;
   fdi::DevStatus* d_status = nullptr;

@@ -48,6 +48,15 @@ constexpr int kThreads = 256;
 
 int pitch4(int n) { return (n + 3) / 4 * 4; }
 
+// fused final reduction (see finish_if_last)
+struct FinishArgs {
+  unsigned* counter;    // zero between launches
+  const double* partials;
+  DevStatus* st;
+  double tol;
+  int kind, want_mean;
+};
+
 struct ResidArgs {
   int nx, ny, nz;
   const float2* wp[3];
@@ -71,7 +80,10 @@ struct ResidArgs {
   int sub_mean;
   int want_mean;        // accumulate sum V b and sum V (first pass) or sum V x (later passes)
   double* partials;     // per block: sum r^2, sum b^2, sum V b (or V x), sum V
+  FinishArgs fin;
 };
+
+__device__ void finish_if_last(const FinishArgs& f, int t, int nt);
 
 __device__ __forceinline__ df::F2 ld2(const float2* p) {
   float2 v = *p;
@@ -337,6 +349,7 @@ __global__ void __launch_bounds__(kResTX * kResTY, 4) k_resid_df(ResidArgs a, co
     resid_body<MODE, SIG, LO, MEAN, OUT, true>(a, sh);
   else
     resid_body<MODE, SIG, LO, MEAN, OUT, false>(a, sh);
+  finish_if_last(a.fin, threadIdx.y * kResTX + threadIdx.x, kResTX * kResTY);
 }
 
 using ResidKernel = void (*)(ResidArgs, const int*);
@@ -434,6 +447,7 @@ __global__ void __launch_bounds__(256) k_init_rhs(ResidArgs a) {
       for (int c = 0; c < 4; ++c) t[c] += sh[4 * q + c];
     for (int c = 0; c < 4; ++c) a.partials[4 * blockIdx.x + c] = t[c];
   }
+  finish_if_last(a.fin, threadIdx.x, blockDim.x);
 }
 
 // r_0 = b for unpadded fields without the mean (nx a multiple of 4): flat
@@ -492,6 +506,7 @@ __global__ void __launch_bounds__(256) k_init_rhs_flat(ResidArgs a, long long P)
     a.partials[4 * blockIdx.x + 2] = 0.0;
     a.partials[4 * blockIdx.x + 3] = 0.0;
   }
+  finish_if_last(a.fin, threadIdx.x, blockDim.x);
 }
 
 // lambda-scaled double-float flux weights of the three directions
@@ -519,38 +534,61 @@ dim3 resid_grid(int nx, int ny, int nz) {
 
 // kind 0: initial pass (b only): record the volume-weighted mean if asked
 // kind 1: first residual check; kind 2: later check (counts a refinement step)
-__global__ void k_finish_mixed(const double* __restrict__ partials, int nblocks, DevStatus* st, double tol,
-                               int kind, int want_mean, const int* __restrict__ skip) {
-  if (skip && *skip) return;
-  __shared__ double sh[4 * 8];
+// Final reduction of the per-block partials (fixed order: deterministic) and
+// the convergence bookkeeping, by one block of nt threads (t = thread index).
+// kind 0: initial pass (b only): record ||b||^2 and the volume-weighted mean
+// kind 1: first residual check; kind 2: later check (counts a refinement step)
+__device__ void finish_block(const double* __restrict__ partials, int nblocks, DevStatus* st, double tol, int kind,
+                             int want_mean, int t, int nt) {
+  __shared__ double shf[4 * 32];
   double s[4] = {0, 0, 0, 0};
-  for (int q = threadIdx.x; q < nblocks; q += blockDim.x)
-    for (int c = 0; c < 4; ++c) s[c] += partials[4 * q + c];
+  // 8 partial records per thread in flight (16-byte loads), fixed order
+  const double2* p2 = reinterpret_cast<const double2*>(partials);
+  for (int q0 = t; q0 < nblocks; q0 += 8 * nt) {
+    double2 v[8][2];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int q = q0 + u * nt;
+      if (q < nblocks) {
+        v[u][0] = p2[2 * q];
+        v[u][1] = p2[2 * q + 1];
+      } else {
+        v[u][0] = v[u][1] = make_double2(0.0, 0.0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      s[0] += v[u][0].x;
+      s[1] += v[u][0].y;
+      s[2] += v[u][1].x;
+      s[3] += v[u][1].y;
+    }
+  }
   for (int o = 16; o > 0; o >>= 1)
     for (int c = 0; c < 4; ++c) s[c] += __shfl_down_sync(0xffffffffu, s[c], o);
-  const int w = threadIdx.x / 32, ln = threadIdx.x % 32;
+  const int w = t / 32, ln = t % 32;
   if (ln == 0)
-    for (int c = 0; c < 4; ++c) sh[4 * w + c] = s[c];
+    for (int c = 0; c < 4; ++c) shf[4 * w + c] = s[c];
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  double t[4] = {0, 0, 0, 0};
-  for (int q = 0; q < (int)(blockDim.x / 32); ++q)
-    for (int c = 0; c < 4; ++c) t[c] += sh[4 * q + c];
+  if (t != 0) return;
+  double tt[4] = {0, 0, 0, 0};
+  for (int q = 0; q < nt / 32; ++q)
+    for (int c = 0; c < 4; ++c) tt[c] += shf[4 * q + c];
   if (kind == 0) {
-    st->bnorm2 = t[1];
-    if (want_mean) st->mean_b = t[2] / t[3];
+    st->bnorm2 = tt[1];
+    if (want_mean) st->mean_b = tt[2] / tt[3];
     st->rel_res = 1.0;
     st->done = 0;
     return;
   }
   // the first check (r_1 = b - A H) also measures ||b||; later checks reuse it
-  const double bn2 = kind == 1 ? t[1] : st->bnorm2;
-  const double rel = bn2 > 0.0 ? sqrt(t[0] / bn2) : sqrt(t[0]);
+  const double bn2 = kind == 1 ? tt[1] : st->bnorm2;
+  const double rel = bn2 > 0.0 ? sqrt(tt[0] / bn2) : sqrt(tt[0]);
   if (kind == 1)
     st->refine_steps = 0;
   else
     st->refine_steps += 1;
-  if (want_mean) st->scal[0] = t[2] / t[3];  // volume-weighted mean of the current solution
+  if (want_mean) st->scal[0] = tt[2] / tt[3];  // volume-weighted mean of the current solution
   st->rel_res = rel;
   st->bnorm2 = bn2;
   if (!isfinite(rel)) {
@@ -559,6 +597,30 @@ __global__ void k_finish_mixed(const double* __restrict__ partials, int nblocks,
   } else {
     st->done = rel <= tol ? 1 : 0;
   }
+}
+
+// The last block of a reduction grid to finish (atomic ticket after its
+// partials are visible) runs finish_block and re-arms the ticket counter, so
+// the reduction needs no second launch.  Every block has passed its own skip
+// test before the last one can change the done flag.
+__device__ void finish_if_last(const FinishArgs& f, int t, int nt) {
+  __shared__ int amlast;
+  const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+  if (t == 0) {
+    __threadfence();
+    amlast = atomicAdd(f.counter, 1u) == nb - 1 ? 1 : 0;
+  }
+  __syncthreads();
+  if (!amlast) return;
+  __threadfence();
+  finish_block(f.partials, (int)nb, f.st, f.tol, f.kind, f.want_mean, t, nt);
+  if (t == 0) *f.counter = 0u;
+}
+
+__global__ void k_finish_mixed(const double* __restrict__ partials, int nblocks, DevStatus* st, double tol,
+                               int kind, int want_mean, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  finish_block(partials, nblocks, st, tol, kind, want_mean, threadIdx.x, blockDim.x);
 }
 
 struct Thomas32Args {
@@ -857,6 +919,8 @@ fdi_status mixed_setup(fdi_plan* p) {
   FDI_CUDA_TRY(cudaMalloc(&p->d_err, sizeof(int)));
   FDI_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
   FDI_CUDA_TRY(cudaMalloc(&p->lam_w, (size_t)9 * kMaxN * sizeof(float2)));
+  FDI_CUDA_TRY(cudaMalloc(&p->d_counter, 4 * sizeof(unsigned)));
+  FDI_CUDA_TRY(cudaMemset(p->d_counter, 0, 4 * sizeof(unsigned)));
   return FDI_OK;
 }
 
@@ -932,15 +996,11 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     a0.sub_mean = 0;
     a0.want_mean = singular ? 1 : 0;
     a0.rmax = p->d_scales + 0;
+    a0.fin = FinishArgs{p->d_counter, p->partials, p->d_status, p->tol, 0, singular ? 1 : 0};
     if (px == nx && !singular && (reinterpret_cast<uintptr_t>(b) & 15u) == 0)
       k_init_rhs_flat<<<iblocks, 256, 0, s>>>(a0, f.P);
     else
       k_init_rhs<<<iblocks, 256, 0, s>>>(a0);
-    FDI_LAUNCH_CHECK(p);
-  }
-  {
-    FDI_KTIMER(p, "reduce", s);
-    k_finish_mixed<<<1, 256, 0, s>>>(p->partials, iblocks, p->d_status, p->tol, 0, singular ? 1 : 0, nullptr);
     FDI_LAUNCH_CHECK(p);
   }
 
@@ -1064,15 +1124,10 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
       ak.r_lo = r1l;
       ak.out = out;
       ak.rmax = sc_next + 0;
+      ak.fin = FinishArgs{p->d_counter, p->partials, p->d_status, p->tol, round == 0 ? 1 : 2, singular ? 1 : 0};
       const bool write_out = !singular && round > 0;
       ResidKernel kern = resid_kernel(ra.sig_mode, round == 0 ? 0 : 1, round >= 2, singular, write_out);
       kern<<<rgrid, dim3(kResTX, kResTY), 0, s>>>(ak, skip);
-      FDI_LAUNCH_CHECK(p);
-    }
-    {
-      FDI_KTIMER(p, "reduce", s);
-      k_finish_mixed<<<1, 256, 0, s>>>(p->partials, rblocks, p->d_status, p->tol, round == 0 ? 1 : 2,
-                                       singular ? 1 : 0, skip);
       FDI_LAUNCH_CHECK(p);
     }
   }

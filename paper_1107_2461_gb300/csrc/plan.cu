@@ -180,6 +180,7 @@ void free_plan(fdi_plan* p) {
   if (p->kpartials) cudaFree(p->kpartials);
   if (p->xdf) cudaFree(p->xdf);
   if (p->wr1) cudaFree(p->wr1);
+  if (p->d_counter) cudaFree(p->d_counter);
   if (p->d_scales) cudaFree(p->d_scales);
   if (p->lam_w) cudaFree(p->lam_w);
   if (p->d_err) cudaFree(p->d_err);
