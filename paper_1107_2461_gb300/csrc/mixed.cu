@@ -908,10 +908,11 @@ fdi_status mixed_setup(fdi_plan* p) {
     szr = std::max(szr, (size_t)f.n[2] * f.n[1] * pitch4(f.n[0]));
     szf = std::max(szf, (size_t)f.n[2] * f.n[0] * pitch4(f.n[1]));
   }
-  FDI_CUDA_TRY(cudaMalloc(&p->wf[0], szr * sizeof(float)));   // r, reused as F4
-  FDI_CUDA_TRY(cudaMalloc(&p->wf[1], szf * sizeof(float)));   // F1
-  FDI_CUDA_TRY(cudaMalloc(&p->wf[2], szf * sizeof(float)));   // F2 / F3
-  FDI_CUDA_TRY(cudaMalloc(&p->wf[3], szf * sizeof(float)));   // Thomas scratch
+  const size_t szw = std::max(szr, szf);  // F1 and F4 take either orientation
+  FDI_CUDA_TRY(cudaMalloc(&p->wf[0], szw * sizeof(float)));   // r, reused as F4
+  FDI_CUDA_TRY(cudaMalloc(&p->wf[1], szw * sizeof(float)));   // F1
+  FDI_CUDA_TRY(cudaMalloc(&p->wf[2], szw * sizeof(float)));   // F2 / F3
+  FDI_CUDA_TRY(cudaMalloc(&p->wf[3], szw * sizeof(float)));   // Thomas scratch
   FDI_CUDA_TRY(cudaMalloc(&p->xdf, (size_t)p->Pmax * 3 * sizeof(float)));  // planes H, L, low part of L
   FDI_CUDA_TRY(cudaMalloc(&p->wr1, szr * 2 * sizeof(float)));              // r_1 as (hi, lo) planes
   p->wr1_plane = (long long)szr;
@@ -945,6 +946,10 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
   float* F2 = p->wf[2];
   float* CS = p->wf[3];
   float* F4 = p->wf[0];
+  // x and y extents that are multiples of 128 allow every pass to write
+  // row-major (TMA-stored) outputs: the y and back-x passes then read their
+  // inputs with the contraction index strided (MN-major slots)
+  const bool mn = nx % 128 == 0 && ny % 128 == 0;
   float* xH = reinterpret_cast<float*>(p->xdf);
   float* xL = xH + f.P;
   float* xLL = xL + f.P;
@@ -1020,17 +1025,29 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     t.mode = TC_OUT_F32;
     t.n_out = nx;
     t.out_f32 = F1;
-    t.S = ny;
-    t.slab_stride = (long long)nx * py;
-    t.row_stride = 1;
-    t.col_stride = py;
+    if (mn) {
+      // F1 [z][y][i] (row-major, TMA stores)
+      t.S = t.R;
+      t.slab_stride = 0;
+      t.row_stride = px;
+      t.col_stride = 1;
+    } else {
+      // F1 [z][i][y] (transposed)
+      t.S = ny;
+      t.slab_stride = (long long)nx * py;
+      t.row_stride = 1;
+      t.col_stride = py;
+    }
     t.scale_out = sc + 1;
     FDI_TRY(launch_tc_transform(p, mx->fwd, t, "transform_xf_tc", s));
-    // forward y: F1 [z][i][y] -> F2 [z][i][j]
+    // forward y: F1 -> F2 [z][i][j]; rows (z, i), contraction over y
     t.in = F1;
     t.R = (long long)nz * nx;
     t.K = ny;
-    t.in_pitch = py;
+    t.in_pitch = mn ? px : py;
+    t.a_mn = mn ? 1 : 0;          // F1 [z][y][i]: i contiguous
+    t.a_mslab = nx;
+    t.a_rows = (long long)nz * ny;
     t.scale_in = sc + 1;
     t.n_out = ny;
     t.out_f32 = F2;
@@ -1077,25 +1094,39 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
       }
       FDI_LAUNCH_CHECK(p);
     }
-    // back y: F2 [z][i][j] -> F4 [z][y][i]
+    // back y: F2 [z][i][j] -> F4
     t.in = F2;
     t.R = (long long)nz * nx;
     t.K = ny;
     t.in_pitch = py;
+    t.a_mn = 0;
     t.scale_in = sc + 2;
     t.n_out = ny;
     t.out_f32 = F4;
-    t.S = nx;
-    t.slab_stride = (long long)ny * px;
-    t.row_stride = 1;
-    t.col_stride = px;
+    if (mn) {
+      // F4 [z][i][y] (row-major, TMA stores)
+      t.S = t.R;
+      t.slab_stride = 0;
+      t.row_stride = py;
+      t.col_stride = 1;
+    } else {
+      // F4 [z][y][i] (transposed)
+      t.S = nx;
+      t.slab_stride = (long long)ny * px;
+      t.row_stride = 1;
+      t.col_stride = px;
+    }
     t.scale_out = sc + 3;
     FDI_TRY(launch_tc_transform(p, my->bwd, t, "transform_yb_tc", s));
-    // back x: F4 [z][y][i] -> H (first solve), L (first correction) or L += (later ones), [z][y][x]
+    // back x: F4 -> H (first solve), L (first correction) or L += (later ones), [z][y][x];
+    // rows (z, y), contraction over i
     t.in = F4;
     t.R = (long long)nz * ny;
     t.K = nx;
-    t.in_pitch = px;
+    t.in_pitch = mn ? py : px;
+    t.a_mn = mn ? 1 : 0;          // F4 [z][i][y]: y contiguous
+    t.a_mslab = ny;
+    t.a_rows = (long long)nz * nx;
     t.scale_in = sc + 3;
     t.mode = round <= 1 ? TC_OUT_F32 : TC_OUT_DF_ADD;
     t.n_out = nx;

@@ -245,6 +245,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int ct = (warp - 2) * 32 + lane;  // 0..255
     const float sA = scale_from_max(a.scale_in ? *a.scale_in : 1.0f);
     const int c8 = ct & 3;                  // 32-byte group within the 128-byte row
+    // the two (row, 8-wide k group) pieces this thread converts per chunk:
+    // K-major slots: rows ct/4 and ct/4 + 64, k group c8; MN-major slots: row
+    // ct % 128, k groups 2 (ct / 128) and 2 (ct / 128) + 1
+    const bool a_mn = a.a_mn != 0;
+    const int row_q[2] = {a_mn ? (ct & 127) : (ct >> 2), a_mn ? (ct & 127) : (ct >> 2) + 64};
+    const int kofs_q[2] = {a_mn ? (ct >> 7) * 16 : c8 * 8, a_mn ? (ct >> 7) * 16 + 8 : c8 * 8};
     const long long total = my_iters * nK;
     int kc = 0;
     for (long long gi = 0; gi < total && !s_abort; ++gi) {
@@ -259,23 +265,32 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       const uint8_t* src = smem + A32_OFF + sa * A32_BYTES;
       float v[2][8];
+      if (!a_mn) {
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int row = (ct >> 2) + 64 * q;
-        const float4 x0 = *reinterpret_cast<const float4*>(src + row * 128 + (((2 * c8) ^ (row & 7)) << 4));
-        const float4 x1 = *reinterpret_cast<const float4*>(src + row * 128 + (((2 * c8 + 1) ^ (row & 7)) << 4));
-        v[q][0] = x0.x; v[q][1] = x0.y; v[q][2] = x0.z; v[q][3] = x0.w;
-        v[q][4] = x1.x; v[q][5] = x1.y; v[q][6] = x1.z; v[q][7] = x1.w;
+        for (int q = 0; q < 2; ++q) {
+          const int row = row_q[q];
+          const float4 x0 = *reinterpret_cast<const float4*>(src + row * 128 + (((2 * c8) ^ (row & 7)) << 4));
+          const float4 x1 = *reinterpret_cast<const float4*>(src + row * 128 + (((2 * c8 + 1) ^ (row & 7)) << 4));
+          v[q][0] = x0.x; v[q][1] = x0.y; v[q][2] = x0.z; v[q][3] = x0.w;
+          v[q][4] = x1.x; v[q][5] = x1.y; v[q][6] = x1.z; v[q][7] = x1.w;
+        }
+      } else {
+        // MN-major slot [32 k][128 m]: a warp reads 32 consecutive m of one k
+        const float* sf = reinterpret_cast<const float*>(src);
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v[q][e] = sf[(kofs_q[q] + e) * BM + row_q[q]];
       }
       if (!tc::mbar_wait(&empty[s], ph ^ 1, &s_abort)) {
         atomicExch(a.err, 4);
         break;
       }
       uint8_t* st = smem + s * STAGE_BYTES;
-      const int k0 = kc * BK + c8 * 8;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        const int row = (ct >> 2) + 64 * q;
+        const int row = row_q[q];
+        const int k0 = kc * BK + kofs_q[q];
         uint32_t hw[4], lw[4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
@@ -287,7 +302,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           hw[e / 2] = pack_half2(h0, h1);
           lw[e / 2] = pack_half2(l0, l1);
         }
-        const uint32_t off = tc::sw64_offset(row, c8 * 8);
+        const uint32_t off = tc::sw64_offset(row, kofs_q[q]);
         *reinterpret_cast<uint4*>(st + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
         *reinterpret_cast<uint4*>(st + A_BYTES + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
@@ -316,7 +331,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             break;
           }
           tc::mbar_expect_tx(&a_full[sa], (uint32_t)A32_BYTES);
-          tc::tma_load_2d(tc::smem_u32(smem + A32_OFF + sa * A32_BYTES), &tmA, kc * BK, row0, &a_full[sa]);
+          if (!a.a_mn) {
+            tc::tma_load_2d(tc::smem_u32(smem + A32_OFF + sa * A32_BYTES), &tmA, kc * BK, row0, &a_full[sa]);
+          } else {
+            // MN-major input: box of 128 consecutive m (one slab) x 32 k rows
+            const long long slab = (long long)row0 / a.a_mslab;
+            tc::tma_load_2d(tc::smem_u32(smem + A32_OFF + sa * A32_BYTES), &tmA, (int)((long long)row0 % a.a_mslab),
+                            (int)(slab * a.K + (long long)kc * BK), &a_full[sa]);
+          }
         }
       }
     }
@@ -675,14 +697,21 @@ fdi_status launch_tc_transform(fdi_plan* p, const TcMatrix& m, TcArgs args, cons
     return FDI_ERR_CUDA;
   }
   CUtensorMap mapA;
+  if (args.a_mn && (args.a_mslab % BM != 0 || args.R % args.a_mslab != 0 || args.a_mslab > args.in_pitch ||
+                    args.a_rows < (args.R / args.a_mslab) * (long long)args.K || args.a_rows > 0x7fffffffLL)) {
+    set_error("MN-major transform input: slabs must hold whole 128-row tiles");
+    return FDI_ERR_INVALID_ARG;
+  }
   {
-    cuuint64_t dims[2] = {(cuuint64_t)args.in_pitch, (cuuint64_t)args.R};
+    // K-major: rows of K contiguous values, 32 x 128 boxes, 128-byte swizzle.
+    // MN-major: a_rows rows of in_pitch values (m contiguous), 128 x 32 boxes.
+    cuuint64_t dims[2] = {(cuuint64_t)args.in_pitch, (cuuint64_t)(args.a_mn ? args.a_rows : args.R)};
     cuuint64_t strides[1] = {(cuuint64_t)args.in_pitch * sizeof(float)};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+    cuuint32_t box[2] = {(cuuint32_t)(args.a_mn ? BM : BK), (cuuint32_t)(args.a_mn ? BK : BM)};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(&mapA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(args.in), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, args.a_mn ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
       set_error("cuTensorMapEncodeTiled failed for a transform input");
       return FDI_ERR_CUDA;

@@ -28,10 +28,15 @@ inline int tc_cluster_index(int c) { return c == 4 ? 2 : (c == 2 ? 1 : 0); }
 
 struct TcArgs {
   // input: rows of K contiguous FP32 values, row r at in + r * in_pitch
+  // (K-major); or, with a_mn, the transposed layout: element (r, k) at
+  //   in + ((r / a_mslab) * K + k) * in_pitch + r % a_mslab
+  // (a_rows rows of in_pitch values, a_mslab % 128 == 0)
   const float* in = nullptr;
   long long R = 0;
   int K = 0;
   int in_pitch = 0;
+  int a_mn = 0;
+  long long a_mslab = 0, a_rows = 0;
   const float* scale_in = nullptr;  // device: max |in| (sets the fp16 scaling)
   // output: element (r, k) of an FP32 field at
   //   (r / S) * slab_stride + (r % S) * row_stride + k * col_stride
