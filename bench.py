@@ -259,12 +259,13 @@ def run_arm(fdi, torch, prec, n, K, W, dev, rank, stream, cluster=None):
             "e2e_s": e2e_s, "h2d": f.nbytes, "d2h": f.nbytes, "clocks": clk.summary()}
 
 
-def run_stokes(fdi, torch, prec, n, reps, warm, stream):
+def run_stokes(fdi, torch, prec, n, reps, warm, stream, krylov=0):
     """Stokes-inverse latency on the staggered n^3 no-slip box (tanh 1.5, Re 1000,
     dt in {1e-2, 1e3}, Gaussian forcing seeds 0-2): p50 / p99 of the wall time of
     complete solves (each call ends with the stream synchronised)."""
     faces = workloads.box_faces((n, n, n), BETA)
     plan = fdi.plan_create(faces, (n, n, n), grid=fdi.GRID_MAC, prec=prec)
+    fdi.set_krylov(plan, krylov)
     shapes = workloads.mac_shapes((n, n, n))
     f = [torch.from_numpy(workloads.rhs_gaussian(shapes[c], i)).cuda() for i, c in enumerate("uvw")]
     u = [torch.empty_like(t) for t in f]
@@ -483,10 +484,12 @@ def main():
         stokes = {}
         for name in args.arms.split(","):
             prec = precs[name][0]
-            try:
-                stokes[name] = run_stokes(fdi, torch, prec, args.stokes_n, args.stokes_reps, 2, stream)
-            except fdi.FdiError as e:
-                stokes[name] = {"error": str(e)}
+            for kname, kry in (("", 0), ("/bicgstab2", 1)):
+                try:
+                    stokes[name + kname] = run_stokes(fdi, torch, prec, args.stokes_n, args.stokes_reps, 2, stream,
+                                                      krylov=kry)
+                except fdi.FdiError as e:
+                    stokes[name + kname] = {"error": str(e)}
     batch = None
     if args.batch > 0:
         batch = {"config": f"{args.batch} Helmholtz solves, grids from {{32,48,64,96,128,160}}^3 with aspect <= 4, "
@@ -525,7 +528,8 @@ def main():
         "roofline": roof,
         "cpu_baseline": cpu,
         "clocks": best["clocks"],
-        "stokes_latency": ({"config": f"MAC {args.stokes_n}^3, tanh {BETA}, no-slip, Re 1000, Gaussian forcing",
+        "stokes_latency": ({"config": f"MAC {args.stokes_n}^3, tanh {BETA}, no-slip, Re 1000, Gaussian forcing; "
+                                      "BiCGstab (default) and BiCGstab(2) (/bicgstab2; iterations are outer ones)",
                             **stokes} if stokes is not None else None),
         "batched": batch,
         "serving": serving,

@@ -133,6 +133,13 @@ fdi_status fdi_field_solve(fdi_plan* plan, fdi_field field, double sigma, double
 fdi_status fdi_stokes_solve(fdi_plan* plan, double dt, double Re, const double* const f[3],
                             double* const u[3], double* p, fdi_stream_t stream);
 
+/* Krylov method of fdi_stokes_solve for the pressure system C q = D u_hat
+ * (Sec. 2): 0 BiCGstab (van der Vorst; default), 1 BiCGstab(2) (Sleijpen &
+ * Fokkema's BiCGstab(l) with l = 2, the paper's choice), both right-
+ * preconditioned, FP64 scalars on the device.  With BiCGstab(2),
+ * fdi_last_result reports outer iterations (four C-products each). */
+fdi_status fdi_plan_set_krylov(fdi_plan* plan, int method);
+
 /* Preconditioner of the pressure-matrix Krylov solve: mode 0 is the paper's
  * inverse pressure Laplacian L_p^{-1} (Sec. 2, after Eq. 9); mode 1 (default)
  * adds the viscous term, L_p^{-1} - lambda*I (Cahouet & Chabard 1988), which is

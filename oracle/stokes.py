@@ -20,8 +20,8 @@ The three-step semi-direct inverse (Sec. 2, 3D steps after Eq. 9), with q = dt*p
   2. solve C q = D u_hat,  C = sum_c D_c H_c^{-1} G_c   (Eq. 9, the pressure matrix)
   3. u_c = u_hat_c - H_c^{-1} (G q)_c
 Step 2 is solved by a Krylov method preconditioned by the inverse pressure
-Laplacian L_p = D G (Sec. 2, after Eq. 9); plain BiCGstab (van der Vorst) is
-used here in place of the paper's BiCGstab(2).
+Laplacian L_p = D G (Sec. 2, after Eq. 9): plain BiCGstab (van der Vorst) or
+the paper's BiCGstab(2) (Sleijpen & Fokkema's BiCGstab(ell), ell = 2).
 """
 from __future__ import annotations
 
@@ -199,13 +199,84 @@ def bicgstab(apply_A, apply_Minv, b, tol, maxiter):
     return x, it, rel
 
 
-def stokes_semi_direct(faces, dt, Re, f, tol=1e-11, maxiter=200, method="tpt", precond="laplace"):
+def bicgstab_l(apply_A, apply_Minv, b, ell, tol, maxiter):
+    """Right-preconditioned BiCGstab(ell) (Sleijpen & Fokkema 1993), the Krylov
+    solver of the paper (ell = 2, Sec. 2), FP64 scalars.
+
+    The iteration runs on y for (A M^{-1}) y = b (so its residuals are the true
+    residuals of x = M^{-1} y, returned at the end).  One outer iteration makes
+    ell BiCG steps (2 ell operator applications) followed by a minimal-residual
+    step over the ell + 1 vectors r_0 .. r_ell (modified Gram-Schmidt).
+    Returns (x, outer iterations, ||b - A x|| / ||b||)."""
+    op = lambda v: apply_A(apply_Minv(v))
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return np.zeros_like(b), 0, 0.0
+    y = np.zeros_like(b)
+    r = [b.copy()] + [np.zeros_like(b) for _ in range(ell)]
+    u = [np.zeros_like(b) for _ in range(ell + 1)]
+    rhat = b.copy()
+    rho0, alpha, omega = 1.0, 0.0, 1.0
+    it = 0
+    rel = 1.0
+    while it < maxiter:
+        it += 1
+        rho0 = -omega * rho0
+        # BiCG part: ell steps, each raising the degree of the u / r sequences
+        for j in range(ell):
+            rho1 = float(np.dot(rhat, r[j]))
+            beta = alpha * rho1 / rho0
+            rho0 = rho1
+            for i in range(j + 1):
+                u[i] = r[i] - beta * u[i]
+            u[j + 1] = op(u[j])
+            alpha = rho0 / float(np.dot(rhat, u[j + 1]))
+            for i in range(j + 1):
+                r[i] = r[i] - alpha * u[i + 1]
+            r[j + 1] = op(r[j])
+            y = y + alpha * u[0]
+        # minimal-residual part: orthogonalise r_1 .. r_ell (MGS), then the
+        # coefficients of the polynomial in the original basis
+        tau = np.zeros((ell + 1, ell + 1))
+        sigma = np.zeros(ell + 1)
+        gp = np.zeros(ell + 1)
+        for j in range(1, ell + 1):
+            for i in range(1, j):
+                tau[i, j] = float(np.dot(r[j], r[i])) / sigma[i]
+                r[j] = r[j] - tau[i, j] * r[i]
+            sigma[j] = float(np.dot(r[j], r[j]))
+            gp[j] = float(np.dot(r[0], r[j])) / sigma[j]
+        g = np.zeros(ell + 1)
+        g[ell] = gp[ell]
+        omega = g[ell]
+        for j in range(ell - 1, 0, -1):
+            g[j] = gp[j] - sum(tau[j, i] * g[i] for i in range(j + 1, ell + 1))
+        gpp = np.zeros(ell + 1)
+        for j in range(1, ell):
+            gpp[j] = g[j + 1] + sum(tau[j, i] * g[i + 1] for i in range(j + 1, ell))
+        y = y + g[1] * r[0]
+        r[0] = r[0] - gp[ell] * r[ell]
+        u[0] = u[0] - g[ell] * u[ell]
+        for j in range(1, ell):
+            u[0] = u[0] - g[j] * u[j]
+            y = y + gpp[j] * r[j]
+            r[0] = r[0] - gp[j] * r[j]
+        rel = float(np.linalg.norm(r[0])) / bnorm
+        if rel <= tol:
+            break
+    x = apply_Minv(y)
+    return x, it, float(np.linalg.norm(b - apply_A(x))) / bnorm
+
+
+def stokes_semi_direct(faces, dt, Re, f, tol=1e-11, maxiter=200, method="tpt", precond="laplace",
+                       krylov="bicgstab"):
     """Three-step semi-direct Stokes inverse (Sec. 2): direct Helmholtz inverses by
     the decomposition solvers, BiCGstab on C preconditioned by L_p^{-1}
     (precond="laplace", the paper's choice) or by L_p^{-1} - lam*I
     (precond="cahouet-chabard": Cahouet & Chabard 1988, the exact inverse of
     C = L_p (I - lam L_p)^{-1} when the discrete operators commute).
 
+    krylov: "bicgstab" or "bicgstab2" (the paper's choice, Sec. 2).
     Returns ((u, v, w), p, iterations, relative C-residual)."""
     lam = dt / Re
     D, G = div_grad_3d(faces)
@@ -228,7 +299,10 @@ def stokes_semi_direct(faces, dt, Re, f, tol=1e-11, maxiter=200, method="tpt", p
 
     uhat = [Hinv(c, f[c]) for c in range(3)]
     b = sum(D[c] @ uhat[c] for c in range(3))
-    q, it, rel = bicgstab(C, Lp_inv, b, tol, maxiter)
+    if krylov == "bicgstab2":
+        q, it, rel = bicgstab_l(C, Lp_inv, b, 2, tol, maxiter)
+    else:
+        q, it, rel = bicgstab(C, Lp_inv, b, tol, maxiter)
     vol = asm.volumes(pops)
     q = q - np.dot(vol, q) / vol.sum()
     vel = tuple((uhat[c] - Hinv(c, G[c] @ q)).reshape(vs[c]) for c in range(3))

@@ -92,6 +92,7 @@ struct fdi_plan {
   double* mac_idc[3] = {nullptr, nullptr, nullptr};
   fdi::KryState* d_kry = nullptr;
   int stokes_precond = 1;           // 0: L_p^{-1} (paper), 1: L_p^{-1} - lambda I
+  int krylov = 0;                   // 0: BiCGstab, 1: BiCGstab(2) (the paper's solver)
   double* kpartials = nullptr;
   // controls
   double tol = 1e-11;
@@ -123,6 +124,7 @@ struct fdi_plan {
   cudaGraphExec_t kgraph = nullptr;
   double kgraph_lambda = 0.0;
   int kgraph_precond = -1;
+  int kgraph_krylov = -1;
   cudaStream_t kgraph_stream = nullptr;
   long long kgraph_launches = 0;
   // optional per-kernel device timing (CUDA events around each launch)

@@ -31,6 +31,9 @@ struct KryState {
   double bnorm2, rnorm2, rel;
   double tol;
   int iters, maxit, done, error;
+  // BiCGstab(2): beta, the MGS coefficient tau_12, sigma_1, sigma_2 and the
+  // polynomial coefficients gamma'_1, gamma'_2, gamma_1, gamma_2, gamma''_1
+  double beta, tau12, sigma1, sigma2, gp1, gp2, g1, g2, gpp1;
 };
 
 namespace {
@@ -126,8 +129,12 @@ __device__ __forceinline__ void sum_partials(const double* partials, double& a, 
   block_reduce2(a, b);
 }
 
-// kinds of scalar updates after a reduction
-enum { KF_INIT = 0, KF_ALPHA = 1, KF_OMEGA = 2, KF_ITER = 3, KF_MEAN = 4 };
+// kinds of scalar updates after a reduction (KF_L2_*: BiCGstab(2))
+enum {
+  KF_INIT = 0, KF_ALPHA = 1, KF_OMEGA = 2, KF_ITER = 3, KF_MEAN = 4,
+  KF_L2_INIT = 5, KF_L2_RHO0 = 6, KF_L2_RHO = 7, KF_L2_ALPHA = 8, KF_L2_MR1 = 9, KF_L2_TAU = 10, KF_L2_MR2 = 11,
+  KF_L2_CONV = 12
+};
 
 __global__ void __launch_bounds__(kDotThreads) k_kry_finish(const double* __restrict__ partials, KryState* st,
                                                             int kind) {
@@ -189,7 +196,153 @@ __global__ void __launch_bounds__(kDotThreads) k_kry_finish(const double* __rest
     case KF_MEAN:  // a = sum V x, b = sum V: store the mean in rho_old slot of a scratch state
       st->rnorm2 = a / b;
       break;
+    // ---- BiCGstab(2) (Sleijpen & Fokkema), right-preconditioned, iterate y ----
+    case KF_L2_INIT:  // a = ||b||^2; rho0 = 1, alpha = 0, omega = 1
+      st->bnorm2 = a;
+      st->rnorm2 = a;
+      st->rho = 1.0;
+      st->alpha = 0.0;
+      st->omega = 1.0;
+      st->iters = 0;
+      st->rel = a > 0.0 ? 1.0 : 0.0;
+      st->done = a > 0.0 ? 0 : 1;
+      st->error = 0;
+      break;
+    case KF_L2_RHO0:  // new outer iteration: rho0 = -omega rho0, then the j = 0 step (a = rhat.r_0)
+      st->rho = -st->omega * st->rho;
+      // fall through
+    case KF_L2_RHO: {  // a = rhat.r_j: beta = alpha rho1 / rho0, rho0 = rho1
+      if (st->rho == 0.0 || !isfinite(a)) {
+        st->error = 6;
+        st->done = 1;
+        break;
+      }
+      st->beta = st->alpha * a / st->rho;
+      st->rho = a;
+      break;
+    }
+    case KF_L2_ALPHA:  // a = rhat.u_{j+1}
+      if (a == 0.0 || !isfinite(a)) {
+        st->error = 2;
+        st->done = 1;
+      } else {
+        st->alpha = st->rho / a;
+      }
+      break;
+    case KF_L2_MR1:  // a = r_1.r_1, b = r_0.r_1
+      if (a == 0.0 || !isfinite(a)) {
+        st->error = 3;
+        st->done = 1;
+      } else {
+        st->sigma1 = a;
+        st->gp1 = b / a;
+      }
+      break;
+    case KF_L2_TAU:  // a = r_2.r_1
+      st->tau12 = a / st->sigma1;
+      break;
+    case KF_L2_MR2:  // a = r_2.r_2 (after orthogonalisation), b = r_0.r_2
+      if (a == 0.0 || !isfinite(a)) {
+        st->error = 3;
+        st->done = 1;
+      } else {
+        st->sigma2 = a;
+        st->gp2 = b / a;
+        st->g2 = st->gp2;
+        st->omega = st->g2;
+        st->g1 = st->gp1 - st->tau12 * st->g2;
+        st->gpp1 = st->g2;
+      }
+      break;
+    case KF_L2_CONV: {  // a = r_0.r_0 after the minimal-residual update
+      st->iters += 1;
+      st->rnorm2 = a;
+      const double rel = sqrt(a / st->bnorm2);
+      st->rel = rel;
+      if (!isfinite(rel)) {
+        st->error = 4;
+        st->done = 1;
+      } else if (rel <= st->tol) {
+        st->done = 1;
+      } else if (st->iters >= st->maxit) {
+        st->done = 1;
+        st->error = 5;
+      } else if (st->omega == 0.0) {
+        st->done = 1;
+        st->error = 6;
+      }
+      break;
+    }
   }
+}
+
+// ---- BiCGstab(2) vector updates (all read the device scalars) ----
+
+// j = 0: u_0 = r_0 - beta u_0;  j = 1: also u_1 = r_1 - beta u_1
+__global__ void k_l2_u(const KryState* __restrict__ st, double* __restrict__ u0, double* __restrict__ u1,
+                       const double* __restrict__ r0, const double* __restrict__ r1, long long n, int j) {
+  if (st->done) return;
+  const double be = st->beta;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    u0[q] = r0[q] - be * u0[q];
+    if (j) u1[q] = r1[q] - be * u1[q];
+  }
+}
+
+// j = 0: r_0 -= alpha u_1, y += alpha u_0;  j = 1: also r_1 -= alpha u_2
+__global__ void k_l2_r(const KryState* __restrict__ st, double* __restrict__ r0, double* __restrict__ r1,
+                       const double* __restrict__ u0, const double* __restrict__ u1, const double* __restrict__ u2,
+                       double* __restrict__ y, long long n, int j) {
+  if (st->done) return;
+  const double al = st->alpha;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    r0[q] -= al * u1[q];
+    if (j) r1[q] -= al * u2[q];
+    y[q] += al * u0[q];
+  }
+}
+
+// r_2 -= tau_12 r_1 (modified Gram-Schmidt)
+__global__ void k_l2_tau(const KryState* __restrict__ st, double* __restrict__ r2, const double* __restrict__ r1,
+                         long long n) {
+  if (st->done) return;
+  const double t = st->tau12;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    r2[q] -= t * r1[q];
+}
+
+// minimal-residual update: y += g1 r_0 + g''1 r_1, r_0 -= g'2 r_2 + g'1 r_1,
+// u_0 -= g2 u_2 + g1 u_1; partial sums of r_0.r_0
+__global__ void __launch_bounds__(kDotThreads) k_l2_final(const KryState* __restrict__ st, double* __restrict__ y,
+                                                          double* __restrict__ r0, const double* __restrict__ r1,
+                                                          const double* __restrict__ r2, double* __restrict__ u0,
+                                                          const double* __restrict__ u1,
+                                                          const double* __restrict__ u2, long long n,
+                                                          double* __restrict__ partials) {
+  const bool live = !st->done;
+  const double g1 = st->g1, g2 = st->g2, gp1 = st->gp1, gp2 = st->gp2, gpp1 = st->gpp1;
+  double s0 = 0.0, s1 = 0.0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    if (live) {
+      const double r0q = r0[q], r1q = r1[q];
+      y[q] += g1 * r0q + gpp1 * r1q;
+      const double rn = r0q - gp2 * r2[q] - gp1 * r1q;
+      r0[q] = rn;
+      u0[q] -= g2 * u2[q] + g1 * u1[q];
+      s0 = fma(rn, rn, s0);
+    }
+  }
+  block_reduce2(s0, s1);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = s0;
+    partials[2 * blockIdx.x + 1] = s1;
+  }
+}
+
+// x = -t
+__global__ void k_neg(double* __restrict__ x, const double* __restrict__ t, long long n) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    x[q] = -t[q];
 }
 
 // p = r + beta (p - omega v),  beta = (rho / rho_old)(alpha / omega)
@@ -403,78 +556,137 @@ fdi_status stokes_solve(fdi_plan* p, double dt, double Re, const double* const f
   FDI_CUDA_TRY(cudaMemcpyAsync(rhat, b, Pc * sizeof(double), cudaMemcpyDeviceToDevice, s));
   k_zero<<<vb, vt, 0, s>>>(x, Pc);
   FDI_LAUNCH_CHECK(p);
-  FDI_TRY(dots(p, b, b, nullptr, nullptr, Pc, KF_INIT, s));
-  // step 2: BiCGstab on C q = b, right-preconditioned by L_p^{-1}
-  auto iteration = [&](int first) -> fdi_status {
-    k_bicg_p<<<vb, vt, 0, s>>>(p->d_kry, pv, r, v, Pc, first);
-    FDI_LAUNCH_CHECK(p);
-    // y = (-L_p)^{-1} p (+ lambda p) = -phat ; v = C phat
-    FDI_TRY(field_solve(p, FDI_FIELD_CELL, 0.0, 1.0, pv, y, s));
-    if (p->stokes_precond == 1) {
-      k_axpy<<<vb, vt, 0, s>>>(y, lambda, pv, Pc);
-      FDI_LAUNCH_CHECK(p);
+  // step 2: Krylov solve of C q = b, right-preconditioned by L_p^{-1} (or its
+  // Cahouet-Chabard form).  Iterations after the first replay one captured
+  // graph of the iteration (plan workspace only, so the launches are
+  // identical); the legacy stream and timed plans run eagerly.
+  const bool graphs = p->use_graphs && !p->timing && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+  auto run_loop = [&](auto&& iteration) -> fdi_status {
+    for (int it = 0; it < p->kmaxit; ++it) {
+      if (it == 0 || !graphs) {
+        FDI_TRY(iteration(it == 0 ? 1 : 0));
+      } else {
+        if (!p->kgraph || p->kgraph_lambda != lambda || p->kgraph_precond != p->stokes_precond ||
+            p->kgraph_krylov != p->krylov || p->kgraph_stream != s) {
+          if (p->kgraph) cudaGraphExecDestroy(p->kgraph);
+          p->kgraph = nullptr;
+          const long long before = p->launches;
+          FDI_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+          fdi_status st = iteration(0);
+          cudaGraph_t gr = nullptr;
+          cudaError_t e = cudaStreamEndCapture(s, &gr);
+          if (st != FDI_OK || e != cudaSuccess || gr == nullptr) {
+            if (gr) cudaGraphDestroy(gr);
+            if (st != FDI_OK) return st;
+            FDI_CUDA_TRY(e);
+            set_error("stream capture of the Krylov iteration failed");
+            return FDI_ERR_CUDA;
+          }
+          cudaGraphExec_t ex = nullptr;
+          e = cudaGraphInstantiate(&ex, gr, 0);
+          cudaGraphDestroy(gr);
+          FDI_CUDA_TRY(e);
+          p->kgraph = ex;
+          p->kgraph_lambda = lambda;
+          p->kgraph_precond = p->stokes_precond;
+          p->kgraph_krylov = p->krylov;
+          p->kgraph_stream = s;
+          p->kgraph_launches = p->launches - before;
+          p->launches = before;
+        }
+        FDI_CUDA_TRY(cudaGraphLaunch(p->kgraph, s));
+        p->launches += p->kgraph_launches;
+      }
+      FDI_CUDA_TRY(cudaMemcpyAsync(p->h_flag, &p->d_kry->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+      FDI_CUDA_TRY(cudaStreamSynchronize(s));
+      if (*p->h_flag) break;
     }
-    FDI_TRY(cmatvec(p, g, lambda, y, v, s));
-    FDI_TRY(dots(p, rhat, v, nullptr, nullptr, Pc, KF_ALPHA, s));
-    k_bicg_s<<<vb, vt, 0, s>>>(p->d_kry, sv, r, v, Pc);
-    FDI_LAUNCH_CHECK(p);
-    FDI_TRY(field_solve(p, FDI_FIELD_CELL, 0.0, 1.0, sv, z, s));
+    return FDI_OK;
+  };
+  // -(M^{-1} v) into `out`: the Laplace solve returns -L_p^{-1} v; mode 1 adds lambda v
+  auto precond = [&](const double* vin, double* vout) -> fdi_status {
+    FDI_TRY(field_solve(p, FDI_FIELD_CELL, 0.0, 1.0, vin, vout, s));
     if (p->stokes_precond == 1) {
-      k_axpy<<<vb, vt, 0, s>>>(z, lambda, sv, Pc);
-      FDI_LAUNCH_CHECK(p);
-    }
-    FDI_TRY(cmatvec(p, g, lambda, z, t, s));
-    FDI_TRY(dots(p, t, sv, t, t, Pc, KF_OMEGA, s));
-    {
-      FDI_KTIMER(p, "stokes_update", s);
-      k_bicg_xr<<<kDotBlocks, kDotThreads, 0, s>>>(p->d_kry, x, y, z, r, sv, t, rhat, Pc, p->kpartials);
-      FDI_LAUNCH_CHECK(p);
-      k_kry_finish<<<1, kDotThreads, 0, s>>>(p->kpartials, p->d_kry, KF_ITER);
+      k_axpy<<<vb, vt, 0, s>>>(vout, lambda, vin, Pc);
       FDI_LAUNCH_CHECK(p);
     }
     return FDI_OK;
   };
-  // iterations after the first replay one captured graph of the iteration
-  // (plan workspace only, so the launches are identical); the legacy stream
-  // and timed plans run eagerly
-  const bool graphs = p->use_graphs && !p->timing && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
-  for (int it = 0; it < p->kmaxit; ++it) {
-    if (it == 0 || !graphs) {
-      FDI_TRY(iteration(it == 0 ? 1 : 0));
-    } else {
-      if (!p->kgraph || p->kgraph_lambda != lambda || p->kgraph_precond != p->stokes_precond ||
-          p->kgraph_stream != s) {
-        if (p->kgraph) cudaGraphExecDestroy(p->kgraph);
-        p->kgraph = nullptr;
-        const long long before = p->launches;
-        FDI_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        fdi_status st = iteration(0);
-        cudaGraph_t gr = nullptr;
-        cudaError_t e = cudaStreamEndCapture(s, &gr);
-        if (st != FDI_OK || e != cudaSuccess || gr == nullptr) {
-          if (gr) cudaGraphDestroy(gr);
-          if (st != FDI_OK) return st;
-          FDI_CUDA_TRY(e);
-          set_error("stream capture of the BiCGstab iteration failed");
-          return FDI_ERR_CUDA;
-        }
-        cudaGraphExec_t ex = nullptr;
-        e = cudaGraphInstantiate(&ex, gr, 0);
-        cudaGraphDestroy(gr);
-        FDI_CUDA_TRY(e);
-        p->kgraph = ex;
-        p->kgraph_lambda = lambda;
-        p->kgraph_precond = p->stokes_precond;
-        p->kgraph_stream = s;
-        p->kgraph_launches = p->launches - before;
-        p->launches = before;
+  if (p->krylov == 1) {
+    // BiCGstab(2) (Sleijpen & Fokkema; the paper's solver, Sec. 2) on
+    // (C M^{-1}) y = b; q = M^{-1} y at the end.  Vectors: x = y, r = r_0,
+    // pv = u_0, v = u_1, sv = u_2, t = r_1, y = r_2, z = work.
+    double *r0 = r, *u0 = pv, *u1 = v, *u2 = sv, *r1 = t, *r2 = y, *w = z;
+    k_zero<<<vb, vt, 0, s>>>(u0, Pc);
+    FDI_LAUNCH_CHECK(p);
+    FDI_TRY(dots(p, b, b, nullptr, nullptr, Pc, KF_L2_INIT, s));
+    auto op = [&](const double* vin, double* vout) -> fdi_status {  // vout = C M^{-1} vin
+      FDI_TRY(precond(vin, w));
+      return cmatvec(p, g, lambda, w, vout, s);
+    };
+    auto iteration = [&](int) -> fdi_status {
+      // BiCG step j = 0
+      FDI_TRY(dots(p, rhat, r0, nullptr, nullptr, Pc, KF_L2_RHO0, s));
+      k_l2_u<<<vb, vt, 0, s>>>(p->d_kry, u0, u1, r0, r1, Pc, 0);
+      FDI_LAUNCH_CHECK(p);
+      FDI_TRY(op(u0, u1));
+      FDI_TRY(dots(p, rhat, u1, nullptr, nullptr, Pc, KF_L2_ALPHA, s));
+      k_l2_r<<<vb, vt, 0, s>>>(p->d_kry, r0, r1, u0, u1, u2, x, Pc, 0);
+      FDI_LAUNCH_CHECK(p);
+      FDI_TRY(op(r0, r1));
+      // BiCG step j = 1
+      FDI_TRY(dots(p, rhat, r1, nullptr, nullptr, Pc, KF_L2_RHO, s));
+      k_l2_u<<<vb, vt, 0, s>>>(p->d_kry, u0, u1, r0, r1, Pc, 1);
+      FDI_LAUNCH_CHECK(p);
+      FDI_TRY(op(u1, u2));
+      FDI_TRY(dots(p, rhat, u2, nullptr, nullptr, Pc, KF_L2_ALPHA, s));
+      k_l2_r<<<vb, vt, 0, s>>>(p->d_kry, r0, r1, u0, u1, u2, x, Pc, 1);
+      FDI_LAUNCH_CHECK(p);
+      FDI_TRY(op(r1, r2));
+      // minimal-residual step over r_0, r_1, r_2
+      FDI_TRY(dots(p, r1, r1, r0, r1, Pc, KF_L2_MR1, s));
+      FDI_TRY(dots(p, r2, r1, nullptr, nullptr, Pc, KF_L2_TAU, s));
+      k_l2_tau<<<vb, vt, 0, s>>>(p->d_kry, r2, r1, Pc);
+      FDI_LAUNCH_CHECK(p);
+      FDI_TRY(dots(p, r2, r2, r0, r2, Pc, KF_L2_MR2, s));
+      {
+        FDI_KTIMER(p, "stokes_update", s);
+        k_l2_final<<<kDotBlocks, kDotThreads, 0, s>>>(p->d_kry, x, r0, r1, r2, u0, u1, u2, Pc, p->kpartials);
+        FDI_LAUNCH_CHECK(p);
+        k_kry_finish<<<1, kDotThreads, 0, s>>>(p->kpartials, p->d_kry, KF_L2_CONV);
+        FDI_LAUNCH_CHECK(p);
       }
-      FDI_CUDA_TRY(cudaGraphLaunch(p->kgraph, s));
-      p->launches += p->kgraph_launches;
-    }
-    FDI_CUDA_TRY(cudaMemcpyAsync(p->h_flag, &p->d_kry->done, sizeof(int), cudaMemcpyDeviceToHost, s));
-    FDI_CUDA_TRY(cudaStreamSynchronize(s));
-    if (*p->h_flag) break;
+      return FDI_OK;
+    };
+    FDI_TRY(run_loop(iteration));
+    // q = M^{-1} y
+    FDI_TRY(precond(x, w));
+    k_neg<<<vb, vt, 0, s>>>(x, w, Pc);
+    FDI_LAUNCH_CHECK(p);
+  } else {
+    FDI_TRY(dots(p, b, b, nullptr, nullptr, Pc, KF_INIT, s));
+    auto iteration = [&](int first) -> fdi_status {
+      k_bicg_p<<<vb, vt, 0, s>>>(p->d_kry, pv, r, v, Pc, first);
+      FDI_LAUNCH_CHECK(p);
+      // y = (-L_p)^{-1} p (+ lambda p) = -phat ; v = C phat
+      FDI_TRY(precond(pv, y));
+      FDI_TRY(cmatvec(p, g, lambda, y, v, s));
+      FDI_TRY(dots(p, rhat, v, nullptr, nullptr, Pc, KF_ALPHA, s));
+      k_bicg_s<<<vb, vt, 0, s>>>(p->d_kry, sv, r, v, Pc);
+      FDI_LAUNCH_CHECK(p);
+      FDI_TRY(precond(sv, z));
+      FDI_TRY(cmatvec(p, g, lambda, z, t, s));
+      FDI_TRY(dots(p, t, sv, t, t, Pc, KF_OMEGA, s));
+      {
+        FDI_KTIMER(p, "stokes_update", s);
+        k_bicg_xr<<<kDotBlocks, kDotThreads, 0, s>>>(p->d_kry, x, y, z, r, sv, t, rhat, Pc, p->kpartials);
+        FDI_LAUNCH_CHECK(p);
+        k_kry_finish<<<1, kDotThreads, 0, s>>>(p->kpartials, p->d_kry, KF_ITER);
+        FDI_LAUNCH_CHECK(p);
+      }
+      return FDI_OK;
+    };
+    FDI_TRY(run_loop(iteration));
   }
   // zero-mean pressure q -> p = q / dt
   {
@@ -517,6 +729,12 @@ extern "C" fdi_status fdi_stokes_solve(fdi_plan* plan, double dt, double Re, con
     if (!f[c] || !u[c]) return FDI_ERR_INVALID_ARG;
   plan->launches = 0;
   return stokes_solve(plan, dt, Re, f, u, p, (cudaStream_t)stream);
+}
+
+extern "C" fdi_status fdi_plan_set_krylov(fdi_plan* plan, int method) {
+  if (!plan || (method != 0 && method != 1)) return FDI_ERR_INVALID_ARG;
+  plan->krylov = method;
+  return FDI_OK;
 }
 
 extern "C" fdi_status fdi_plan_set_stokes_preconditioner(fdi_plan* plan, int mode) {

@@ -61,6 +61,7 @@ SIGNATURES = {
     "fdi_apply_transform": (_i, [_vp, _i, _i, _i, _vp, _vp, C.c_longlong, _vp]),
     "fdi_plan_set_transform_config": (_i, [_vp, _i]),
     "fdi_plan_set_stokes_preconditioner": (_i, [_vp, _i]),
+    "fdi_plan_set_krylov": (_i, [_vp, _i]),
     "fdi_eigen_noalloc": (_i, [C.POINTER(_d), _i, _i, _i, _i, _vp, _vp, _vp, C.POINTER(_i), _vp]),
     "fdi_plan_set_graphs": (_i, [_vp, _i]),
     "fdi_plan_set_thomas_config": (_i, [_vp, _i]),
@@ -260,6 +261,11 @@ def _fptr(x):
 def apply_transform(plan: Plan, field, d, inverse, inp, out, rows, stream=None):
     _check(load().fdi_apply_transform(plan.handle, int(field), int(d), 1 if inverse else 0, _fptr(inp), _fptr(out),
                                       int(rows), _stream(stream)), "fdi_apply_transform")
+
+
+def set_krylov(plan: Plan, method: int):
+    """0: BiCGstab, 1: BiCGstab(2) (the paper's solver) for the Stokes pressure system."""
+    _check(load().fdi_plan_set_krylov(plan.handle, int(method)), "fdi_plan_set_krylov")
 
 
 def set_stokes_preconditioner(plan: Plan, mode: int):

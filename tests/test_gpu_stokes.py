@@ -137,3 +137,40 @@ def test_stokes_graph_replay_matches_eager(fdi, prec):
             assert np.array_equal(ut[c].cpu().numpy(), vel_e[c])
         assert np.array_equal(pt.cpu().numpy(), p_e)
     plan.destroy()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (3, 1e-10)])
+@pytest.mark.parametrize("dt", [1e-2, 1e3])
+def test_bicgstab2_matches_oracle(fdi, prec, tol, dt):
+    # the paper's Krylov solver (BiCGstab(2), Sec. 2) on the device, against the
+    # oracle's BiCGstab(2) three-step solve and the assembled saddle system
+    import torch
+    faces = box_faces((20, 18, 16), 1.5)
+    f = forcing(faces, 7)
+    n = tuple(len(fc) - 1 for fc in faces)
+    plan = fdi.plan_create(faces, n, grid=fdi.GRID_MAC, prec=prec)
+    fdi.set_krylov(plan, 1)
+    vs, ps = st.shapes(faces)
+    ft = [torch.from_numpy(np.ascontiguousarray(fc)).cuda() for fc in f]
+    stream = torch.cuda.Stream()
+    results = []
+    for _ in range(2):  # eager, then captured iterations
+        ut = [torch.empty_like(t) for t in ft]
+        pt = torch.empty(ps, dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            fdi.stokes_solve(plan, dt, 1000.0, ft, ut, pt, stream)
+        stream.synchronize()
+        it, _, res, status = fdi.last_result(plan)
+        assert status == 0 and res <= tol, (it, res)
+        results.append(([t.cpu().numpy() for t in ut], pt.cpu().numpy()))
+    plan.destroy()
+    vel, p = results[1]
+    for c in range(3):
+        assert np.array_equal(results[0][0][c], vel[c])
+    mom, div = st.saddle_residual(faces, dt, 1000.0, f, vel, p)
+    assert mom <= 1e-9 and div <= 1000 * tol, (mom, div)
+    vel_o, p_o, it_o, _ = st.stokes_semi_direct(faces, dt, 1000.0, f, tol=1e-12, precond="cahouet-chabard",
+                                                krylov="bicgstab2")
+    for c in range(3):
+        assert rel(vel[c], vel_o[c]) <= 1e-8
+    assert rel(p, p_o) <= 1e-6

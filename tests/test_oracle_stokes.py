@@ -156,3 +156,44 @@ def test_cahouet_chabard_exact_on_uniform_periodic_analogue():
     C = L @ np.linalg.inv(np.eye(12) - lam * L)
     P = np.linalg.inv(L) - lam * np.eye(12)
     assert np.abs(P @ C - np.eye(12)).max() < 1e-12
+
+
+def test_bicgstab_l_with_l1_is_bicgstab():
+    # BiCGstab(1) and van der Vorst's BiCGstab generate the same iterates: two
+    # independent formulations of the method agree step by step
+    rng = np.random.default_rng(0)
+    n = 30
+    A = np.eye(n) * 4 + rng.standard_normal((n, n)) * 0.3
+    Md = np.diag(A).copy()
+    b = rng.standard_normal(n)
+    for k in (1, 2, 3, 5, 8):
+        x1, _, r1 = st.bicgstab(lambda v: A @ v, lambda v: v / Md, b, 0.0, k)
+        xl, _, rl = st.bicgstab_l(lambda v: A @ v, lambda v: v / Md, b, 1, 0.0, k)
+        assert np.abs(x1 - xl).max() <= 1e-12 * np.abs(x1).max()
+        assert abs(r1 - rl) <= 1e-10 * r1 + 1e-14
+
+
+@pytest.mark.parametrize("ell", [2, 3])
+def test_bicgstab_l_solves_nonsymmetric(ell):
+    rng = np.random.default_rng(ell)
+    n = 40
+    A = np.eye(n) * 3 + rng.standard_normal((n, n)) * 0.25
+    b = rng.standard_normal(n)
+    x, it, rel = st.bicgstab_l(lambda v: A @ v, lambda v: v, b, ell, 1e-13, 200)
+    assert rel <= 1e-12
+    assert np.abs(x - np.linalg.solve(A, b)).max() <= 1e-10 * np.abs(np.linalg.solve(A, b)).max()
+
+
+@pytest.mark.parametrize("dt", [1e-2, 1.0, 1e3])
+@pytest.mark.parametrize("precond", ["laplace", "cahouet-chabard"])
+def test_semi_direct_bicgstab2_matches_direct(dt, precond):
+    # the paper's Krylov solver (Sec. 2) inside the three-step algorithm
+    faces = [tanh_faces(6, 1.5), tanh_faces(7, 1.5), tanh_faces(8, 2.0)]
+    vs, ps = st.shapes(faces)
+    f = [rhs_gaussian(vs[c], c) for c in range(3)]
+    vd, pd = st.stokes_direct(faces, dt, 1000.0, f)
+    v, p, it, rel = st.stokes_semi_direct(faces, dt, 1000.0, f, tol=1e-12, precond=precond, krylov="bicgstab2")
+    assert rel <= 1e-12
+    for c in range(3):
+        assert np.abs(v[c] - vd[c]).max() <= 1e-10 * np.abs(vd[c]).max()
+    assert np.abs(p - pd).max() <= 1e-9 * np.abs(pd).max()
