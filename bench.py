@@ -201,9 +201,9 @@ def tensor_flops(name, n):
     return 6.0 * P * n[d] if name.endswith("_tc") else None
 
 
-def run_arm(fdi, torch, prec, n, K, W, dev, rank, stream, cluster=None):
+def run_arm(fdi, torch, prec, n, K, W, dev, rank, stream, cluster=None, thomas_axis=2):
     faces = workloads.box_faces(n, BETA)
-    plan = fdi.plan_create(faces, n, prec=prec)
+    plan = fdi.plan_create(faces, n, prec=prec, thomas_axis=thomas_axis)
     if cluster is not None and prec != fdi.PREC_FP64:
         fdi.set_transform_config(plan, cluster)
     f = workloads.rhs_uniform(n[::-1], rank)
@@ -372,6 +372,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--arms", default="fp64,mixed")
+    ap.add_argument("--no-tpf", action="store_true", help="skip the FP64 TPF arm")
     ap.add_argument("--cluster", type=int, default=None, help="tensor-core transform cluster size (1, 2, 4)")
     ap.add_argument("--stokes-n", type=int, default=64, help="Stokes latency grid (0: skip)")
     ap.add_argument("--stokes-reps", type=int, default=10)
@@ -424,10 +425,16 @@ def main():
 
     arms = {}
     precs = {"fp64": (fdi.PREC_FP64, 1e-11), "mixed": (fdi.PREC_MIXED_F16, 1e-10)}
-    for name in args.arms.split(","):
-        prec, tol = precs[name]
+    # the TPF variant (eigen transforms in all three directions, Eq. 29) runs on the FP64 path
+    helm_arms = {"fp64": (fdi.PREC_FP64, 1e-11, 2), "mixed": (fdi.PREC_MIXED_F16, 1e-10, 2),
+                 "fp64_tpf": (fdi.PREC_FP64, 1e-11, -1)}
+    for name in args.arms.split(",") + ([] if args.no_tpf else ["fp64_tpf"]):
+        prec, tol, taxis = helm_arms[name]
         try:
-            arms[name] = run_arm(fdi, torch, prec, n, K, W, dev, rank, stream, args.cluster)
+            arms[name] = run_arm(fdi, torch, prec, n, K if taxis == 2 else max(3, K // 10), W, dev, rank, stream,
+                                 args.cluster, thomas_axis=taxis)
+            if taxis != 2:
+                arms[name]["K"] = max(3, K // 10)
             arms[name]["tol"] = tol
             arms[name]["prec"] = prec
         except fdi.FdiError as e:
@@ -440,7 +447,7 @@ def main():
         if world > 1:
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         a["ms_max"], a["e2e_max"] = float(t[0]), float(t[1])
-        a["value"] = world * P * K / (a["ms_max"] * 1e-3)
+        a["value"] = world * P * a.get("K", K) / (a["ms_max"] * 1e-3)
         a["ok"] = a["status"] == 0 and a["rel"] <= a["tol"]
     best_name = max((k for k in arms if arms[k]["ok"]), key=lambda k: arms[k]["value"], default=None)
     if best_name is None:
@@ -519,10 +526,10 @@ def main():
         return 0
     line = {
         "metric": METRIC, "value": best["value"], "unit": "grid-pts/s", "n_gpus": world, "steps": K, "warmup": W,
-        "ms_per_step": best["ms_max"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": best["ms_max"] / best.get("K", K), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if best_name == "fp64" else "f16-split/f32-acc + f64 refinement",
         "data": "synthetic", "config": dict(workload, arm=best_name, parallelism=f"replicas x{world}"),
-        "e2e": {"value": world * P * K / best["e2e_max"], "unit": "grid-pts/s", "h2d_bytes_per_step": best["h2d"],
+        "e2e": {"value": world * P * best.get("K", K) / best["e2e_max"], "unit": "grid-pts/s", "h2d_bytes_per_step": best["h2d"],
                 "d2h_bytes_per_step": best["d2h"]},
         "gpu_launches": best["launches_per"] * K,
         "roofline": roof,
@@ -536,7 +543,7 @@ def main():
         "kernels": {k: {kk: round(vv, 4) if isinstance(vv, float) else vv for kk, vv in e.items()
                         if kk in ("achieved", "unit", "frac", "avg_launch_ms", "launches", "tensor_frac")}
                     for k, e in per_kernel.items()},
-        "arms": {k: {"value": a["value"], "ms_per_solve": a["ms_max"] / K, "rel_residual": a["rel"],
+        "arms": {k: {"value": a["value"], "ms_per_solve": a["ms_max"] / a.get("K", K), "rel_residual": a["rel"],
                      "refine_steps": a["steps"], "tol": a["tol"], "met_tol": a["ok"],
                      "kernels": {kn: {"ms_total": v[0], "launches": v[1]} for kn, v in a["ktimes"].items()}}
                  for k, a in arms.items()},
