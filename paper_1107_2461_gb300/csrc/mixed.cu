@@ -340,7 +340,9 @@ __device__ __forceinline__ void resid_body(const ResidArgs& a, double* sh) {
 }
 
 template <int MODE, int SIG, bool LO, bool MEAN, bool OUT>
-__global__ void __launch_bounds__(kResTX * kResTY, 4) k_resid_df(ResidArgs a, const int* __restrict__ skip) {
+// occupancy: 4 CTAs per SM for the first check, 5 for the correction checks
+// (measured best; the latter spills a few registers to L1)
+__global__ void __launch_bounds__(kResTX * kResTY, MODE == 1 ? 5 : 4) k_resid_df(ResidArgs a, const int* __restrict__ skip) {
   if (skip && *skip) return;
   __shared__ double sh[4 * kResTY];
   const bool interior = blockIdx.x > 0 && (int)(blockIdx.x + 1) * kResTX < a.nx && blockIdx.y > 0 &&
