@@ -206,13 +206,15 @@ fdi_status fdi_plan_set_transform_config(fdi_plan* plan, int cluster);
 fdi_status fdi_eigen_noalloc(const double* faces, int n, int face_kind, fdi_bc bc_lo, fdi_bc bc_hi, double* lam,
                              double* E, double* Einv, int* converged, fdi_stream_t stream);
 
-/* FP32 Thomas sweep of mixed plans: lines (threads) per CTA, 64 or 128
- * (default 128).  A tuning knob: results are bitwise identical. */
+/* FP32 Thomas sweep of mixed plans: 64 or 128 lines (one per thread) per
+ * CTA, or 2: two adjacent lines per thread, 64 threads per CTA (default 2).
+ * A tuning knob: results are bitwise identical. */
 fdi_status fdi_plan_set_thomas_config(fdi_plan* plan, int lines_per_cta);
 
 /* Autotuner for mixed plans: times `reps` complete Helmholtz solves
  * (sigma = 1, `lambda`, rhs -> out on `stream`, after one warm-up solve each)
- * for every transform cluster size (1, 2, 4) and Thomas CTA size (64, 128),
+ * for every transform cluster size (1, 2, 4) and Thomas configuration (2, 64,
+ * 128),
  * keeps the fastest on the plan and records it for the plan's grid shape:
  * plans created later with the same shape and precision start with it.  Every
  * configuration computes bitwise-identical results.  rhs and out: device FP64

@@ -78,7 +78,7 @@ struct fdi_plan {
   float* d_scales = nullptr;        // per refinement round: max |field| of the pass inputs
   int* d_err = nullptr;             // nonzero: a tensor-core kernel hit a wait limit
   int tc_cluster = 1;               // CTAs sharing each transform-matrix chunk by TMA multicast
-  int thomas_tl = 128;              // FP32 Thomas lines per CTA (64 or 128)
+  int thomas_tl = 2;                // FP32 Thomas: lines per CTA (64, 128) or 2 = two lines per thread
   float2* lam_w = nullptr;          // lambda-scaled double-float flux weights [3][3][kMaxN]
   unsigned* d_counter = nullptr;    // ticket counter of the fused last-block reductions (zero between launches)
   double* partials = nullptr;       // reduction partials

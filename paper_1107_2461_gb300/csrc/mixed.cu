@@ -809,6 +809,123 @@ __global__ void __launch_bounds__(TL) k_thomas_f32(Thomas32Args a, const int* __
   if ((threadIdx.x & 31) == 0 && vmax > 0.f) atomicMax(reinterpret_cast<unsigned int*>(a.fmax), __float_as_uint(vmax));
 }
 
+__device__ __forceinline__ void cp_async8(unsigned dst, const float2* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// FP32 Thomas sweep, two adjacent lines (i, j) and (i, j + 1) per thread (j
+// even): the copies, shared-memory reads, stores and coefficient reads are
+// shared by the two recurrences, which also give the thread two independent
+// dependency chains.  A pair holding the singular line of the zero-flux
+// Laplacian is left to k_thomas_f32 (launched over that pair only).  When ny
+// is odd the last pair's second line is a padding column of the row: it is
+// swept with a valid eigenvalue and excluded from the scale.
+template <int TL, bool FULL>
+__global__ void __launch_bounds__(TL) k_thomas2_f32(Thomas32Args a, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ float4 s_co[kMaxN];
+  __shared__ float2 ring[kNBR * kTB][TL];
+  __shared__ float2 ckp[kMaxN / kTB][TL];
+  const int nz = a.nz;
+  const float lam = (float)a.lambda;
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+    const float lko_k = (k + 1 < nz) ? lam * a.koz[k] : 0.f;
+    const float lko_m = (k > 0) ? lam * a.koz[k - 1] : 0.f;
+    s_co[k] = make_float4(a.mz[k], lam * a.kdz[k], -lko_m, -lko_k);
+  }
+  __syncthreads();
+  const int tid = threadIdx.x;
+  const int npair = (a.ny + 1) / 2;
+  const long long t = (long long)blockIdx.x * blockDim.x + tid;
+  float vmax = 0.f;
+  if (t < (long long)a.nx * npair) {
+    const int i = (int)(t / npair), j0 = 2 * (int)(t % npair);
+    const bool second = j0 + 1 < a.ny;
+    const int pl2 = (int)(a.plane / 2);  // plane stride in float2 (plane and pitch are even)
+    const double lab0 = a.lamx[i] + a.lamy[j0];
+    const double lab1 = a.lamx[i] + a.lamy[second ? j0 + 1 : j0];
+    if (!(a.singular_possible && (lab0 == 0.0 || lab1 == 0.0))) {
+      const float s0 = (float)(a.sigma - a.lambda * lab0), s1 = (float)(a.sigma - a.lambda * lab1);
+      float2* f = reinterpret_cast<float2*>(a.f + (long long)i * a.pitch + j0);
+      const int nb = (nz + kTB - 1) / kTB;
+      const unsigned ring0 = (unsigned)__cvta_generic_to_shared(&ring[0][tid]);
+      auto fetch = [&](int b) {
+        if (b >= 0 && b < nb) {
+          const unsigned dst = ring0 + (unsigned)((b % kNBR) * kTB * TL * 8);
+          const float2* src = f + (long long)b * kTB * pl2;
+          const int cnt = FULL ? kTB : min(kTB, nz - b * kTB);
+#pragma unroll
+          for (int e = 0; e < kTB; ++e)
+            if (FULL || e < cnt) cp_async8(dst + e * TL * 8, src + e * pl2);
+        }
+        cp_async_commit();
+      };
+      for (int q = 0; q < kNBR - 1; ++q) fetch(q);
+      float cp0 = 0.f, dp0 = 0.f, cp1 = 0.f, dp1 = 0.f;
+      for (int b = 0; b < nb; ++b) {
+        fetch(b + kNBR - 1);
+        cp_async_wait<kNBR - 1>();
+        ckp[b][tid] = make_float2(cp0, cp1);
+        const float2* rs = &ring[(b % kNBR) * kTB][tid];
+        float2* fo = f + (long long)b * kTB * pl2;
+        const int k0 = b * kTB;
+#pragma unroll
+        for (int e = 0; e < kTB; ++e) {
+          if (FULL || k0 + e < nz) {
+            const float4 co = s_co[k0 + e];
+            const float2 fv = rs[e * TL];
+            const float inv0 = rcp_fast(fmaf(-co.z, cp0, fmaf(s0, co.x, -co.y)));
+            const float inv1 = rcp_fast(fmaf(-co.z, cp1, fmaf(s1, co.x, -co.y)));
+            cp0 = co.w * inv0;
+            cp1 = co.w * inv1;
+            dp0 = fmaf(co.x, fv.x, -co.z * dp0) * inv0;
+            dp1 = fmaf(co.x, fv.y, -co.z * dp1) * inv1;
+            fo[e * pl2] = make_float2(dp0, dp1);
+          }
+        }
+      }
+      cp_async_wait<0>();
+      for (int q = 0; q < kNBR - 1; ++q) fetch(nb - 1 - q);
+      float u0 = 0.f, u1 = 0.f;
+      for (int b = nb - 1; b >= 0; --b) {
+        fetch(b - (kNBR - 1));
+        const int k0 = b * kTB;
+        float cpb0[kTB], cpb1[kTB];
+        const float2 cc = ckp[b][tid];
+        float c0 = cc.x, c1 = cc.y;
+#pragma unroll
+        for (int e = 0; e < kTB; ++e) {
+          if (FULL || k0 + e < nz) {
+            const float4 co = s_co[k0 + e];
+            c0 = co.w * rcp_fast(fmaf(-co.z, c0, fmaf(s0, co.x, -co.y)));
+            c1 = co.w * rcp_fast(fmaf(-co.z, c1, fmaf(s1, co.x, -co.y)));
+          }
+          cpb0[e] = c0;
+          cpb1[e] = c1;
+        }
+        cp_async_wait<kNBR - 1>();
+        const float2* rs = &ring[(b % kNBR) * kTB][tid];
+        float2* fo = f + (long long)k0 * pl2;
+#pragma unroll
+        for (int e = kTB - 1; e >= 0; --e) {
+          if (FULL || k0 + e < nz) {
+            const float2 dv = rs[e * TL];
+            u0 = fmaf(-cpb0[e], u0, dv.x);
+            u1 = fmaf(-cpb1[e], u1, dv.y);
+            fo[e * pl2] = make_float2(u0, u1);
+            vmax = fmaxf(vmax, fabsf(u0));
+            if (second) vmax = fmaxf(vmax, fabsf(u1));
+          }
+        }
+      }
+      cp_async_wait<0>();
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  if ((threadIdx.x & 31) == 0 && vmax > 0.f) atomicMax(reinterpret_cast<unsigned int*>(a.fmax), __float_as_uint(vmax));
+}
+
 __global__ void k_absmax(const float* __restrict__ in, long long rows, int n, int pitch, float* __restrict__ mx) {
   float v = 0.f;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < rows * n;
@@ -1081,7 +1198,26 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
       ta.fmax = sc + 2;
       const long long lines = (long long)nx * ny;
       const bool full = nz % kTB == 0;
-      if (p->thomas_tl == 64) {
+      if (p->thomas_tl == 2) {
+        // two lines per thread, 64 threads (128 lines) per CTA
+        const long long pairs = (long long)nx * ((ny + 1) / 2);
+        const unsigned g = (unsigned)((pairs + 63) / 64);
+        if (full)
+          k_thomas2_f32<64, true><<<g, 64, 0, s>>>(ta, skip);
+        else
+          k_thomas2_f32<64, false><<<g, 64, 0, s>>>(ta, skip);
+        FDI_LAUNCH_CHECK(p);
+        if (singular) {
+          // the null line (0, 0) and its pair partner, one line per thread
+          Thomas32Args t1 = ta;
+          t1.nx = 1;
+          t1.ny = std::min(ny, 2);
+          if (full)
+            k_thomas_f32<64, true><<<1, 64, 0, s>>>(t1, skip);
+          else
+            k_thomas_f32<64, false><<<1, 64, 0, s>>>(t1, skip);
+        }
+      } else if (p->thomas_tl == 64) {
         const unsigned g = (unsigned)((lines + 63) / 64);
         if (full)
           k_thomas_f32<64, true><<<g, 64, 0, s>>>(ta, skip);
