@@ -58,6 +58,21 @@ struct Field {
 
 }  // namespace fdi
 
+// Per-solve device workspace of a plan.  A MAC plan owns three extra slots so
+// that the u, v, w Helmholtz solves of a Stokes step can run concurrently.
+struct fdi_work_slot {
+  double* ws[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  float* wf[4] = {nullptr, nullptr, nullptr, nullptr};
+  float2* xdf = nullptr;
+  float* wr1 = nullptr;
+  long long wr1_plane = 0;
+  float* d_scales = nullptr;
+  float2* lam_w = nullptr;
+  double* partials = nullptr;
+  fdi::DevStatus* d_status = nullptr;
+  unsigned* d_counter = nullptr;
+};
+
 struct fdi_plan {
   fdi_grid grid;
   fdi_precision prec;
@@ -91,6 +106,10 @@ struct fdi_plan {
   double* mac_ih[3] = {nullptr, nullptr, nullptr};
   double* mac_idc[3] = {nullptr, nullptr, nullptr};
   fdi::KryState* d_kry = nullptr;
+  fdi_work_slot extra[3];           // MAC plans: workspaces of the concurrent u, v, w solves
+  int nextra = 0;
+  cudaStream_t sstream[3] = {nullptr, nullptr, nullptr};  // streams of those solves
+  cudaEvent_t sfork = nullptr, sjoin[3] = {nullptr, nullptr, nullptr};
   int stokes_precond = 1;           // 0: L_p^{-1} (paper), 1: L_p^{-1} - lambda I
   int krylov = 0;                   // 0: BiCGstab, 1: BiCGstab(2) (the paper's solver)
   double* kpartials = nullptr;
@@ -172,6 +191,24 @@ struct KTimer {
 
 // drop the captured solve graph (arguments or controls changed)
 void invalidate_graph(fdi_plan* p);
+
+// exchange the plan's per-solve workspace pointers with a slot (host side, so
+// a solve enqueued in between uses the slot's buffers)
+void swap_slot(fdi_plan* p, fdi_work_slot& w);
+struct SlotSwap {
+  fdi_plan* p;
+  fdi_work_slot* w;
+  SlotSwap(fdi_plan* p_, fdi_work_slot* w_) : p(p_), w(w_) {
+    if (w) swap_slot(p, *w);
+  }
+  ~SlotSwap() {
+    if (w) swap_slot(p, *w);
+  }
+};
+// allocate / free the per-solve workspace held in the plan's own pointers
+fdi_status alloc_workspace(fdi_plan* p);
+void free_workspace(fdi_plan* p);
+fdi_status mixed_alloc_workspace(fdi_plan* p);
 
 // autotuned configurations per grid shape (fdi_plan_autotune records, plan
 // creation applies)

@@ -1021,6 +1021,12 @@ fdi_status mixed_setup(fdi_plan* p) {
   cudaStreamDestroy(s);
   if (st != FDI_OK) return st;
   FDI_CUDA_TRY(e);
+  FDI_CUDA_TRY(cudaMalloc(&p->d_err, sizeof(int)));
+  FDI_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
+  return mixed_alloc_workspace(p);
+}
+
+fdi_status mixed_alloc_workspace(fdi_plan* p) {
   size_t szr = 1, szf = 1;
   for (int fi = 0; fi < p->nfields; ++fi) {
     const Field& f = p->fields[fi];
@@ -1036,8 +1042,6 @@ fdi_status mixed_setup(fdi_plan* p) {
   FDI_CUDA_TRY(cudaMalloc(&p->wr1, szr * 2 * sizeof(float)));              // r_1 as (hi, lo) planes
   p->wr1_plane = (long long)szr;
   FDI_CUDA_TRY(cudaMalloc(&p->d_scales, (size_t)(kMaxRefineCap + 2) * 4 * sizeof(float)));
-  FDI_CUDA_TRY(cudaMalloc(&p->d_err, sizeof(int)));
-  FDI_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
   FDI_CUDA_TRY(cudaMalloc(&p->lam_w, (size_t)9 * kMaxN * sizeof(float2)));
   FDI_CUDA_TRY(cudaMalloc(&p->d_counter, 4 * sizeof(unsigned)));
   FDI_CUDA_TRY(cudaMemset(p->d_counter, 0, 4 * sizeof(unsigned)));

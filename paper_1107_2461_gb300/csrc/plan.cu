@@ -9,6 +9,8 @@
 #include <cstring>
 #include <string>
 
+#include <utility>
+
 #include "fdi_internal.h"
 
 namespace fdi {
@@ -155,6 +157,52 @@ void free_axis(Axis* ax) {
   delete ax;
 }
 
+}  // namespace
+
+void swap_slot(fdi_plan* p, fdi_work_slot& w) {
+  for (int i = 0; i < 5; ++i) std::swap(p->ws[i], w.ws[i]);
+  for (int i = 0; i < 4; ++i) std::swap(p->wf[i], w.wf[i]);
+  std::swap(p->xdf, w.xdf);
+  std::swap(p->wr1, w.wr1);
+  std::swap(p->wr1_plane, w.wr1_plane);
+  std::swap(p->d_scales, w.d_scales);
+  std::swap(p->lam_w, w.lam_w);
+  std::swap(p->partials, w.partials);
+  std::swap(p->d_status, w.d_status);
+  std::swap(p->d_counter, w.d_counter);
+}
+
+fdi_status alloc_workspace(fdi_plan* p) {
+  for (int i = 0; i < 5; ++i) FDI_TRY(dev_alloc(&p->ws[i], (size_t)p->Pmax));
+  FDI_TRY(dev_alloc(&p->partials, (size_t)p->npartials * 4));
+  FDI_TRY(dev_alloc(&p->d_status, 1));
+  FDI_CUDA_TRY(cudaMemset(p->d_status, 0, sizeof(DevStatus)));
+  return FDI_OK;
+}
+
+void free_workspace(fdi_plan* p) {
+  for (double*& w : p->ws) {
+    if (w) cudaFree(w);
+    w = nullptr;
+  }
+  for (float*& w : p->wf) {
+    if (w) cudaFree(w);
+    w = nullptr;
+  }
+  void* ptrs[] = {p->xdf, p->wr1, p->d_counter, p->d_scales, p->lam_w, p->partials, p->d_status};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  p->xdf = nullptr;
+  p->wr1 = nullptr;
+  p->d_counter = nullptr;
+  p->d_scales = nullptr;
+  p->lam_w = nullptr;
+  p->partials = nullptr;
+  p->d_status = nullptr;
+}
+
+namespace {
+
 void free_plan(fdi_plan* p) {
   invalidate_graph(p);
   if (!p) return;
@@ -164,10 +212,15 @@ void free_plan(fdi_plan* p) {
   }
   for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
   for (Axis* a : p->axes) free_axis(a);
-  for (double* w : p->ws)
-    if (w) cudaFree(w);
-  for (float* w : p->wf)
-    if (w) cudaFree(w);
+  for (int c = 0; c < 3; ++c) {
+    swap_slot(p, p->extra[c]);
+    free_workspace(p);
+    swap_slot(p, p->extra[c]);
+    if (p->sstream[c]) cudaStreamDestroy(p->sstream[c]);
+    if (p->sjoin[c]) cudaEventDestroy(p->sjoin[c]);
+  }
+  if (p->sfork) cudaEventDestroy(p->sfork);
+  free_workspace(p);
   for (double* w : p->sk)
     if (w) cudaFree(w);
   for (double* w : p->skf)
@@ -178,14 +231,7 @@ void free_plan(fdi_plan* p) {
   }
   if (p->d_kry) cudaFree(p->d_kry);
   if (p->kpartials) cudaFree(p->kpartials);
-  if (p->xdf) cudaFree(p->xdf);
-  if (p->wr1) cudaFree(p->wr1);
-  if (p->d_counter) cudaFree(p->d_counter);
-  if (p->d_scales) cudaFree(p->d_scales);
-  if (p->lam_w) cudaFree(p->lam_w);
   if (p->d_err) cudaFree(p->d_err);
-  if (p->partials) cudaFree(p->partials);
-  if (p->d_status) cudaFree(p->d_status);
   if (p->h_flag) cudaFreeHost(p->h_flag);
   delete p;
 }
@@ -265,14 +311,25 @@ fdi_status build_plan(fdi_plan* p, const double* const faces[3], const fdi_bc bc
     f.zero_flux_all = f.ax[0]->zero_flux && f.ax[1]->zero_flux && f.ax[2]->zero_flux;
     if (f.P > p->Pmax) p->Pmax = f.P;
   }
-  for (int i = 0; i < 5; ++i) FDI_TRY(dev_alloc(&p->ws[i], (size_t)p->Pmax));
   p->npartials = 16384;  // per-block partial sums of the reductions (>= blocks of any reduction grid)
-  FDI_TRY(dev_alloc(&p->partials, (size_t)p->npartials * 4));
-  FDI_TRY(dev_alloc(&p->d_status, 1));
-  FDI_CUDA_TRY(cudaMemset(p->d_status, 0, sizeof(DevStatus)));
+  FDI_TRY(alloc_workspace(p));
   FDI_CUDA_TRY(cudaMallocHost((void**)&p->h_flag, sizeof(int) * 4));
   if (p->prec != FDI_PREC_FP64) FDI_TRY(mixed_setup(p));
-  if (p->grid == FDI_GRID_MAC) FDI_TRY(stokes_setup(p));
+  if (p->grid == FDI_GRID_MAC) {
+    FDI_TRY(stokes_setup(p));
+    // three more workspaces and streams for the concurrent velocity solves
+    for (int c = 0; c < 3; ++c) {
+      swap_slot(p, p->extra[c]);
+      fdi_status st2 = alloc_workspace(p);
+      if (st2 == FDI_OK && p->prec != FDI_PREC_FP64) st2 = mixed_alloc_workspace(p);
+      swap_slot(p, p->extra[c]);
+      p->nextra = c + 1;
+      FDI_TRY(st2);
+      FDI_CUDA_TRY(cudaStreamCreateWithFlags(&p->sstream[c], cudaStreamNonBlocking));
+      FDI_CUDA_TRY(cudaEventCreateWithFlags(&p->sjoin[c], cudaEventDisableTiming));
+    }
+    FDI_CUDA_TRY(cudaEventCreateWithFlags(&p->sfork, cudaEventDisableTiming));
+  }
   return FDI_OK;
 }
 

@@ -89,8 +89,9 @@ std::vector<double> tanh_faces(int n, double beta) {
 
 // Device bytes a MAC Stokes plan allocates (upper estimate of plan.cu,
 // mixed.cu, tc_transform.cu and stokes.cu): per direction and kind the FP64
-// operator and eigen data (+ split fp16 copies for mixed plans), five FP64
-// workspace fields, the mixed FP32 workspace, and the Krylov / face vectors.
+// operator and eigen data (+ split fp16 copies for mixed plans), four per-solve
+// workspaces (five FP64 fields, partials, the mixed FP32 planes), and the
+// Krylov / face vectors.
 extern "C" size_t fdi_stokes_plan_bytes_estimate(const int n[3], int prec) {
   const long long P = cells(n);
   size_t b = 0;
@@ -100,10 +101,12 @@ extern "C" size_t fdi_stokes_plan_bytes_estimate(const int n[3], int prec) {
     b += 3 * per_axis;  // cell-Dirichlet, cell-Neumann, face kinds
   }
   const size_t Pp = (size_t)(n[0] + 4) * (n[1] + 4) * n[2];  // padded FP32 rows
-  b += 5 * (size_t)P * 8;                                      // FP64 workspace
-  if (prec != FDI_PREC_FP64) b += 4 * Pp * 4 + 3 * (size_t)P * 4 + 2 * Pp * 4;
+  // four per-solve workspaces (the plan's own and one per velocity component)
+  size_t slot = 5 * (size_t)P * 8 + (size_t)16384 * 4 * 8;  // FP64 workspace, partials
+  if (prec != FDI_PREC_FP64) slot += 4 * Pp * 4 + 3 * (size_t)P * 4 + 2 * Pp * 4;
+  b += 4 * slot;
   b += 10 * (size_t)P * 8 + 6 * (size_t)P * 8;  // Krylov vectors, face work fields
-  b += (size_t)16384 * 4 * 8 + ((size_t)4 << 20);  // partials, small tables, slack
+  b += (size_t)4 << 20;                          // small tables, slack
   return b;
 }
 

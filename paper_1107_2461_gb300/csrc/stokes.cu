@@ -509,6 +509,28 @@ fdi_status stokes_setup(fdi_plan* p) {
 
 namespace {
 
+// H_c^{-1} in_c -> out_c for c = u, v, w: the three solves run concurrently on
+// the plan's side streams, each with its own workspace slot, forked from and
+// joined back to s (also inside a stream capture)
+fdi_status three_solves(fdi_plan* p, double lambda, const double* const in[3], double* const out[3],
+                        cudaStream_t s) {
+  if (p->nextra < 3) {
+    for (int c = 0; c < 3; ++c) FDI_TRY(field_solve(p, 1 + c, 1.0, lambda, in[c], out[c], s));
+    return FDI_OK;
+  }
+  FDI_CUDA_TRY(cudaEventRecord(p->sfork, s));
+  for (int c = 0; c < 3; ++c) {
+    FDI_CUDA_TRY(cudaStreamWaitEvent(p->sstream[c], p->sfork, 0));
+    {
+      SlotSwap guard(p, &p->extra[c]);
+      FDI_TRY(field_solve(p, 1 + c, 1.0, lambda, in[c], out[c], p->sstream[c]));
+    }
+    FDI_CUDA_TRY(cudaEventRecord(p->sjoin[c], p->sstream[c]));
+    FDI_CUDA_TRY(cudaStreamWaitEvent(s, p->sjoin[c], 0));
+  }
+  return FDI_OK;
+}
+
 fdi_status cmatvec(fdi_plan* p, const MacGeom& g, double lambda, double* q, double* out, cudaStream_t s) {
   // out = C (-q) = -sum_c D_c H_c^{-1} G_c q   (q holds -phat, see k_bicg_xr)
   dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
@@ -517,7 +539,11 @@ fdi_status cmatvec(fdi_plan* p, const MacGeom& g, double lambda, double* q, doub
     k_grad<<<grd, blk, 0, s>>>(g, q, -1.0, p->skf[0], p->skf[1], p->skf[2]);
     FDI_LAUNCH_CHECK(p);
   }
-  for (int c = 0; c < 3; ++c) FDI_TRY(field_solve(p, 1 + c, 1.0, lambda, p->skf[c], p->skf[3 + c], s));
+  {
+    const double* in[3] = {p->skf[0], p->skf[1], p->skf[2]};
+    double* out3[3] = {p->skf[3], p->skf[4], p->skf[5]};
+    FDI_TRY(three_solves(p, lambda, in, out3, s));
+  }
   FDI_KTIMER(p, "stokes_div", s);
   k_div<<<grd, blk, 0, s>>>(g, p->skf[3], p->skf[4], p->skf[5], out);
   FDI_LAUNCH_CHECK(p);
@@ -546,7 +572,7 @@ fdi_status stokes_solve(fdi_plan* p, double dt, double Re, const double* const f
   const unsigned vb = 152 * 4, vt = 256;
   const dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
   // step 1: predictors u_hat_c = H_c^{-1} f_c, kept in the outputs
-  for (int c = 0; c < 3; ++c) FDI_TRY(field_solve(p, 1 + c, 1.0, lambda, f[c], u[c], s));
+  FDI_TRY(three_solves(p, lambda, f, u, s));
   // b = D u_hat; r = rhat = b; x = p = v = 0
   k_div<<<grd, blk, 0, s>>>(g, u[0], u[1], u[2], b);
   FDI_LAUNCH_CHECK(p);
@@ -700,8 +726,12 @@ fdi_status stokes_solve(fdi_plan* p, double dt, double Re, const double* const f
   // step 3: u_c = u_hat_c - H_c^{-1} (G q)_c   (x holds q; grad with +1)
   k_grad<<<grd, blk, 0, s>>>(g, x, 1.0, p->skf[0], p->skf[1], p->skf[2]);
   FDI_LAUNCH_CHECK(p);
+  {
+    const double* in[3] = {p->skf[0], p->skf[1], p->skf[2]};
+    double* out3[3] = {p->skf[3], p->skf[4], p->skf[5]};
+    FDI_TRY(three_solves(p, lambda, in, out3, s));
+  }
   for (int c = 0; c < 3; ++c) {
-    FDI_TRY(field_solve(p, 1 + c, 1.0, lambda, p->skf[c], p->skf[3 + c], s));
     k_sub<<<vb, vt, 0, s>>>(u[c], p->skf[3 + c], p->fields[1 + c].P);
     FDI_LAUNCH_CHECK(p);
   }
