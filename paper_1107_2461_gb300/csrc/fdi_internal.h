@@ -96,6 +96,7 @@ struct fdi_plan {
   int thomas_tl = 2;                // FP32 Thomas: lines per CTA (64, 128) or 2 = two lines per thread
   float2* lam_w = nullptr;          // lambda-scaled double-float flux weights [3][3][kMaxN]
   unsigned* d_counter = nullptr;    // ticket counter of the fused last-block reductions (zero between launches)
+  cudaStream_t cstream = nullptr;   // mixed plans: captures the bodies of conditional refinement rounds
   double* partials = nullptr;       // reduction partials
   int npartials = 0;
   fdi::DevStatus* d_status = nullptr;

@@ -23,6 +23,7 @@
 // Every refinement-round kernel reads the device "done" flag and returns at
 // once after convergence, so the solve is enqueued without host round trips.
 #include <cmath>
+#include <vector>
 
 #include "df.cuh"
 #include "fdi_internal.h"
@@ -55,6 +56,9 @@ struct FinishArgs {
   DevStatus* st;
   double tol;
   int kind, want_mean;
+  // captured solves: condition of the next refinement round's graph node
+  // (set to "not converged"); 0 when running eagerly
+  cudaGraphConditionalHandle next_round = 0;
 };
 
 struct ResidArgs {
@@ -616,7 +620,10 @@ __device__ void finish_if_last(const FinishArgs& f, int t, int nt) {
   if (!amlast) return;
   __threadfence();
   finish_block(f.partials, (int)nb, f.st, f.tol, f.kind, f.want_mean, t, nt);
-  if (t == 0) *f.counter = 0u;
+  if (t == 0) {
+    *f.counter = 0u;
+    if (f.next_round) cudaGraphSetConditional(f.next_round, f.st->done ? 0u : 1u);
+  }
 }
 
 __global__ void k_finish_mixed(const double* __restrict__ partials, int nblocks, DevStatus* st, double tol,
@@ -1023,6 +1030,7 @@ fdi_status mixed_setup(fdi_plan* p) {
   FDI_CUDA_TRY(e);
   FDI_CUDA_TRY(cudaMalloc(&p->d_err, sizeof(int)));
   FDI_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
+  FDI_CUDA_TRY(cudaStreamCreateWithFlags(&p->cstream, cudaStreamNonBlocking));
   return mixed_alloc_workspace(p);
 }
 
@@ -1132,7 +1140,9 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     FDI_LAUNCH_CHECK(p);
   }
 
-  for (int round = 0; round <= p->max_refine; ++round) {
+  // one refinement round (round 0: the first solve) enqueued on stream s;
+  // next_round: graph condition the round's residual check sets
+  auto enqueue_round = [&](int round, cudaStream_t s, cudaGraphConditionalHandle next_round) -> fdi_status {
     const int* skip = round == 0 ? nullptr : done;
     float* sc = p->d_scales + 4 * round;
     float* sc_next = p->d_scales + 4 * (round + 1);
@@ -1297,12 +1307,64 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
       ak.r_lo = r1l;
       ak.out = out;
       ak.rmax = sc_next + 0;
-      ak.fin = FinishArgs{p->d_counter, p->partials, p->d_status, p->tol, round == 0 ? 1 : 2, singular ? 1 : 0};
+      ak.fin = FinishArgs{p->d_counter, p->partials, p->d_status, p->tol, round == 0 ? 1 : 2, singular ? 1 : 0,
+                          next_round};
       const bool write_out = !singular && round > 0;
       ResidKernel kern = resid_kernel(ra.sig_mode, round == 0 ? 0 : 1, round >= 2, singular, write_out);
       kern<<<rgrid, dim3(kResTX, kResTY), 0, s>>>(ak, skip);
       FDI_LAUNCH_CHECK(p);
     }
+      return FDI_OK;
+  };
+  // Eagerly, every round is enqueued and returns at once after convergence.
+  // In a captured solve, round r >= 2 sits in a conditional graph node placed
+  // (nested) in round r-1's graph, whose residual check sets the condition, so
+  // a converged solve launches nothing more.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaGraph_t cgraph = nullptr;
+  if (p->max_refine >= 2 && p->cstream &&
+      cudaStreamGetCaptureInfo(s, &cap, nullptr, &cgraph, nullptr, nullptr, nullptr) == cudaSuccess &&
+      cap == cudaStreamCaptureStatusActive && cgraph) {
+    // add an IF node after the current capture point of `st` (capturing into
+    // `g`); returns its body graph
+    auto add_if = [&](cudaStream_t st, cudaGraph_t g, cudaGraphConditionalHandle h, cudaGraph_t* body) -> fdi_status {
+      const cudaGraphNode_t* deps = nullptr;
+      size_t ndeps = 0;
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      cudaGraph_t gg = nullptr;
+      FDI_CUDA_TRY(cudaStreamGetCaptureInfo(st, &cs, nullptr, &gg, &deps, nullptr, &ndeps));
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeIf;
+      cp.conditional.size = 1;
+      cudaGraphNode_t node = nullptr;
+      FDI_CUDA_TRY(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &cp));
+      FDI_CUDA_TRY(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+      *body = cp.conditional.phGraph_out[0];
+      return FDI_OK;
+    };
+    cudaGraphConditionalHandle h = 0;
+    FDI_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, cgraph, 0, cudaGraphCondAssignDefault));
+    FDI_TRY(enqueue_round(0, s, 0));
+    FDI_TRY(enqueue_round(1, s, h));
+    cudaGraph_t body = nullptr;
+    FDI_TRY(add_if(s, cgraph, h, &body));
+    for (int r = 2; r <= p->max_refine; ++r) {
+      cudaGraphConditionalHandle hn = 0;
+      if (r < p->max_refine) FDI_CUDA_TRY(cudaGraphConditionalHandleCreate(&hn, body, 0, cudaGraphCondAssignDefault));
+      FDI_CUDA_TRY(cudaStreamBeginCaptureToGraph(p->cstream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+      fdi_status st = enqueue_round(r, p->cstream, hn);
+      cudaGraph_t next_body = nullptr;
+      if (st == FDI_OK && hn) st = add_if(p->cstream, body, hn, &next_body);
+      cudaGraph_t done_graph = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(p->cstream, &done_graph);
+      FDI_TRY(st);
+      FDI_CUDA_TRY(e);
+      body = next_body;
+    }
+  } else {
+    for (int round = 0; round <= p->max_refine; ++round) FDI_TRY(enqueue_round(round, s, 0));
   }
   {
     // FP64 output when the loop stopped before its last round (and, for the

@@ -220,6 +220,7 @@ void free_plan(fdi_plan* p) {
     if (p->sjoin[c]) cudaEventDestroy(p->sjoin[c]);
   }
   if (p->sfork) cudaEventDestroy(p->sfork);
+  if (p->cstream) cudaStreamDestroy(p->cstream);
   free_workspace(p);
   for (double* w : p->sk)
     if (w) cudaFree(w);
