@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/fdi.h"
@@ -128,6 +129,7 @@ struct fdi_plan {
   // arguments (field, sigma, lambda, arrays, stream) is captured once and then
   // replayed with a single graph launch
   bool use_graphs = true;
+  bool pdl = true;                  // programmatic dependent launch between the mixed solve's kernels
   struct GraphKey {
     int field = -1;
     double sigma = 0.0, lambda = 0.0;
@@ -189,6 +191,30 @@ struct KTimer {
   ~KTimer();
 };
 #define FDI_KTIMER(plan, name, stream) ::fdi::KTimer _kt_##__LINE__((plan), (name), (stream))
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization is launched while its predecessor in the stream completes and
+// calls pdl_wait() before touching anything the predecessor writes (returns
+// once the predecessor has completed and its memory is visible); a no-op for
+// ordinary launches.  (Triggering the successor early, as each CTA starts,
+// measured slower: its CTAs then held SMs the predecessor's tail needed.)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = pdl ? attr : nullptr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // drop the captured solve graph (arguments or controls changed)
 void invalidate_graph(fdi_plan* p);

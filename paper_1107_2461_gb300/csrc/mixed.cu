@@ -347,6 +347,7 @@ template <int MODE, int SIG, bool LO, bool MEAN, bool OUT>
 // occupancy: 4 CTAs per SM for the first check, 5 for the correction checks
 // (measured best; the latter spills a few registers to L1)
 __global__ void __launch_bounds__(kResTX * kResTY, MODE == 1 ? 5 : 4) k_resid_df(ResidArgs a, const int* __restrict__ skip) {
+  pdl_wait();
   if (skip && *skip) return;
   __shared__ double sh[4 * kResTY];
   const bool interior = blockIdx.x > 0 && (int)(blockIdx.x + 1) * kResTX < a.nx && blockIdx.y > 0 &&
@@ -380,6 +381,7 @@ ResidKernel resid_kernel(int sig_mode, int mode, bool lo, bool mean, bool out) {
 __global__ void k_finalize_out(const float* __restrict__ xh, const float* __restrict__ xl,
                                const float* __restrict__ xll, double* __restrict__ out, long long P,
                                const DevStatus* __restrict__ st, int max_refine, int singular) {
+  pdl_wait();
   // refinement passes write the output themselves: only convergence in round 0
   // (no refinement step taken, L = 0) and the singular problem need this pass
   if (!singular && (st->refine_steps > 0 || max_refine == 0)) return;
@@ -398,6 +400,7 @@ __global__ void k_finalize_out(const float* __restrict__ xh, const float* __rest
 // r_0 = b: FP64 -> FP32 copy into the padded residual layout, ||b||^2, max |b|
 // and (singular problems) the volume-weighted sums; one warp per x-line
 __global__ void __launch_bounds__(256) k_init_rhs(ResidArgs a) {
+  pdl_wait();
   __shared__ double sh[4 * 8];
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -460,6 +463,7 @@ __global__ void __launch_bounds__(256) k_init_rhs(ResidArgs a) {
 // stream, 8 values per thread and iteration (four 16-byte loads in flight),
 // ||b||^2 and max |b|
 __global__ void __launch_bounds__(256) k_init_rhs_flat(ResidArgs a, long long P) {
+  pdl_wait();
   __shared__ double sh[8];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   float sbb = 0.f, rmax = 0.f;
@@ -683,6 +687,7 @@ __device__ __forceinline__ void cp_async_wait() {
 template <int TL, bool FULL>
 __global__ void __launch_bounds__(TL) k_thomas_f32(Thomas32Args a, const int* __restrict__ skip) {
   constexpr int kTL = TL;
+  pdl_wait();
   if (skip && *skip) return;
   // coefficients of the z operator in shared memory: {M_k, lambda Kd_k,
   // lower, upper} with the off-diagonals negated (lambda-scaled), and the
@@ -829,6 +834,7 @@ __device__ __forceinline__ void cp_async8(unsigned dst, const float2* src) {
 // swept with a valid eigenvalue and excluded from the scale.
 template <int TL, bool FULL>
 __global__ void __launch_bounds__(TL) k_thomas2_f32(Thomas32Args a, const int* __restrict__ skip) {
+  pdl_wait();
   if (skip && *skip) return;
   __shared__ float4 s_co[kMaxN];
   __shared__ float2 ring[kNBR * kTB][TL];
@@ -1134,20 +1140,22 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     a0.rmax = p->d_scales + 0;
     a0.fin = FinishArgs{p->d_counter, p->partials, p->d_status, p->tol, 0, singular ? 1 : 0};
     if (px == nx && !singular && (reinterpret_cast<uintptr_t>(b) & 15u) == 0)
-      k_init_rhs_flat<<<iblocks, 256, 0, s>>>(a0, f.P);
+      FDI_CUDA_TRY(launch_pdl(true, k_init_rhs_flat, dim3(iblocks), dim3(256), 0, s, a0, f.P));
     else
-      k_init_rhs<<<iblocks, 256, 0, s>>>(a0);
+      FDI_CUDA_TRY(launch_pdl(true, k_init_rhs, dim3(iblocks), dim3(256), 0, s, a0));
     FDI_LAUNCH_CHECK(p);
   }
 
   // one refinement round (round 0: the first solve) enqueued on stream s;
   // next_round: graph condition the round's residual check sets
   auto enqueue_round = [&](int round, cudaStream_t s, cudaGraphConditionalHandle next_round) -> fdi_status {
+    const bool pdl = p->pdl && round < 2;  // later rounds may run inside conditional graph bodies
     const int* skip = round == 0 ? nullptr : done;
     float* sc = p->d_scales + 4 * round;
     float* sc_next = p->d_scales + 4 * (round + 1);
     // forward x: r [z][y][x] -> F1 [z][i][y] (round 1 reads r_1 from its own planes)
     TcArgs t{};
+    t.pdl = pdl ? 1 : 0;
     t.skip = skip;
     t.err = p->d_err;
     t.in = round == 1 ? r1h : r;
@@ -1217,9 +1225,9 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
         const long long pairs = (long long)nx * ((ny + 1) / 2);
         const unsigned g = (unsigned)((pairs + 63) / 64);
         if (full)
-          k_thomas2_f32<64, true><<<g, 64, 0, s>>>(ta, skip);
+          FDI_CUDA_TRY(launch_pdl(pdl, k_thomas2_f32<64, true>, dim3(g), dim3(64), 0, s, ta, skip));
         else
-          k_thomas2_f32<64, false><<<g, 64, 0, s>>>(ta, skip);
+          FDI_CUDA_TRY(launch_pdl(pdl, k_thomas2_f32<64, false>, dim3(g), dim3(64), 0, s, ta, skip));
         FDI_LAUNCH_CHECK(p);
         if (singular) {
           // the null line (0, 0) and its pair partner, one line per thread
@@ -1234,15 +1242,15 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
       } else if (p->thomas_tl == 64) {
         const unsigned g = (unsigned)((lines + 63) / 64);
         if (full)
-          k_thomas_f32<64, true><<<g, 64, 0, s>>>(ta, skip);
+          FDI_CUDA_TRY(launch_pdl(pdl, k_thomas_f32<64, true>, dim3(g), dim3(64), 0, s, ta, skip));
         else
-          k_thomas_f32<64, false><<<g, 64, 0, s>>>(ta, skip);
+          FDI_CUDA_TRY(launch_pdl(pdl, k_thomas_f32<64, false>, dim3(g), dim3(64), 0, s, ta, skip));
       } else {
         const unsigned g = (unsigned)((lines + 127) / 128);
         if (full)
-          k_thomas_f32<128, true><<<g, 128, 0, s>>>(ta, skip);
+          FDI_CUDA_TRY(launch_pdl(pdl, k_thomas_f32<128, true>, dim3(g), dim3(128), 0, s, ta, skip));
         else
-          k_thomas_f32<128, false><<<g, 128, 0, s>>>(ta, skip);
+          FDI_CUDA_TRY(launch_pdl(pdl, k_thomas_f32<128, false>, dim3(g), dim3(128), 0, s, ta, skip));
       }
       FDI_LAUNCH_CHECK(p);
     }
@@ -1311,7 +1319,7 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
                           next_round};
       const bool write_out = !singular && round > 0;
       ResidKernel kern = resid_kernel(ra.sig_mode, round == 0 ? 0 : 1, round >= 2, singular, write_out);
-      kern<<<rgrid, dim3(kResTX, kResTY), 0, s>>>(ak, skip);
+      FDI_CUDA_TRY(launch_pdl(pdl, kern, rgrid, dim3(kResTX, kResTY), 0, s, ak, skip));
       FDI_LAUNCH_CHECK(p);
     }
       return FDI_OK;
@@ -1372,8 +1380,9 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     // projects the null line only to single precision, and the constant is
     // outside the range of A, so shifting it leaves the residual)
     FDI_KTIMER(p, "finalize_out", s);
-    k_finalize_out<<<kBlocks, kThreads, 0, s>>>(xH, xL, xLL, out, f.P, p->d_status, p->max_refine,
-                                                singular ? 1 : 0);
+    FDI_CUDA_TRY(launch_pdl(true, k_finalize_out, dim3(kBlocks), dim3(kThreads), 0, s, (const float*)xH,
+                            (const float*)xL, (const float*)xLL, out, f.P, (const DevStatus*)p->d_status,
+                            p->max_refine, singular ? 1 : 0));
     FDI_LAUNCH_CHECK(p);
   }
   return FDI_OK;

@@ -82,6 +82,7 @@ template <int C>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_transform(const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmA,
                    const __grid_constant__ CUtensorMap tmO, TcArgs a) {
+  pdl_wait();
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // the swizzled layouts need a 1024-byte aligned base; the launch reserves no
@@ -667,13 +668,15 @@ fdi_status launch_cluster(fdi_plan* p, const TcMatrix& m, const CUtensorMap& map
   cfg.blockDim = dim3(THREADS);
   cfg.dynamicSmemBytes = SMEM_BYTES;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = args.pdl ? 2 : 1;
   FDI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_transform<C>, map, mapA, mapO, args));
   FDI_LAUNCH_CHECK(p);
   return FDI_OK;

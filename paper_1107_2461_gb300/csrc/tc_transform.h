@@ -53,6 +53,7 @@ struct TcArgs {
   int tma_store = 0;
   const int* skip = nullptr;
   int* err = nullptr;
+  int pdl = 0;                      // launch with programmatic stream serialization
   // filled by the launcher
   int N_pad = 0, nK = 0;
   const float* col_scale = nullptr;
