@@ -74,9 +74,6 @@ __device__ __forceinline__ float scale_from_max(float mx) {
   return __uint_as_float((uint32_t)se << 23);
 }
 
-__device__ __forceinline__ uint32_t pack_half2(__half a, __half b) {
-  return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
-}
 
 template <int C>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -297,11 +294,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int e = 0; e < 8; e += 2) {
           const float x0 = (k0 + e < a.K) ? v[q][e] * sA : 0.f;
           const float x1 = (k0 + e + 1 < a.K) ? v[q][e + 1] * sA : 0.f;
-          const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
-          const __half l0 = __float2half_rn(x0 - __half2float(h0));
-          const __half l1 = __float2half_rn(x1 - __half2float(h1));
-          hw[e / 2] = pack_half2(h0, h1);
-          lw[e / 2] = pack_half2(l0, l1);
+          // packed conversions (one instruction per pair, round to nearest)
+          const __half2 h = __floats2half2_rn(x0, x1);
+          const float2 hf = __half22float2(h);
+          const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+          hw[e / 2] = *reinterpret_cast<const uint32_t*>(&h);
+          lw[e / 2] = *reinterpret_cast<const uint32_t*>(&l);
         }
         const uint32_t off = tc::sw64_offset(row, kofs_q[q]);
         *reinterpret_cast<uint4*>(st + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
