@@ -240,23 +240,37 @@ def run_arm(fdi, torch, prec, n, K, W, dev, rank, stream, cluster=None, thomas_a
     torch.cuda.synchronize()
     ktimes = fdi.kernel_times(plan)
     fdi.enable_timing(plan, False)
-    # end to end through the C ABI with host buffers: H2D of f, solve, D2H of u
-    h_in = torch.from_numpy(f).pin_memory()
-    h_out = torch.empty(h_in.shape, dtype=torch.float64).pin_memory()
+    # end to end through the C ABI with host buffers (fdi_field_solve_host):
+    # every step copies its right-hand side from pinned host memory to the
+    # device and its solution back; the library pipelines the copies of
+    # neighbouring steps with the solves.  Two distinct right-hand sides and
+    # two result arrays alternate.
+    h_in = [torch.from_numpy(f).pin_memory(),
+            torch.from_numpy(workloads.rhs_uniform(n[::-1], rank + 1000)).pin_memory()]
+    h_out = [torch.empty(h_in[0].shape, dtype=torch.float64).pin_memory() for _ in range(2)]
+    rhs_seq = [h_in[i % 2] for i in range(K)]
+    out_seq = [h_out[i % 2] for i in range(K)]
+    fdi.field_solve_host(plan, fdi.FIELD_CELL, 1.0, LAM, rhs_seq[:4], out_seq[:4], stream)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rel_host = fdi.field_solve_host(plan, fdi.FIELD_CELL, 1.0, LAM, rhs_seq, out_seq, stream)
+    e2e_s = time.perf_counter() - t0
+    # the same without overlap: copy in, solve, copy out, one step after another
     d_in = torch.empty_like(rhs)
     d_out = torch.empty_like(rhs)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
-        for _ in range(K):
-            d_in.copy_(h_in, non_blocking=True)
+        for i in range(K):
+            d_in.copy_(h_in[i % 2], non_blocking=True)
             fdi.helmholtz_solve(plan, LAM, d_in, d_out, stream)
-            h_out.copy_(d_out, non_blocking=True)
+            h_out[i % 2].copy_(d_out, non_blocking=True)
     stream.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_serial_s = time.perf_counter() - t0
     plan.destroy()
     return {"ms": ms, "steps": steps, "rel": rel, "status": st, "ktimes": ktimes, "launches_per": launches_per,
-            "e2e_s": e2e_s, "h2d": f.nbytes, "d2h": f.nbytes, "clocks": clk.summary()}
+            "e2e_s": e2e_s, "e2e_serial_s": e2e_serial_s, "e2e_max_rel": max(rel_host), "h2d": f.nbytes,
+            "d2h": f.nbytes, "clocks": clk.summary()}
 
 
 def run_stokes(fdi, torch, prec, n, reps, warm, stream, krylov=0):
@@ -443,10 +457,10 @@ def main():
             raise
     # slowest rank
     for a in arms.values():
-        t = torch.tensor([a["ms"], a["e2e_s"]], dtype=torch.float64, device=dev)
+        t = torch.tensor([a["ms"], a["e2e_s"], a["e2e_serial_s"]], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        a["ms_max"], a["e2e_max"] = float(t[0]), float(t[1])
+        a["ms_max"], a["e2e_max"], a["e2e_serial_max"] = float(t[0]), float(t[1]), float(t[2])
         a["value"] = world * P * a.get("K", K) / (a["ms_max"] * 1e-3)
         a["ok"] = a["status"] == 0 and a["rel"] <= a["tol"]
     best_name = max((k for k in arms if arms[k]["ok"]), key=lambda k: arms[k]["value"], default=None)
@@ -529,8 +543,12 @@ def main():
         "ms_per_step": best["ms_max"] / best.get("K", K), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if best_name == "fp64" else "f16-split/f32-acc + f64 refinement",
         "data": "synthetic", "config": dict(workload, arm=best_name, parallelism=f"replicas x{world}"),
-        "e2e": {"value": world * P * best.get("K", K) / best["e2e_max"], "unit": "grid-pts/s", "h2d_bytes_per_step": best["h2d"],
-                "d2h_bytes_per_step": best["d2h"]},
+        "e2e": {"value": world * P * best.get("K", K) / best["e2e_max"], "unit": "grid-pts/s",
+                "h2d_bytes_per_step": best["h2d"], "d2h_bytes_per_step": best["d2h"],
+                "api": "fdi_field_solve_host (host FP64 arrays in and out, copies pipelined with the solves)",
+                "max_rel_residual": best["e2e_max_rel"],
+                "serial_value": world * P * best.get("K", K) / best["e2e_serial_max"],
+                "serial": "copy in, solve, copy out per step on one stream, no overlap"},
         "gpu_launches": best["launches_per"] * K,
         "roofline": roof,
         "cpu_baseline": cpu,

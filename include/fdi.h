@@ -127,6 +127,25 @@ fdi_status fdi_laplace_solve(fdi_plan* plan, const double* rhs, double* out, fdi
 fdi_status fdi_field_solve(fdi_plan* plan, fdi_field field, double sigma, double lambda,
                            const double* rhs, double* out, fdi_stream_t stream);
 
+/* fdi_field_solve for count right-hand sides held in HOST memory (Sec. 3 direct
+ * inverse with refinement, once per right-hand side).  h_rhs[i], h_out[i]:
+ * host arrays of the field's size (C order, FP64); h_out[i] may equal
+ * h_rhs[i]; page-locked memory (cudaHostAlloc / cudaHostRegister) lets the
+ * copies overlap the solves, pageable memory works serialised.  The solves are
+ * pipelined: the host-to-device copy of right-hand side i+1 and the
+ * device-to-host copy of solution i-1 run on two plan-owned copy streams while
+ * solve i runs on `stream` (the default stream is replaced by a plan-owned
+ * one).  Device staging for two right-hand sides and two solutions (4 x the
+ * field size in doubles) is allocated by the plan on first use and kept until
+ * fdi_plan_destroy.  Blocking: returns once every solution is in host memory.
+ * rel_residual: NULL or count doubles, each solve's final relative residual.
+ * Returns FDI_OK when every solve met its tolerance, else the status of the
+ * first that did not (the message names its index); fdi_last_result then
+ * describes the last solve. */
+fdi_status fdi_field_solve_host(fdi_plan* plan, fdi_field field, double sigma, double lambda,
+                                const double* const* h_rhs, double* const* h_out, int count,
+                                double* rel_residual, fdi_stream_t stream);
+
 /* Semi-direct Stokes inverse on a FDI_GRID_MAC plan (Sec. 2, three steps after
  * Eq. 9).  f[c], u[c]: device velocity fields (sizes above); p: device pressure.
  * Outputs must not alias inputs. */

@@ -125,9 +125,10 @@ struct fdi_plan {
   double last_res = 0.0;
   long long launches = 0;
   bool status_valid = false;
-  // CUDA graph of the field solve: a call that repeats the previous call's
-  // arguments (field, sigma, lambda, arrays, stream) is captured once and then
-  // replayed with a single graph launch
+  // CUDA graphs of the field solve: a call that repeats the arguments (field,
+  // sigma, lambda, arrays, stream) of one of the last few distinct calls is
+  // captured on its second occurrence and replayed with a single graph launch
+  // afterwards (a small LRU set, so alternating buffers keep their graphs)
   bool use_graphs = true;
   bool pdl = true;                  // programmatic dependent launch between the mixed solve's kernels
   struct GraphKey {
@@ -137,10 +138,26 @@ struct fdi_plan {
     double* out = nullptr;
     cudaStream_t s = nullptr;
   };
-  GraphKey gkey;
-  bool gkey_valid = false;
-  cudaGraphExec_t gexec = nullptr;
-  long long glaunches = 0;
+  static constexpr int kGraphSlots = 4;
+  struct GraphSlot {
+    GraphKey key;
+    bool valid = false;
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+    unsigned long long last_use = 0;
+  };
+  GraphSlot gslots[kGraphSlots];
+  unsigned long long gclock = 0;
+  // host-buffer solves (fdi_field_solve_host): device staging for two
+  // right-hand sides and two solutions, copy streams and their events, and
+  // the per-solve status records
+  double* hstage[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long hstage_len = 0;
+  cudaStream_t hcopy[3] = {nullptr, nullptr, nullptr};  // host-to-device, device-to-host, compute fallback
+  cudaEvent_t hev[7] = {};          // in[2], solved[2], out[2], start
+  fdi::DevStatus* d_hstat = nullptr;
+  fdi::DevStatus* h_hstat = nullptr;  // pinned
+  int hstat_cap = 0;
   // CUDA graph of one BiCGstab iteration of the Stokes inverse (every
   // iteration after the first enqueues the same launches on plan workspace)
   cudaGraphExec_t kgraph = nullptr;
@@ -162,6 +179,8 @@ namespace fdi {
 
 // error helpers
 void set_error(const std::string& msg);
+fdi_status solve_status(const fdi_plan* plan, const DevStatus& st, int kerr);
+void free_host_staging(fdi_plan* p);
 #define FDI_CUDA_TRY(expr)                                                      \
   do {                                                                          \
     cudaError_t _e = (expr);                                                    \
@@ -271,6 +290,8 @@ fdi_status launch_reset_status(fdi_plan* p, cudaStream_t s);
 fdi_status field_solve(fdi_plan* p, int field, double sigma, double lambda, const double* rhs, double* out,
                        cudaStream_t s);
 fdi_status validate_field_args(const fdi_plan* p, int field, double sigma, double lambda);
+fdi_status field_solve_entry(fdi_plan* p, int field, double sigma, double lambda, const double* rhs, double* out,
+                             cudaStream_t s);
 
 // mixed path (mixed.cu)
 fdi_status mixed_setup(fdi_plan* p);

@@ -317,7 +317,10 @@ __global__ void k_finish_residual(const double* __restrict__ partials, int nbloc
       st->refine_steps += 1;
     }
     st->rel_res = rel;
-    if (!isfinite(rel)) {
+    if (first && !isfinite(b)) {
+      st->error = 7;  // non-finite right-hand side
+      st->done = 1;
+    } else if (!isfinite(rel)) {
       st->error = 1;
       st->done = 1;
     } else {

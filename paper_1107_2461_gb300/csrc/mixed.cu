@@ -589,6 +589,14 @@ __device__ void finish_block(const double* __restrict__ partials, int nblocks, D
     if (want_mean) st->mean_b = tt[2] / tt[3];
     st->rel_res = 1.0;
     st->done = 0;
+    if (!isfinite(tt[1])) {  // non-finite right-hand side: nothing more runs
+      st->error = 7;
+      st->done = 1;
+    }
+    return;
+  }
+  if (st->error == 7) {  // a non-finite right-hand side stays reported as such
+    st->done = 1;
     return;
   }
   // the first check (r_1 = b - A H) also measures ||b||; later checks reuse it
@@ -1330,6 +1338,7 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
   // a converged solve launches nothing more.
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaGraph_t cgraph = nullptr;
+  bool conditional = false;
   if (p->max_refine >= 2 && p->cstream &&
       cudaStreamGetCaptureInfo(s, &cap, nullptr, &cgraph, nullptr, nullptr, nullptr) == cudaSuccess &&
       cap == cudaStreamCaptureStatusActive && cgraph) {
@@ -1352,6 +1361,7 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
       *body = cp.conditional.phGraph_out[0];
       return FDI_OK;
     };
+    conditional = true;
     cudaGraphConditionalHandle h = 0;
     FDI_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, cgraph, 0, cudaGraphCondAssignDefault));
     FDI_TRY(enqueue_round(0, s, 0));
@@ -1379,8 +1389,11 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     // zero-flux Laplace problem, minus the volume-weighted mean: the FP32 sweep
     // projects the null line only to single precision, and the constant is
     // outside the range of A, so shifting it leaves the residual)
+    // after a conditional node the launch is an ordinary one: a programmatic
+    // edge needs a kernel upstream, and this pass reads what the node's body
+    // writes
     FDI_KTIMER(p, "finalize_out", s);
-    FDI_CUDA_TRY(launch_pdl(true, k_finalize_out, dim3(kBlocks), dim3(kThreads), 0, s, (const float*)xH,
+    FDI_CUDA_TRY(launch_pdl(!conditional, k_finalize_out, dim3(kBlocks), dim3(kThreads), 0, s, (const float*)xH,
                             (const float*)xL, (const float*)xLL, out, f.P, (const DevStatus*)p->d_status,
                             p->max_refine, singular ? 1 : 0));
     FDI_LAUNCH_CHECK(p);

@@ -18,6 +18,29 @@ namespace fdi {
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+// Status of a finished solve from its device record and the plan's wait-limit
+// flag: a kernel that gave up waiting, a non-finite right-hand side, a
+// numerical failure, or a residual above the tolerance of that solve.
+fdi_status solve_status(const fdi_plan* plan, const DevStatus& st, int kerr) {
+  if (kerr) {
+    set_error("a tensor-core kernel stopped at a wait limit");
+    return FDI_ERR_TIMEOUT;
+  }
+  if (st.error == 7) {
+    set_error("non-finite values in the right-hand side");
+    return FDI_ERR_INVALID_ARG;
+  }
+  if (st.error) {
+    set_error("numerical breakdown (non-finite residual, Krylov breakdown or iteration limit)");
+    return FDI_ERR_NOT_CONVERGED;
+  }
+  if (!(st.rel_res <= (st.tol_used > 0.0 ? st.tol_used : plan->tol))) {
+    set_error("residual above the tolerance after the last refinement step");
+    return FDI_ERR_NOT_CONVERGED;
+  }
+  return FDI_OK;
+}
+
 static cudaEvent_t pool_event(fdi_plan* p) {
   cudaEvent_t e = nullptr;
   if (!p->event_pool.empty()) {
@@ -204,8 +227,9 @@ void free_workspace(fdi_plan* p) {
 namespace {
 
 void free_plan(fdi_plan* p) {
-  invalidate_graph(p);
   if (!p) return;
+  invalidate_graph(p);
+  free_host_staging(p);
   for (auto& t : p->pending) {
     cudaEventDestroy(t.e0);
     cudaEventDestroy(t.e1);
@@ -461,24 +485,15 @@ fdi_status fdi_last_result(const fdi_plan* plan, int* iters, int* refine_steps, 
   if (iters) *iters = st.iters;
   if (refine_steps) *refine_steps = st.refine_steps;
   if (rel_residual) *rel_residual = st.rel_res;
+  int kerr = 0;
   if (plan->d_err) {
-    int kerr = 0;
     e = cudaMemcpy(&kerr, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) {
       set_error(std::string("status copy: ") + cudaGetErrorString(e));
       return FDI_ERR_CUDA;
     }
-    if (kerr) {
-      set_error("a tensor-core kernel stopped at a wait limit");
-      return FDI_ERR_TIMEOUT;
-    }
   }
-  if (st.error) return FDI_ERR_NOT_CONVERGED;
-  if (!(st.rel_res <= (st.tol_used > 0.0 ? st.tol_used : plan->tol))) {
-    set_error("residual above the tolerance after the last refinement step");
-    return FDI_ERR_NOT_CONVERGED;
-  }
-  return FDI_OK;
+  return fdi::solve_status(plan, st, kerr);
 }
 
 fdi_status fdi_plan_eigen(const fdi_plan* plan, fdi_field field, int d, double* lam, double* E,

@@ -136,10 +136,10 @@ void apply_tuning(fdi_plan* p) {
 }
 
 void invalidate_graph(fdi_plan* p) {
-  if (p->gexec) cudaGraphExecDestroy(p->gexec);
-  p->gexec = nullptr;
-  p->gkey_valid = false;
-  p->glaunches = 0;
+  for (fdi_plan::GraphSlot& g : p->gslots) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = fdi_plan::GraphSlot{};
+  }
   if (p->kgraph) cudaGraphExecDestroy(p->kgraph);
   p->kgraph = nullptr;
   p->kgraph_precond = -1;
@@ -153,11 +153,14 @@ bool same_key(const fdi_plan::GraphKey& a, const fdi_plan::GraphKey& b) {
          a.s == b.s;
 }
 
+}  // namespace
+
 // Field solve through the graph cache: the first call with new arguments runs
 // eagerly, the second identical call is captured (stream capture of the same
 // launch sequence) and every later identical call is one graph launch.  The
-// legacy default stream cannot be captured and timed plans need their events,
-// so both run eagerly.
+// cache keeps the graphs of the last few distinct argument sets.  The legacy
+// default stream cannot be captured and timed plans need their events, so both
+// run eagerly.
 fdi_status field_solve_entry(fdi_plan* p, int field, double sigma, double lambda, const double* rhs, double* out,
                              cudaStream_t s) {
   if (!p) return FDI_ERR_INVALID_ARG;
@@ -171,47 +174,66 @@ fdi_status field_solve_entry(fdi_plan* p, int field, double sigma, double lambda
   key.rhs = rhs;
   key.out = out;
   key.s = s;
-  if (p->gkey_valid && same_key(key, p->gkey) && p->gexec) {
-    FDI_CUDA_TRY(cudaGraphLaunch(p->gexec, s));
-    p->launches = p->glaunches;
+  fdi_plan::GraphSlot* g = nullptr;
+  for (fdi_plan::GraphSlot& c : p->gslots)
+    if (c.valid && same_key(key, c.key)) g = &c;
+  if (g && g->exec) {
+    g->last_use = ++p->gclock;
+    FDI_CUDA_TRY(cudaGraphLaunch(g->exec, s));
+    p->launches = g->launches;
     return FDI_OK;
   }
-  if (!p->gkey_valid || !same_key(key, p->gkey)) {
-    invalidate_graph(p);
+  if (!g) {
+    // first call with these arguments: eager; remember the key in a free or
+    // the least recently used slot
+    g = &p->gslots[0];
+    for (fdi_plan::GraphSlot& c : p->gslots) {
+      if (!c.valid) {
+        g = &c;
+        break;
+      }
+      if (c.last_use < g->last_use) g = &c;
+    }
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    *g = fdi_plan::GraphSlot{};
     fdi_status st = field_solve(p, field, sigma, lambda, rhs, out, s);
     if (st == FDI_OK) {
-      p->gkey = key;
-      p->gkey_valid = true;
+      g->key = key;
+      g->valid = true;
+      g->last_use = ++p->gclock;
     }
     return st;
   }
   // second call with these arguments: capture, instantiate, launch
+  g->last_use = ++p->gclock;
   FDI_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   fdi_status st = field_solve(p, field, sigma, lambda, rhs, out, s);
-  cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamEndCapture(s, &g);
-  if (st != FDI_OK || e != cudaSuccess || g == nullptr) {
-    if (g) cudaGraphDestroy(g);
+  cudaGraph_t gr = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s, &gr);
+  if (st != FDI_OK || e != cudaSuccess || gr == nullptr) {
+    if (gr) cudaGraphDestroy(gr);
     cudaGetLastError();
-    invalidate_graph(p);
+    *g = fdi_plan::GraphSlot{};
     if (st != FDI_OK) return st;
     return field_solve(p, field, sigma, lambda, rhs, out, s);  // capture refused: eager
   }
   const long long n_launch = p->launches;
   cudaGraphExec_t ex = nullptr;
-  e = cudaGraphInstantiate(&ex, g, 0);
-  cudaGraphDestroy(g);
+  e = cudaGraphInstantiate(&ex, gr, 0);
+  cudaGraphDestroy(gr);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    invalidate_graph(p);
+    *g = fdi_plan::GraphSlot{};
     return field_solve(p, field, sigma, lambda, rhs, out, s);
   }
-  p->gexec = ex;
-  p->glaunches = n_launch;
-  FDI_CUDA_TRY(cudaGraphLaunch(p->gexec, s));
+  g->exec = ex;
+  g->launches = n_launch;
+  FDI_CUDA_TRY(cudaGraphLaunch(g->exec, s));
   p->launches = n_launch;
   return FDI_OK;
 }
+
+namespace {
 
 // ---- batched solves: independent plans run concurrently on a pool of streams ----
 

@@ -154,6 +154,10 @@ __global__ void __launch_bounds__(kDotThreads) k_kry_finish(const double* __rest
       st->rel = a > 0.0 ? 1.0 : 0.0;
       st->done = a > 0.0 ? 0 : 1;
       st->error = 0;
+      if (!isfinite(a)) {  // non-finite right-hand side
+        st->error = 7;
+        st->done = 1;
+      }
       break;
     case KF_ALPHA:  // a = rhat.v
       if (a == 0.0 || !isfinite(a)) {
@@ -207,6 +211,10 @@ __global__ void __launch_bounds__(kDotThreads) k_kry_finish(const double* __rest
       st->rel = a > 0.0 ? 1.0 : 0.0;
       st->done = a > 0.0 ? 0 : 1;
       st->error = 0;
+      if (!isfinite(a)) {  // non-finite right-hand side
+        st->error = 7;
+        st->done = 1;
+      }
       break;
     case KF_L2_RHO0:  // new outer iteration: rho0 = -omega rho0, then the j = 0 step (a = rhat.r_0)
       st->rho = -st->omega * st->rho;
@@ -439,7 +447,7 @@ __global__ void k_stokes_report(const KryState* __restrict__ st, DevStatus* ds) 
   ds->iters = st->iters;
   ds->refine_steps = 0;
   ds->rel_res = st->rel;
-  ds->error = st->error ? 1 : 0;
+  ds->error = st->error == 7 ? 7 : (st->error ? 1 : 0);
   ds->done = 1;
   ds->tol_used = st->tol;
 }

@@ -55,6 +55,7 @@ SIGNATURES = {
     "fdi_field_solve": (_i, [_vp, _i, _d, _d, _vp, _vp, _vp]),
     "fdi_stokes_solve": (_i, [_vp, _d, _d, C.POINTER(_vp), C.POINTER(_vp), _vp, _vp]),
     "fdi_helmholtz_solve_batched": (_i, [C.POINTER(_vp), C.POINTER(_d), C.POINTER(_vp), C.POINTER(_vp), _i, _vp]),
+    "fdi_field_solve_host": (_i, [_vp, _i, _d, _d, C.POINTER(_vp), C.POINTER(_vp), _i, C.POINTER(_d), _vp]),
     "fdi_last_result": (_i, [_vp, C.POINTER(_i), C.POINTER(_i), C.POINTER(_d)]),
     "fdi_plan_eigen": (_i, [_vp, _i, _i, C.POINTER(_d), C.POINTER(_d), C.POINTER(_d), C.POINTER(_i)]),
     "fdi_last_launch_count": (_i, [_vp, C.POINTER(C.c_longlong)]),
@@ -234,6 +235,40 @@ def helmholtz_solve_batched(plans, lambdas, rhs, out, stream=None):
     ra = (C.c_void_p * k)(*[_ptr(t) for t in rhs])
     oa = (C.c_void_p * k)(*[_ptr(t) for t in out])
     _check(load().fdi_helmholtz_solve_batched(pa, la, ra, oa, k, _stream(stream)), "fdi_helmholtz_solve_batched")
+
+
+def _host_ptr(x, count):
+    """Address of a C-contiguous FP64 host array (numpy array or CPU torch tensor)."""
+    if hasattr(x, "data_ptr"):
+        if x.is_cuda or not x.is_contiguous() or str(x.dtype) != "torch.float64":
+            raise ValueError("host arrays must be contiguous float64 CPU tensors")
+        if x.numel() != count:
+            raise ValueError(f"host array has {x.numel()} values, the field {count}")
+        return x.data_ptr()
+    if not (x.dtype == "float64" and x.flags["C_CONTIGUOUS"]):
+        raise ValueError("host arrays must be C-contiguous float64")
+    if x.size != count:
+        raise ValueError(f"host array has {x.size} values, the field {count}")
+    return x.ctypes.data
+
+
+def field_solve_host(plan: Plan, field, sigma, lam, rhs, out, stream=None):
+    """Solves for each host right-hand side rhs[i] into the host array out[i]
+    (pipelined host-device copies; pinned CPU tensors overlap best).  Returns
+    the relative residual of every solve; raises if one missed its tolerance."""
+    k = len(rhs)
+    if len(out) != k:
+        raise ValueError("rhs and out must have the same length")
+    count = int(np.prod(plan.field_shape(field)))
+    for o in out:
+        if not hasattr(o, "data_ptr") and not o.flags["WRITEABLE"]:
+            raise ValueError("output host array is read-only")
+    ra = (C.c_void_p * max(k, 1))(*[_host_ptr(t, count) for t in rhs])
+    oa = (C.c_void_p * max(k, 1))(*[_host_ptr(t, count) for t in out])
+    rel = (C.c_double * max(k, 1))()
+    _check(load().fdi_field_solve_host(plan.handle, int(field), float(sigma), float(lam), ra, oa, k, rel,
+                                       _stream(stream)), "fdi_field_solve_host")
+    return [rel[i] for i in range(k)]
 
 
 def last_result(plan: Plan):
