@@ -51,7 +51,7 @@ constexpr int NCONV = 8;
 constexpr int WARP_A = 2 + NCONV + 4;         // A producer warp
 constexpr int THREADS = 32 * (WARP_A + 1);
 constexpr bool kTmaTransposed = false;
-constexpr int EPI_WARP_BYTES = 5 * 1024;      // per epilogue warp: transpose tile (32 x 33) or TMA staging (32 x 32)
+constexpr int EPI_WARP_BYTES = 8 * 1024;      // per epilogue warp: transpose tile (32 x 33) or two TMA staging tiles (32 x 32)
 constexpr int TP_BYTES = 4 * EPI_WARP_BYTES;
 constexpr int BAR_BYTES = 256;
 constexpr int CS_BYTES = NMAX * 4;            // per-column unscale factors
@@ -125,8 +125,13 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmB);
   if (warp == WARP_A && lane == 0) tc::prefetch_tmap(&tmA);
+  // per output column: the matrix row's scale times the input's inverse scale
+  // (both powers of two)
   float* s_cs = reinterpret_cast<float*>(smem + BAR_OFF + BAR_BYTES);
-  for (int k = threadIdx.x; k < N_pad; k += blockDim.x) s_cs[k] = a.col_scale[k];
+  {
+    const float inv_s = 1.0f / scale_from_max(a.scale_in ? *a.scale_in : 1.0f);
+    for (int k = threadIdx.x; k < N_pad; k += blockDim.x) s_cs[k] = a.col_scale[k] * inv_s;
+  }
   if (warp == 1) {
     tc::tmem_alloc(tmem_slot, tmem_cols);
     tc::tmem_relinquish();
@@ -349,9 +354,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     // column (transposed outputs) or 4 consecutive columns of one row (row-major
     // outputs) and stores them with one 16-byte access where the layout allows.
     const int q = warp & 3;  // TMEM lane quarter accessible to this warp
-    const float inv_sA = 1.0f / scale_from_max(a.scale_in ? *a.scale_in : 1.0f);
-    float* tp = reinterpret_cast<float*>(smem + EPI_OFF + (warp - (2 + NCONV)) * EPI_WARP_BYTES);
-    const uint32_t stg_u32 = tc::smem_u32(tp);  // TMA staging (1024-byte aligned)
+    float* tp0 = reinterpret_cast<float*>(smem + EPI_OFF + (warp - (2 + NCONV)) * EPI_WARP_BYTES);
+    uint32_t nstore = 0;  // TMA stores issued by this warp: staging tile nstore & 1 is next
     const bool rowmajor = a.col_stride == 1;
     // vector stores need 16-byte aligned groups of 4 along the contiguous index
     const bool vec_t = !rowmajor && a.row_stride == 1 && (a.S % 4 == 0) && (a.slab_stride % 4 == 0) &&
@@ -387,16 +391,19 @@ __global__ void __launch_bounds__(THREADS, 1)
         tc::tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * N_pad + c0), r);
         tc::tmem_ld_wait();
         if (a.tma_store) {
-          // unscale into the staging tile and hand it to a TMA store; rows past
+          // unscale into a staging tile and hand it to a TMA store; rows past
           // R and columns past n_out hold zeros (zero-filled A rows, zero B
-          // rows) and are clipped by the store
-          if (lane == 0) tc::bulk_wait_read_all();  // the previous store has read the tile
+          // rows) and are clipped by the store.  Two staging tiles alternate:
+          // the store two back (same tile) must have read it, the last one may
+          // still be reading the other
+          float* tp = tp0 + (nstore & 1u) * 1024;
+          if (lane == 0) tc::bulk_wait_read_1();
           __syncwarp();
           if (a.tma_store == 1) {
             // staging [column][row]: 32 rows of one column are 128 contiguous bytes
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-              const float v = __uint_as_float(r[j]) * s_cs[c0 + j] * inv_sA;
+              const float v = __uint_as_float(r[j]) * s_cs[c0 + j];
               vmax = fmaxf(vmax, fabsf(v));
               tp[j * 32 + lane] = v;
             }
@@ -408,7 +415,7 @@ __global__ void __launch_bounds__(THREADS, 1)
               float v4[4];
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
-                v4[e] = __uint_as_float(r[4 * u + e]) * s_cs[c0 + 4 * u + e] * inv_sA;
+                v4[e] = __uint_as_float(r[4 * u + e]) * s_cs[c0 + 4 * u + e];
                 vmax = fmaxf(vmax, fabsf(v4[e]));
               }
               *reinterpret_cast<float4*>(tp + lane * 32 + ((u ^ (lane & 7)) << 2)) =
@@ -417,15 +424,20 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           tc::fence_proxy_async_smem();
           __syncwarp();
-          if (lane == 0 && nrows > 0) {
-            if (a.tma_store == 1)
-              tc::tma_store_3d(&tmO, stg_u32, (int)(wrow0 % a.S), c0, (int)(wrow0 / a.S));
-            else
-              tc::tma_store_2d(&tmO, stg_u32, c0, (int)wrow0);
-            tc::bulk_commit();
+          if (nrows > 0) {
+            if (lane == 0) {
+              const uint32_t stg = tc::smem_u32(tp);  // 1024-byte aligned
+              if (a.tma_store == 1)
+                tc::tma_store_3d(&tmO, stg, (int)(wrow0 % a.S), c0, (int)(wrow0 / a.S));
+              else
+                tc::tma_store_2d(&tmO, stg, c0, (int)wrow0);
+              tc::bulk_commit();
+            }
+            ++nstore;
           }
           continue;
         }
+        float* tp = tp0;
 #pragma unroll
         for (int j = 0; j < 32; ++j) tp[lane * 33 + j] = __uint_as_float(r[j]);
         __syncwarp();
@@ -437,7 +449,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int cl = 4 * qq + g8;
             const int k = c0 + cl;
             if (k < a.n_out) {
-              const float cs = s_cs[k] * inv_sA;
+              const float cs = s_cs[k];
               float v4[4];
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
@@ -461,7 +473,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const int k = c0 + cc + e;
-            cs[e] = (k < a.n_out) ? s_cs[k] * inv_sA : 0.f;
+            cs[e] = (k < a.n_out) ? s_cs[k] : 0.f;
           }
           const bool fullcols = c0 + cc + 3 < a.n_out;
           if (a.mode == TC_OUT_F32) {
