@@ -505,7 +505,7 @@ def main():
         stokes = {}
         for name in args.arms.split(","):
             prec = precs[name][0]
-            for kname, kry in (("", 0), ("/bicgstab2", 1)):
+            for kname, kry in (("", 0), ("/bicgstab2", 1), ("/cg", 2)):
                 try:
                     stokes[name + kname] = run_stokes(fdi, torch, prec, args.stokes_n, args.stokes_reps, 2, stream,
                                                       krylov=kry)
@@ -554,7 +554,8 @@ def main():
         "cpu_baseline": cpu,
         "clocks": best["clocks"],
         "stokes_latency": ({"config": f"MAC {args.stokes_n}^3, tanh {BETA}, no-slip, Re 1000, Gaussian forcing; "
-                                      "BiCGstab (default) and BiCGstab(2) (/bicgstab2; iterations are outer ones)",
+                                      "BiCGstab (default), BiCGstab(2) (/bicgstab2; iterations are outer ones) and "
+                                      "volume-weighted CG (/cg; one C-product per iteration)",
                             **stokes} if stokes is not None else None),
         "batched": batch,
         "serving": serving,

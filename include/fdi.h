@@ -155,8 +155,13 @@ fdi_status fdi_stokes_solve(fdi_plan* plan, double dt, double Re, const double* 
 /* Krylov method of fdi_stokes_solve for the pressure system C q = D u_hat
  * (Sec. 2): 0 BiCGstab (van der Vorst; default), 1 BiCGstab(2) (Sleijpen &
  * Fokkema's BiCGstab(l) with l = 2, the paper's choice), both right-
- * preconditioned, FP64 scalars on the device.  With BiCGstab(2),
- * fdi_last_result reports outer iterations (four C-products each). */
+ * preconditioned, or 2 conjugate gradients on -C q = -D u_hat in the
+ * volume-weighted inner product sum(V x y), in which C is self-adjoint and -C
+ * and the preconditioner's negative are positive definite on zero-mean
+ * pressures (one C-product per iteration); FP64 scalars on the device.
+ * fdi_last_result reports iterations: outer ones for BiCGstab(2) (four
+ * C-products each), two C-products each for BiCGstab, one for CG.
+ * Other values: FDI_ERR_INVALID_ARG. */
 fdi_status fdi_plan_set_krylov(fdi_plan* plan, int method);
 
 /* Preconditioner of the pressure-matrix Krylov solve: mode 0 is the paper's

@@ -20,8 +20,13 @@ The three-step semi-direct inverse (Sec. 2, 3D steps after Eq. 9), with q = dt*p
   2. solve C q = D u_hat,  C = sum_c D_c H_c^{-1} G_c   (Eq. 9, the pressure matrix)
   3. u_c = u_hat_c - H_c^{-1} (G q)_c
 Step 2 is solved by a Krylov method preconditioned by the inverse pressure
-Laplacian L_p = D G (Sec. 2, after Eq. 9): plain BiCGstab (van der Vorst) or
-the paper's BiCGstab(2) (Sleijpen & Fokkema's BiCGstab(ell), ell = 2).
+Laplacian L_p = D G (Sec. 2, after Eq. 9): plain BiCGstab (van der Vorst), the
+paper's BiCGstab(2) (Sleijpen & Fokkema's BiCGstab(ell), ell = 2), or
+conjugate gradients in the volume-weighted inner product.  C is not symmetric
+as a matrix (Sec. 2) but it is self-adjoint in that inner product: D is minus
+the volume-weighted adjoint of G, and M_u H_c^{-1} is symmetric, so
+V C = -G^T (M_u H^{-1}) G with V the cell volumes; -C is positive definite on
+the zero-mean pressures, and so are -L_p^{-1} and -L_p^{-1} + lam*I.
 """
 from __future__ import annotations
 
@@ -199,6 +204,38 @@ def bicgstab(apply_A, apply_Minv, b, tol, maxiter):
     return x, it, rel
 
 
+def pcg(apply_A, apply_B, b, weights, tol, maxiter):
+    """Preconditioned conjugate gradients (Hestenes & Stiefel 1952) for A x = b
+    with A and the preconditioner B self-adjoint and positive definite in the
+    inner product <x, y> = sum(weights * x * y), FP64 scalars.
+
+    Returns (x, iterations, ||b - A x|| / ||b||) (Euclidean norms)."""
+    w = np.asarray(weights, dtype=np.float64)
+    x = np.zeros_like(b)
+    r = b.copy()
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return x, 0, 0.0
+    p = np.zeros_like(b)
+    rho = 1.0
+    it = 0
+    rel = 1.0
+    while it < maxiter:
+        z = apply_B(r)
+        rho_new = float(np.sum(w * r * z))
+        p = z if it == 0 else z + (rho_new / rho) * p
+        rho = rho_new
+        v = apply_A(p)
+        alpha = rho / float(np.sum(w * p * v))
+        x = x + alpha * p
+        r = r - alpha * v
+        it += 1
+        rel = float(np.linalg.norm(r)) / bnorm
+        if rel <= tol:
+            break
+    return x, it, rel
+
+
 def bicgstab_l(apply_A, apply_Minv, b, ell, tol, maxiter):
     """Right-preconditioned BiCGstab(ell) (Sleijpen & Fokkema 1993), the Krylov
     solver of the paper (ell = 2, Sec. 2), FP64 scalars.
@@ -276,7 +313,9 @@ def stokes_semi_direct(faces, dt, Re, f, tol=1e-11, maxiter=200, method="tpt", p
     (precond="cahouet-chabard": Cahouet & Chabard 1988, the exact inverse of
     C = L_p (I - lam L_p)^{-1} when the discrete operators commute).
 
-    krylov: "bicgstab" or "bicgstab2" (the paper's choice, Sec. 2).
+    krylov: "bicgstab", "bicgstab2" (the paper's choice, Sec. 2) or "cg"
+    (conjugate gradients on -C q = -b in the volume-weighted inner product,
+    preconditioned by minus the chosen preconditioner).
     Returns ((u, v, w), p, iterations, relative C-residual)."""
     lam = dt / Re
     D, G = div_grad_3d(faces)
@@ -299,11 +338,13 @@ def stokes_semi_direct(faces, dt, Re, f, tol=1e-11, maxiter=200, method="tpt", p
 
     uhat = [Hinv(c, f[c]) for c in range(3)]
     b = sum(D[c] @ uhat[c] for c in range(3))
+    vol = asm.volumes(pops)
     if krylov == "bicgstab2":
         q, it, rel = bicgstab_l(C, Lp_inv, b, 2, tol, maxiter)
+    elif krylov == "cg":
+        q, it, rel = pcg(lambda v: -C(v), lambda v: -Lp_inv(v), -b, vol, tol, maxiter)
     else:
         q, it, rel = bicgstab(C, Lp_inv, b, tol, maxiter)
-    vol = asm.volumes(pops)
     q = q - np.dot(vol, q) / vol.sum()
     vel = tuple((uhat[c] - Hinv(c, G[c] @ q)).reshape(vs[c]) for c in range(3))
     return vel, (q / dt).reshape(ps), it, rel

@@ -12,7 +12,8 @@
 //     stream; a request arriving while others run is admitted as soon as a
 //     slot and memory are free, and its kernels overlap theirs on the device.
 //   * Each worker runs the whole request: host -> device copies of the forcing,
-//     the Stokes inverse on its plan, device -> host copies of u and p.  A plan
+//     the Stokes inverse on its plan (pressure system by conjugate gradients in
+//     the volume-weighted inner product), device -> host copies of u and p.  A plan
 //     is used by one request at a time (plans are not shared across streams).
 //   * Latency = completion - submission (queueing included); p50 / p99 and
 //     throughput are reported by fdi_server_stats.
@@ -225,6 +226,12 @@ void worker(fdi_server* sv) {
       const double* faces[3] = {fx.data(), fy.data(), fz.data()};
       const fdi_bc dir[3] = {FDI_BC_DIRICHLET, FDI_BC_DIRICHLET, FDI_BC_DIRICHLET};
       st = fdi_plan_create(faces, r.n, dir, dir, FDI_GRID_MAC, r.prec, 2, &plan);
+      // conjugate gradients in the volume-weighted inner product: one C-product
+      // per iteration (the lowest latency of the three Krylov methods)
+      if (st == FDI_OK && (st = fdi_plan_set_krylov(plan, 2)) != FDI_OK) {
+        fdi_plan_destroy(plan);
+        plan = nullptr;
+      }
       std::lock_guard<std::mutex> lk(sv->mu);
       if (st == FDI_OK) {
         const PlanKey key{r.n[0], r.n[1], r.n[2], r.beta, (int)r.prec};

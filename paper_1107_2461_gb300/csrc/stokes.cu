@@ -14,6 +14,11 @@
 // operators C = L_p (I - lambda L_p)^{-1}, whose inverse is exactly
 // L_p^{-1} - lambda I; it reduces to the paper's choice as dt -> 0 and keeps
 // the iteration count bounded at large dt, where L_p^{-1} alone stagnates.
+// Krylov methods: BiCGstab (default), the paper's BiCGstab(2), or conjugate
+// gradients in the volume-weighted inner product <x, y> = sum V x y, in which C
+// is self-adjoint (D is minus the volume-weighted adjoint of G): -C and the
+// preconditioners -L_p^{-1} and -L_p^{-1} + lambda I are positive definite on
+// zero-mean pressures, and CG needs one C-product per iteration.
 // The Krylov scalars, dot products and vector updates stay on the device in
 // FP64 (deterministic two-stage reductions); the host reads one convergence
 // flag per iteration.  The pressure is returned with zero volume-weighted mean.
@@ -133,7 +138,7 @@ __device__ __forceinline__ void sum_partials(const double* partials, double& a, 
 enum {
   KF_INIT = 0, KF_ALPHA = 1, KF_OMEGA = 2, KF_ITER = 3, KF_MEAN = 4,
   KF_L2_INIT = 5, KF_L2_RHO0 = 6, KF_L2_RHO = 7, KF_L2_ALPHA = 8, KF_L2_MR1 = 9, KF_L2_TAU = 10, KF_L2_MR2 = 11,
-  KF_L2_CONV = 12
+  KF_L2_CONV = 12, KF_CG_RHO = 13, KF_CG_ALPHA = 14, KF_CG_ITER = 15
 };
 
 __global__ void __launch_bounds__(kDotThreads) k_kry_finish(const double* __restrict__ partials, KryState* st,
@@ -262,6 +267,41 @@ __global__ void __launch_bounds__(kDotThreads) k_kry_finish(const double* __rest
         st->gpp1 = st->g2;
       }
       break;
+    // ---- conjugate gradients (volume-weighted inner product) ----
+    case KF_CG_RHO: {  // a = <r, z>: beta = a / rho (after the first iteration), rho = a
+      if (!(a > 0.0) || !isfinite(a)) {
+        st->error = 2;
+        st->done = 1;
+        break;
+      }
+      st->beta = st->iters > 0 ? a / st->rho : 0.0;
+      st->rho = a;
+      break;
+    }
+    case KF_CG_ALPHA:  // a = <p, A p>
+      if (!(a > 0.0) || !isfinite(a)) {
+        st->error = 2;
+        st->done = 1;
+      } else {
+        st->alpha = st->rho / a;
+      }
+      break;
+    case KF_CG_ITER: {  // a = r.r after the update
+      st->iters += 1;
+      st->rnorm2 = a;
+      const double rel = sqrt(a / st->bnorm2);
+      st->rel = rel;
+      if (!isfinite(rel)) {
+        st->error = 4;
+        st->done = 1;
+      } else if (rel <= st->tol) {
+        st->done = 1;
+      } else if (st->iters >= st->maxit) {
+        st->done = 1;
+        st->error = 5;
+      }
+      break;
+    }
     case KF_L2_CONV: {  // a = r_0.r_0 after the minimal-residual update
       st->iters += 1;
       st->rnorm2 = a;
@@ -353,6 +393,12 @@ __global__ void k_neg(double* __restrict__ x, const double* __restrict__ t, long
     x[q] = -t[q];
 }
 
+// x = -x
+__global__ void k_negate(double* __restrict__ x, long long n) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    x[q] = -x[q];
+}
+
 // p = r + beta (p - omega v),  beta = (rho / rho_old)(alpha / omega)
 __global__ void k_bicg_p(const KryState* __restrict__ st, double* __restrict__ p, const double* __restrict__ r,
                          const double* __restrict__ v, long long n, int first) {
@@ -436,6 +482,59 @@ __global__ void k_sub(double* __restrict__ u, const double* __restrict__ h, long
 __global__ void k_axpy(double* __restrict__ y, double c, const double* __restrict__ x, long long n) {
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
     y[q] = fma(c, x[q], y[q]);
+}
+
+// ---- conjugate gradients ----
+
+// partial sums of sum V a b over the cells (V = cell volume)
+__global__ void __launch_bounds__(kDotThreads) k_wdot(MacGeom g, const double* __restrict__ a,
+                                                      const double* __restrict__ b, double* __restrict__ partials) {
+  const int nx = g.nx, ny = g.ny;
+  const long long n = (long long)nx * ny * g.nz;
+  double s0 = 0.0, s1 = 0.0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % nx);
+    const long long t = q / nx;
+    const int j = (int)(t % ny), k = (int)(t / ny);
+    s0 = fma(g.m[0][i] * g.m[1][j] * g.m[2][k], a[q] * b[q], s0);
+  }
+  block_reduce2(s0, s1);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = s0;
+    partials[2 * blockIdx.x + 1] = s1;
+  }
+}
+
+// p = z (first iteration) or z + beta p
+__global__ void k_cg_p(const KryState* __restrict__ st, double* __restrict__ p, const double* __restrict__ z,
+                       long long n, int first) {
+  if (st->done) return;
+  const double be = st->beta;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
+    p[q] = first ? z[q] : fma(be, p[q], z[q]);
+}
+
+// x += alpha p, r -= alpha v (v = A p); partial sums of r.r
+__global__ void __launch_bounds__(kDotThreads) k_cg_xr(const KryState* __restrict__ st, double* __restrict__ x,
+                                                       double* __restrict__ r, const double* __restrict__ p,
+                                                       const double* __restrict__ v, long long n,
+                                                       double* __restrict__ partials) {
+  const bool live = !st->done;
+  const double al = st->alpha;
+  double s0 = 0.0, s1 = 0.0;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    if (live) {
+      x[q] = fma(al, p[q], x[q]);
+      const double rq = fma(-al, v[q], r[q]);
+      r[q] = rq;
+      s0 = fma(rq, rq, s0);
+    }
+  }
+  block_reduce2(s0, s1);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = s0;
+    partials[2 * blockIdx.x + 1] = s1;
+  }
 }
 
 __global__ void k_zero(double* __restrict__ a, long long n) {
@@ -558,6 +657,15 @@ fdi_status cmatvec(fdi_plan* p, const MacGeom& g, double lambda, double* q, doub
   return FDI_OK;
 }
 
+fdi_status wdots(fdi_plan* p, const MacGeom& g, const double* a, const double* b, int kind, cudaStream_t s) {
+  FDI_KTIMER(p, "stokes_dot", s);
+  k_wdot<<<kDotBlocks, kDotThreads, 0, s>>>(g, a, b, p->kpartials);
+  FDI_LAUNCH_CHECK(p);
+  k_kry_finish<<<1, kDotThreads, 0, s>>>(p->kpartials, p->d_kry, kind);
+  FDI_LAUNCH_CHECK(p);
+  return FDI_OK;
+}
+
 fdi_status dots(fdi_plan* p, const double* a, const double* b, const double* c, const double* d, long long n,
                 int kind, cudaStream_t s) {
   FDI_KTIMER(p, "stokes_dot", s);
@@ -646,7 +754,31 @@ fdi_status stokes_solve(fdi_plan* p, double dt, double Re, const double* const f
     }
     return FDI_OK;
   };
-  if (p->krylov == 1) {
+  if (p->krylov == 2) {
+    // conjugate gradients on (-C) y = b (y = -q) in the volume-weighted inner
+    // product, preconditioned by precond() = -L_p^{-1} (+ lambda I); x = y, r,
+    // z = preconditioned residual, pv = search direction, v = -C pv
+    FDI_TRY(dots(p, b, b, nullptr, nullptr, Pc, KF_INIT, s));
+    auto iteration = [&](int first) -> fdi_status {
+      FDI_TRY(precond(r, z));
+      FDI_TRY(wdots(p, g, r, z, KF_CG_RHO, s));
+      k_cg_p<<<vb, vt, 0, s>>>(p->d_kry, pv, z, Pc, first);
+      FDI_LAUNCH_CHECK(p);
+      FDI_TRY(cmatvec(p, g, lambda, pv, v, s));
+      FDI_TRY(wdots(p, g, pv, v, KF_CG_ALPHA, s));
+      {
+        FDI_KTIMER(p, "stokes_update", s);
+        k_cg_xr<<<kDotBlocks, kDotThreads, 0, s>>>(p->d_kry, x, r, pv, v, Pc, p->kpartials);
+        FDI_LAUNCH_CHECK(p);
+        k_kry_finish<<<1, kDotThreads, 0, s>>>(p->kpartials, p->d_kry, KF_CG_ITER);
+        FDI_LAUNCH_CHECK(p);
+      }
+      return FDI_OK;
+    };
+    FDI_TRY(run_loop(iteration));
+    k_negate<<<vb, vt, 0, s>>>(x, Pc);  // q = -y
+    FDI_LAUNCH_CHECK(p);
+  } else if (p->krylov == 1) {
     // BiCGstab(2) (Sleijpen & Fokkema; the paper's solver, Sec. 2) on
     // (C M^{-1}) y = b; q = M^{-1} y at the end.  Vectors: x = y, r = r_0,
     // pv = u_0, v = u_1, sv = u_2, t = r_1, y = r_2, z = work.
@@ -770,7 +902,7 @@ extern "C" fdi_status fdi_stokes_solve(fdi_plan* plan, double dt, double Re, con
 }
 
 extern "C" fdi_status fdi_plan_set_krylov(fdi_plan* plan, int method) {
-  if (!plan || (method != 0 && method != 1)) return FDI_ERR_INVALID_ARG;
+  if (!plan || method < 0 || method > 2) return FDI_ERR_INVALID_ARG;
   plan->krylov = method;
   return FDI_OK;
 }

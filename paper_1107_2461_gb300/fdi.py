@@ -299,7 +299,8 @@ def apply_transform(plan: Plan, field, d, inverse, inp, out, rows, stream=None):
 
 
 def set_krylov(plan: Plan, method: int):
-    """0: BiCGstab, 1: BiCGstab(2) (the paper's solver) for the Stokes pressure system."""
+    """0: BiCGstab, 1: BiCGstab(2) (the paper's solver), 2: conjugate gradients in
+    the volume-weighted inner product, for the Stokes pressure system."""
     _check(load().fdi_plan_set_krylov(plan.handle, int(method)), "fdi_plan_set_krylov")
 
 

@@ -197,3 +197,91 @@ def test_semi_direct_bicgstab2_matches_direct(dt, precond):
     for c in range(3):
         assert np.abs(v[c] - vd[c]).max() <= 1e-10 * np.abs(vd[c]).max()
     assert np.abs(p - pd).max() <= 1e-9 * np.abs(pd).max()
+
+
+def _weighted_spd(n, seed):
+    # A = W^{-1} S with S symmetric positive definite: self-adjoint and positive
+    # definite in the inner product weighted by W
+    rng = np.random.default_rng(seed)
+    w = rng.uniform(0.2, 3.0, n)
+    X = rng.standard_normal((n, n))
+    S = X @ X.T + n * np.eye(n)
+    return w, S / w[:, None]
+
+
+def test_pcg_solves_weighted_spd_system():
+    # against the dense solve, with and without a (weighted-SPD) preconditioner
+    w, A = _weighted_spd(40, 3)
+    b = np.random.default_rng(4).standard_normal(40)
+    ref = np.linalg.solve(A, b)
+    d = np.diag(A)
+    for B in (lambda v: v, lambda v: v / d):
+        x, it, rel = st.pcg(lambda v: A @ v, B, b, w, 1e-13, 200)
+        assert rel <= 1e-13 and it <= 40
+        assert np.abs(x - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_pcg_exact_preconditioner_converges_in_one_step():
+    w, A = _weighted_spd(25, 5)
+    Ainv = np.linalg.inv(A)
+    b = np.random.default_rng(6).standard_normal(25)
+    x, it, rel = st.pcg(lambda v: A @ v, lambda v: Ainv @ v, b, w, 1e-12, 10)
+    assert it == 1 and rel <= 1e-12
+
+
+def test_pcg_energy_error_decreases_and_terminates():
+    # CG minimises the A-norm of the error over the Krylov space in the weighted
+    # inner product: that norm never increases, and with n distinct eigenvalues the
+    # iteration ends within n steps (up to rounding)
+    n = 12
+    w, A = _weighted_spd(n, 7)
+    b = np.random.default_rng(8).standard_normal(n)
+    ref = np.linalg.solve(A, b)
+    errs = []
+    for k in range(1, n + 1):
+        x, _, _ = st.pcg(lambda v: A @ v, lambda v: v, b, w, 0.0, k)
+        e = x - ref
+        errs.append(float(np.sum(w * e * (A @ e))))
+    errs = np.array(errs)
+    assert np.all(errs[1:] <= errs[:-1] * (1 + 1e-9))
+    assert errs[-1] <= 1e-20 * float(np.sum(w * ref * (A @ ref)))
+    # the Euclidean inner product is the wrong one for this A: its iterates lose
+    # the monotone energy error or fail to terminate in n steps
+    bad = []
+    for k in range(1, n + 1):
+        x, _, _ = st.pcg(lambda v: A @ v, lambda v: v, b, np.ones(n), 0.0, k)
+        e = x - ref
+        bad.append(float(np.sum(w * e * (A @ e))))
+    bad = np.array(bad)
+    assert bad[-1] > 1e3 * errs[-1] or np.any(bad[1:] > bad[:-1] * (1 + 1e-9))
+
+
+@pytest.mark.parametrize("dt", [1e-2, 1.0, 1e3])
+@pytest.mark.parametrize("precond", ["laplace", "cahouet-chabard"])
+def test_semi_direct_cg_matches_direct(dt, precond):
+    # -C is self-adjoint positive definite on zero-mean pressures in the
+    # volume-weighted inner product, so CG applies to the pressure system
+    faces = [tanh_faces(6, 1.5), tanh_faces(7, 1.5), tanh_faces(8, 2.0)]
+    vs, ps = st.shapes(faces)
+    f = [rhs_gaussian(vs[c], 20 + c) for c in range(3)]
+    vd, pd = st.stokes_direct(faces, dt, 1000.0, f)
+    v, p, it, rel = st.stokes_semi_direct(faces, dt, 1000.0, f, tol=1e-12, precond=precond, krylov="cg")
+    assert rel <= 1e-12
+    for c in range(3):
+        assert np.abs(v[c] - vd[c]).max() <= 1e-10 * np.abs(vd[c]).max()
+    assert np.abs(p - pd).max() <= 1e-9 * np.abs(pd).max()
+
+
+def test_cg_with_exact_pressure_inverse_takes_one_step():
+    # preconditioned by the exact inverse of -C on zero-mean pressures (dense
+    # pseudo-inverse), CG ends after one step: pins the sign conventions
+    faces = _faces()
+    dt, Re = 0.5, 10.0
+    C = st.pressure_matrix(faces, dt, Re)
+    vol = asm.volumes(st.pressure_ops(faces))
+    P = np.eye(len(vol)) - np.outer(np.ones(len(vol)), vol) / vol.sum()  # zero-mean projector
+    Cp = np.linalg.pinv(-C @ P) @ P
+    b = np.random.default_rng(13).standard_normal(len(vol))
+    b -= np.dot(vol, b) / vol.sum()
+    x, it, rel = st.pcg(lambda v: -C @ v, lambda v: P @ (Cp @ v), -b, vol, 1e-10, 5)
+    assert it == 1 and rel <= 1e-10
