@@ -201,9 +201,11 @@ def tensor_flops(name, n):
     return 6.0 * P * n[d] if name.endswith("_tc") else None
 
 
-def run_arm(fdi, torch, prec, n, K, W, dev, rank, stream, cluster=None, thomas_axis=2):
+def run_arm(fdi, torch, prec, n, K, W, dev, rank, stream, cluster=None, thomas_axis=2, refine_tol=None):
     faces = workloads.box_faces(n, BETA)
     plan = fdi.plan_create(faces, n, prec=prec, thomas_axis=thomas_axis)
+    if refine_tol is not None:
+        plan.set_tolerances(refine_tol, 3)
     if cluster is not None and prec != fdi.PREC_FP64:
         fdi.set_transform_config(plan, cluster)
     f = workloads.rhs_uniform(n[::-1], rank)
@@ -387,6 +389,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--arms", default="fp64,mixed")
     ap.add_argument("--no-tpf", action="store_true", help="skip the FP64 TPF arm")
+    ap.add_argument("--no-fp64tol", action="store_true", help="skip the mixed arm refined to 1e-11")
     ap.add_argument("--cluster", type=int, default=None, help="tensor-core transform cluster size (1, 2, 4)")
     ap.add_argument("--stokes-n", type=int, default=64, help="Stokes latency grid (0: skip)")
     ap.add_argument("--stokes-reps", type=int, default=10)
@@ -440,13 +443,18 @@ def main():
     arms = {}
     precs = {"fp64": (fdi.PREC_FP64, 1e-11), "mixed": (fdi.PREC_MIXED_F16, 1e-10)}
     # the TPF variant (eigen transforms in all three directions, Eq. 29) runs on the FP64 path
+    # mixed_fp64tol: the mixed path refined to the FP64 path's tolerance
     helm_arms = {"fp64": (fdi.PREC_FP64, 1e-11, 2), "mixed": (fdi.PREC_MIXED_F16, 1e-10, 2),
-                 "fp64_tpf": (fdi.PREC_FP64, 1e-11, -1)}
-    for name in args.arms.split(",") + ([] if args.no_tpf else ["fp64_tpf"]):
+                 "fp64_tpf": (fdi.PREC_FP64, 1e-11, -1), "mixed_fp64tol": (fdi.PREC_MIXED_F16, 1e-11, 2)}
+    helm_names = args.arms.split(",") + ([] if args.no_tpf else ["fp64_tpf"])
+    if "mixed" in helm_names and not args.no_fp64tol:
+        helm_names.append("mixed_fp64tol")
+    for name in helm_names:
         prec, tol, taxis = helm_arms[name]
         try:
             arms[name] = run_arm(fdi, torch, prec, n, K if taxis == 2 else max(3, K // 10), W, dev, rank, stream,
-                                 args.cluster, thomas_axis=taxis)
+                                 args.cluster, thomas_axis=taxis,
+                                 refine_tol=tol if name == "mixed_fp64tol" else None)
             if taxis != 2:
                 arms[name]["K"] = max(3, K // 10)
             arms[name]["tol"] = tol

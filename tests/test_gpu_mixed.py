@@ -189,3 +189,29 @@ def test_clustered_mixed_solve(fdi, cluster):
     plan.destroy()
     assert st == 0 and rel <= MIXED_TOL
     assert asm.relative_residual(ops, out.cpu().numpy(), f, 1.0) <= MIXED_TOL
+
+
+def test_mixed_refined_to_fp64_tolerance(fdi):
+    # the mixed path with one more refinement step reaches the FP64 path's
+    # tolerance (1e-11): 128^3, tanh 2.0, the three Helmholtz lambdas and the
+    # zero-flux Laplacian, residuals recomputed with the oracle's operator
+    import torch
+    n = (128, 128, 128)
+    faces = box_faces(n, 2.0)
+    cases = [((D, D, D), lam, 1.0, s) for s, lam in enumerate([1e-5, 1e-3, 1.0])] + [((N, N, N), 1.0, 0.0, 3)]
+    for bc, lam, sigma, seed in cases:
+        ops = asm.cell_ops(faces, bc, bc)
+        f = rhs_uniform(n[::-1], seed)
+        plan = fdi.plan_create(faces, n, bc, bc, prec=fdi.PREC_MIXED_F16)
+        try:
+            plan.set_tolerances(1e-11, 3)
+            rhs = torch.from_numpy(f).cuda()
+            out = torch.empty_like(rhs)
+            fdi.field_solve(plan, fdi.FIELD_CELL, sigma, lam, rhs, out)
+            torch.cuda.synchronize()
+            it, steps, rel, st = fdi.last_result(plan)
+        finally:
+            plan.destroy()
+        got = out.cpu().numpy()
+        assert st == 0 and rel <= 1e-11, (lam, sigma, steps, rel)
+        assert asm.relative_residual(ops, got, f, lam, sigma) <= 1e-11
