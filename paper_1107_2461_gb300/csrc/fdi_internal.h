@@ -166,6 +166,8 @@ struct fdi_plan {
   int kgraph_krylov = -1;
   cudaStream_t kgraph_stream = nullptr;
   long long kgraph_launches = 0;
+  long long kgraph_body_launches = 0;  // launches of one pass of the device-side Krylov loop
+  long long kloop_body_launches = 0;   // the same for the last solve (0: no device-side loop)
   // optional per-kernel device timing (CUDA events around each launch)
   bool timing = false;
   struct TimedLaunch { const char* name; cudaEvent_t e0, e1; };
@@ -181,6 +183,7 @@ namespace fdi {
 void set_error(const std::string& msg);
 fdi_status solve_status(const fdi_plan* plan, const DevStatus& st, int kerr);
 void free_host_staging(fdi_plan* p);
+long long stokes_loop_launches(const fdi_plan* p);
 #define FDI_CUDA_TRY(expr)                                                      \
   do {                                                                          \
     cudaError_t _e = (expr);                                                    \

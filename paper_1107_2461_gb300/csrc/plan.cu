@@ -556,7 +556,7 @@ fdi_status fdi_plan_reset_kernel_times(fdi_plan* plan) {
 
 fdi_status fdi_last_launch_count(const fdi_plan* plan, long long* launches) {
   if (!plan || !launches) return FDI_ERR_INVALID_ARG;
-  *launches = plan->launches;
+  *launches = plan->launches + fdi::stokes_loop_launches(plan);
   return FDI_OK;
 }
 

@@ -165,6 +165,7 @@ fdi_status field_solve_entry(fdi_plan* p, int field, double sigma, double lambda
                              cudaStream_t s) {
   if (!p) return FDI_ERR_INVALID_ARG;
   p->launches = 0;
+  p->kloop_body_launches = 0;
   if (!p->use_graphs || p->timing || s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread)
     return field_solve(p, field, sigma, lambda, rhs, out, s);
   fdi_plan::GraphKey key;

@@ -20,8 +20,11 @@
 // preconditioners -L_p^{-1} and -L_p^{-1} + lambda I are positive definite on
 // zero-mean pressures, and CG needs one C-product per iteration.
 // The Krylov scalars, dot products and vector updates stay on the device in
-// FP64 (deterministic two-stage reductions); the host reads one convergence
-// flag per iteration.  The pressure is returned with zero volume-weighted mean.
+// FP64 (deterministic two-stage reductions).  On a capturable stream the
+// iterations after the first run as one CUDA graph whose WHILE node repeats a
+// captured iteration until the device-side convergence flag is set (no host
+// round trip per iteration); eagerly the host reads the flag after every
+// iteration.  The pressure is returned with zero volume-weighted mean.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -39,6 +42,7 @@ struct KryState {
   // BiCGstab(2): beta, the MGS coefficient tau_12, sigma_1, sigma_2 and the
   // polynomial coefficients gamma'_1, gamma'_2, gamma_1, gamma_2, gamma''_1
   double beta, tau12, sigma1, sigma2, gp1, gp2, g1, g2, gpp1;
+  int loops;  // iterations run by the device-side loop of a captured solve
 };
 
 namespace {
@@ -557,6 +561,23 @@ __global__ void k_kry_setup(KryState* st, double tol, int maxit) {
   st->done = 0;
   st->error = 0;
   st->iters = 0;
+  st->loops = 0;
+}
+
+// Device-side Krylov loop of a captured solve: a WHILE graph node runs one
+// iteration per pass while its condition is set.  k_loop_init sets it before
+// the node from the state after the first (eager) iteration; k_loop_cond, the
+// last node of every pass, sets it again.  Every pass runs k_loop_cond, and
+// the pass count is capped by the iteration limit independently of the done
+// flag, so the loop ends after at most maxit passes.
+__global__ void k_loop_init(KryState* st, cudaGraphConditionalHandle h) {
+  st->loops = 0;
+  cudaGraphSetConditional(h, (st->done == 0 && st->maxit > 1) ? 1u : 0u);
+}
+
+__global__ void k_loop_cond(KryState* st, cudaGraphConditionalHandle h) {
+  st->loops += 1;
+  cudaGraphSetConditional(h, (st->done == 0 && st->loops + 1 < st->maxit) ? 1u : 0u);
 }
 
 #define FDI_TRY(expr)            \
@@ -704,45 +725,116 @@ fdi_status stokes_solve(fdi_plan* p, double dt, double Re, const double* const f
   // identical); the legacy stream and timed plans run eagerly.
   const bool graphs = p->use_graphs && !p->timing && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
   auto run_loop = [&](auto&& iteration) -> fdi_status {
-    for (int it = 0; it < p->kmaxit; ++it) {
-      if (it == 0 || !graphs) {
+    p->kloop_body_launches = 0;
+    if (!graphs) {
+      // eager: one iteration at a time, the host reads the convergence flag
+      for (int it = 0; it < p->kmaxit; ++it) {
         FDI_TRY(iteration(it == 0 ? 1 : 0));
-      } else {
-        if (!p->kgraph || p->kgraph_lambda != lambda || p->kgraph_precond != p->stokes_precond ||
-            p->kgraph_krylov != p->krylov || p->kgraph_stream != s) {
-          if (p->kgraph) cudaGraphExecDestroy(p->kgraph);
-          p->kgraph = nullptr;
-          const long long before = p->launches;
-          FDI_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-          fdi_status st = iteration(0);
-          cudaGraph_t gr = nullptr;
-          cudaError_t e = cudaStreamEndCapture(s, &gr);
-          if (st != FDI_OK || e != cudaSuccess || gr == nullptr) {
-            if (gr) cudaGraphDestroy(gr);
-            if (st != FDI_OK) return st;
-            FDI_CUDA_TRY(e);
-            set_error("stream capture of the Krylov iteration failed");
-            return FDI_ERR_CUDA;
-          }
-          cudaGraphExec_t ex = nullptr;
-          e = cudaGraphInstantiate(&ex, gr, 0);
-          cudaGraphDestroy(gr);
-          FDI_CUDA_TRY(e);
-          p->kgraph = ex;
-          p->kgraph_lambda = lambda;
-          p->kgraph_precond = p->stokes_precond;
-          p->kgraph_krylov = p->krylov;
-          p->kgraph_stream = s;
-          p->kgraph_launches = p->launches - before;
-          p->launches = before;
-        }
-        FDI_CUDA_TRY(cudaGraphLaunch(p->kgraph, s));
-        p->launches += p->kgraph_launches;
+        FDI_CUDA_TRY(cudaMemcpyAsync(p->h_flag, &p->d_kry->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FDI_CUDA_TRY(cudaStreamSynchronize(s));
+        if (*p->h_flag) break;
       }
-      FDI_CUDA_TRY(cudaMemcpyAsync(p->h_flag, &p->d_kry->done, sizeof(int), cudaMemcpyDeviceToHost, s));
-      FDI_CUDA_TRY(cudaStreamSynchronize(s));
-      if (*p->h_flag) break;
+      return FDI_OK;
     }
+    // the first iteration eagerly, the rest as one graph: a WHILE node whose
+    // body is one iteration, so the loop runs on the device without a host
+    // round trip per iteration
+    FDI_TRY(iteration(1));
+    if (!p->kgraph || p->kgraph_lambda != lambda || p->kgraph_precond != p->stokes_precond ||
+        p->kgraph_krylov != p->krylov || p->kgraph_stream != s) {
+      if (p->kgraph) cudaGraphExecDestroy(p->kgraph);
+      p->kgraph = nullptr;
+      const long long before = p->launches;
+      cudaGraph_t gr = nullptr, body = nullptr;
+      cudaGraphConditionalHandle h = 0;
+      fdi_status st = FDI_OK;
+      FDI_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaGraph_t g = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd);
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess) {
+          k_loop_init<<<1, 1, 0, s>>>(p->d_kry, h);
+          e = cudaGetLastError();
+          p->launches++;
+        }
+        if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd);
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &cp);
+        if (e == cudaSuccess)
+          e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e == cudaSuccess) {
+          body = cp.conditional.phGraph_out[0];
+        } else {
+          set_error(std::string("Krylov loop node: ") + cudaGetErrorString(e));
+          st = FDI_ERR_CUDA;
+        }
+      }
+      cudaError_t e = cudaStreamEndCapture(s, &gr);
+      if (st != FDI_OK || e != cudaSuccess || gr == nullptr) {
+        if (gr) cudaGraphDestroy(gr);
+        cudaGetLastError();
+        if (st != FDI_OK) return st;
+        FDI_CUDA_TRY(e);
+        set_error("stream capture of the Krylov loop failed");
+        return FDI_ERR_CUDA;
+      }
+      // the loop body: one iteration, then the loop condition
+      const long long body_start = p->launches;
+      e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        st = iteration(0);
+        if (st == FDI_OK) {
+          k_loop_cond<<<1, 1, 0, s>>>(p->d_kry, h);
+          p->launches++;
+          if (cudaGetLastError() != cudaSuccess) st = FDI_ERR_CUDA;
+        }
+        cudaGraph_t bg = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(s, &bg);
+        if (st == FDI_OK && e2 != cudaSuccess) {
+          set_error(std::string("stream capture of the Krylov iteration: ") + cudaGetErrorString(e2));
+          st = FDI_ERR_CUDA;
+        }
+      } else {
+        set_error(std::string("stream capture of the Krylov iteration: ") + cudaGetErrorString(e));
+        st = FDI_ERR_CUDA;
+      }
+      const long long body_launches = p->launches - body_start;
+      cudaGraphExec_t ex = nullptr;
+      if (st == FDI_OK) {
+        e = cudaGraphInstantiate(&ex, gr, 0);
+        if (e != cudaSuccess) {
+          set_error(std::string("Krylov loop graph: ") + cudaGetErrorString(e));
+          st = FDI_ERR_CUDA;
+        }
+      }
+      cudaGraphDestroy(gr);
+      if (st != FDI_OK) {
+        cudaGetLastError();
+        return st;
+      }
+      p->kgraph = ex;
+      p->kgraph_lambda = lambda;
+      p->kgraph_precond = p->stokes_precond;
+      p->kgraph_krylov = p->krylov;
+      p->kgraph_stream = s;
+      p->kgraph_launches = p->launches - before;
+      p->kgraph_body_launches = body_launches;
+      p->launches = before;
+    }
+    FDI_CUDA_TRY(cudaGraphLaunch(p->kgraph, s));
+    // the loop init launch; the body's launches are counted once the number of
+    // passes is known (fdi_last_launch_count)
+    p->launches += p->kgraph_launches - p->kgraph_body_launches;
+    p->kloop_body_launches = p->kgraph_body_launches;
     return FDI_OK;
   };
   // -(M^{-1} v) into `out`: the Laplace solve returns -L_p^{-1} v; mode 1 adds lambda v
@@ -880,6 +972,15 @@ fdi_status stokes_solve(fdi_plan* p, double dt, double Re, const double* const f
   return FDI_OK;
 }
 
+// launches run by the device-side Krylov loop of the last Stokes solve (its
+// pass count is read from the device)
+long long stokes_loop_launches(const fdi_plan* p) {
+  if (!p || p->kloop_body_launches == 0 || !p->d_kry) return 0;
+  int loops = 0;
+  if (cudaMemcpy(&loops, &p->d_kry->loops, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+  return (long long)loops * p->kloop_body_launches;
+}
+
 }  // namespace fdi
 
 using namespace fdi;
@@ -898,6 +999,7 @@ extern "C" fdi_status fdi_stokes_solve(fdi_plan* plan, double dt, double Re, con
   for (int c = 0; c < 3; ++c)
     if (!f[c] || !u[c]) return FDI_ERR_INVALID_ARG;
   plan->launches = 0;
+  plan->kloop_body_launches = 0;
   return stokes_solve(plan, dt, Re, f, u, p, (cudaStream_t)stream);
 }
 
