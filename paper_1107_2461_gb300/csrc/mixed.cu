@@ -78,6 +78,7 @@ struct ResidArgs {
   float* r;             // FP32 residual (the next solve's input)
   float* r_lo;          // MODE 0: low plane of r_1
   int r_pitch;
+  int zchunk;           // planes per block (resid_grid)
   double* out;          // FP64 solution output (null: not written)
   float* rmax;          // atomic max |r|
   const DevStatus* st;
@@ -108,7 +109,7 @@ __device__ __forceinline__ df::F2 ld2(const float2* p) {
 // FP32 (it is 2^-24 smaller).  b and -sigma x enter the same accumulator, and
 // the FP32 residual is its rounded value: r is stored in FP32, so only the
 // cancellation inside the sum needs the extra precision.
-constexpr int kResTX = 32, kResTY = 8, kResZChunk = 16;
+constexpr int kResTX = 32, kResTY = 8, kResZChunk = 16;  // planes per block (at most)
 
 struct Acc {
   float h, l;  // unnormalised double-float accumulator
@@ -159,7 +160,7 @@ __device__ __forceinline__ void resid_body(const ResidArgs& a, double* sh) {
   const long long sy = nx, sz = (long long)nx * ny;
   const int lane = threadIdx.x, wy = threadIdx.y;
   const int i = blockIdx.x * kResTX + lane, j = blockIdx.y * kResTY + wy;
-  const int k0 = blockIdx.z * kResZChunk, k1 = min(nz, k0 + kResZChunk);
+  const int k0 = blockIdx.z * a.zchunk, k1 = min(nz, k0 + a.zchunk);
   const bool act = i < nx && j < ny;
   const int ic = min(i, nx - 1), jc = min(j, ny - 1);
   float mean_h = 0.f, mean_l = 0.f;
@@ -537,9 +538,19 @@ __global__ void k_scale_weights(const float2* __restrict__ wp0, const float2* __
   }
 }
 
-dim3 resid_grid(int nx, int ny, int nz) {
+// Residual grid: 32 x 8 columns per block, `zchunk` planes marched per block.
+// Long marches amortise the loads of the planes above and below; grids with
+// fewer blocks than SMs halve the march (down to 4 planes) until every SM has
+// a block.  (Filling the SMs several times over made a lone small solve a
+// little faster but concurrent small solves slower.)  The order of the
+// reduction is fixed by the grid, which depends on the shape only.
+dim3 resid_grid(int nx, int ny, int nz, int* zchunk) {
+  const long long cols = (long long)((nx + kResTX - 1) / kResTX) * ((ny + kResTY - 1) / kResTY);
+  int zc = kResZChunk;
+  while (zc > 4 && cols * ((nz + zc - 1) / zc) < 152) zc /= 2;
+  *zchunk = zc;
   return dim3((unsigned)((nx + kResTX - 1) / kResTX), (unsigned)((ny + kResTY - 1) / kResTY),
-              (unsigned)((nz + kResZChunk - 1) / kResZChunk));
+              (unsigned)((nz + zc - 1) / zc));
 }
 
 // kind 0: initial pass (b only): record the volume-weighted mean if asked
@@ -1102,7 +1113,8 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
   float* r1l = p->wr1 + p->wr1_plane;
   const int* done = &p->d_status->done;
 
-  const dim3 rgrid = resid_grid(nx, ny, nz);
+  int zchunk = kResZChunk;
+  const dim3 rgrid = resid_grid(nx, ny, nz, &zchunk);
   const int rblocks = (int)(rgrid.x * rgrid.y * rgrid.z);
   if (rblocks > p->npartials) {
     set_error("grid too large for the reduction buffer");
@@ -1132,6 +1144,7 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
   ra.b = b;
   ra.r = r;
   ra.r_pitch = px;
+  ra.zchunk = zchunk;
   ra.st = p->d_status;
   ra.partials = p->partials;
 
@@ -1149,8 +1162,8 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     a0.fin = FinishArgs{p->d_counter, p->partials, p->d_status, p->tol, 0, singular ? 1 : 0};
     if (px == nx && !singular && (reinterpret_cast<uintptr_t>(b) & 15u) == 0)
       FDI_CUDA_TRY(launch_pdl(true, k_init_rhs_flat, dim3(iblocks), dim3(256), 0, s, a0, f.P));
-    else
-      FDI_CUDA_TRY(launch_pdl(true, k_init_rhs, dim3(iblocks), dim3(256), 0, s, a0));
+    else  // one warp per x-line: no more blocks than lines / 8
+      FDI_CUDA_TRY(launch_pdl(true, k_init_rhs, dim3(std::min(iblocks, (ny * nz + 7) / 8)), dim3(256), 0, s, a0));
     FDI_LAUNCH_CHECK(p);
   }
 
