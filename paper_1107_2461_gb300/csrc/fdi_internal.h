@@ -131,6 +131,10 @@ struct fdi_plan {
   // afterwards (a small LRU set, so alternating buffers keep their graphs)
   bool use_graphs = true;
   bool pdl = true;                  // programmatic dependent launch between the mixed solve's kernels
+  // mixed field solves run one direct solve only (no residual check, no
+  // refinement; FP64 output of the first solve): set around preconditioner
+  // applications, which need no more than an approximate inverse
+  bool single_pass = false;
   struct GraphKey {
     int field = -1;
     double sigma = 0.0, lambda = 0.0;

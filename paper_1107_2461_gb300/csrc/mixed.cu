@@ -1097,6 +1097,7 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     b = p->ws[4];
   }
   const bool singular = sigma == 0.0 && f.zero_flux_all;
+  const bool one_pass = p->single_pass;
   float* r = p->wf[0];
   float* F1 = p->wf[1];
   float* F2 = p->wf[2];
@@ -1324,7 +1325,7 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
                                 s));
     // residual and convergence check: r_1 = b - A H after the first solve,
     // r = r_1 - A L after each correction (which also writes the FP64 solution)
-    {
+    if (!one_pass) {
       FDI_KTIMER(p, round == 0 ? "residual_df" : "residual_corr", s);
       ResidArgs ak = ra;
       ak.xh = xH;
@@ -1352,7 +1353,7 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaGraph_t cgraph = nullptr;
   bool conditional = false;
-  if (p->max_refine >= 2 && p->cstream &&
+  if (!one_pass && p->max_refine >= 2 && p->cstream &&
       cudaStreamGetCaptureInfo(s, &cap, nullptr, &cgraph, nullptr, nullptr, nullptr) == cudaSuccess &&
       cap == cudaStreamCaptureStatusActive && cgraph) {
     // add an IF node after the current capture point of `st` (capturing into
@@ -1395,7 +1396,7 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
       body = next_body;
     }
   } else {
-    for (int round = 0; round <= p->max_refine; ++round) FDI_TRY(enqueue_round(round, s, 0));
+    for (int round = 0; round <= (one_pass ? 0 : p->max_refine); ++round) FDI_TRY(enqueue_round(round, s, 0));
   }
   {
     // FP64 output when the loop stopped before its last round (and, for the
@@ -1406,9 +1407,10 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     // edge needs a kernel upstream, and this pass reads what the node's body
     // writes
     FDI_KTIMER(p, "finalize_out", s);
+    // (single pass: out = H, no refinement step and no mean removal)
     FDI_CUDA_TRY(launch_pdl(!conditional, k_finalize_out, dim3(kBlocks), dim3(kThreads), 0, s, (const float*)xH,
                             (const float*)xL, (const float*)xLL, out, f.P, (const DevStatus*)p->d_status,
-                            p->max_refine, singular ? 1 : 0));
+                            one_pass ? 1 : p->max_refine, (singular && !one_pass) ? 1 : 0));
     FDI_LAUNCH_CHECK(p);
   }
   return FDI_OK;

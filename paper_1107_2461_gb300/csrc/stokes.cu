@@ -272,13 +272,14 @@ __global__ void __launch_bounds__(kDotThreads) k_kry_finish(const double* __rest
       }
       break;
     // ---- conjugate gradients (volume-weighted inner product) ----
-    case KF_CG_RHO: {  // a = <r, z>: beta = a / rho (after the first iteration), rho = a
+    case KF_CG_RHO: {  // a = <r, z>, b = <v, z> (v = A p of the last step):
+      // Polak-Ribiere beta = <r - r_old, z> / rho_old = -alpha b / rho_old
       if (!(a > 0.0) || !isfinite(a)) {
         st->error = 2;
         st->done = 1;
         break;
       }
-      st->beta = st->iters > 0 ? a / st->rho : 0.0;
+      st->beta = st->iters > 0 ? -st->alpha * b / st->rho : 0.0;
       st->rho = a;
       break;
     }
@@ -490,9 +491,11 @@ __global__ void k_axpy(double* __restrict__ y, double c, const double* __restric
 
 // ---- conjugate gradients ----
 
-// partial sums of sum V a b over the cells (V = cell volume)
+// partial sums of sum V a b and sum V c b (c may be null) over the cells
+// (V = cell volume)
 __global__ void __launch_bounds__(kDotThreads) k_wdot(MacGeom g, const double* __restrict__ a,
-                                                      const double* __restrict__ b, double* __restrict__ partials) {
+                                                      const double* __restrict__ b, const double* __restrict__ c,
+                                                      double* __restrict__ partials) {
   const int nx = g.nx, ny = g.ny;
   const long long n = (long long)nx * ny * g.nz;
   double s0 = 0.0, s1 = 0.0;
@@ -500,7 +503,9 @@ __global__ void __launch_bounds__(kDotThreads) k_wdot(MacGeom g, const double* _
     const int i = (int)(q % nx);
     const long long t = q / nx;
     const int j = (int)(t % ny), k = (int)(t / ny);
-    s0 = fma(g.m[0][i] * g.m[1][j] * g.m[2][k], a[q] * b[q], s0);
+    const double vb = g.m[0][i] * g.m[1][j] * g.m[2][k] * b[q];
+    s0 = fma(vb, a[q], s0);
+    if (c) s1 = fma(vb, c[q], s1);
   }
   block_reduce2(s0, s1);
   if (threadIdx.x == 0) {
@@ -678,9 +683,10 @@ fdi_status cmatvec(fdi_plan* p, const MacGeom& g, double lambda, double* q, doub
   return FDI_OK;
 }
 
-fdi_status wdots(fdi_plan* p, const MacGeom& g, const double* a, const double* b, int kind, cudaStream_t s) {
+fdi_status wdots(fdi_plan* p, const MacGeom& g, const double* a, const double* b, const double* c, int kind,
+                 cudaStream_t s) {
   FDI_KTIMER(p, "stokes_dot", s);
-  k_wdot<<<kDotBlocks, kDotThreads, 0, s>>>(g, a, b, p->kpartials);
+  k_wdot<<<kDotBlocks, kDotThreads, 0, s>>>(g, a, b, c, p->kpartials);
   FDI_LAUNCH_CHECK(p);
   k_kry_finish<<<1, kDotThreads, 0, s>>>(p->kpartials, p->d_kry, kind);
   FDI_LAUNCH_CHECK(p);
@@ -838,8 +844,18 @@ fdi_status stokes_solve(fdi_plan* p, double dt, double Re, const double* const f
     return FDI_OK;
   };
   // -(M^{-1} v) into `out`: the Laplace solve returns -L_p^{-1} v; mode 1 adds lambda v
+  // The preconditioner only has to approximate C^{-1}: for CG and BiCGstab a
+  // mixed plan applies its Laplace inverse as one direct solve without
+  // refinement (CG takes the Polak-Ribiere coefficient, which tolerates the
+  // slightly varying operator; BiCGstab builds the solution from the
+  // preconditioned directions themselves).  BiCGstab(2) recovers q by one more
+  // application at the end and keeps the refined solve.
+  const bool approx_precond = p->prec != FDI_PREC_FP64 && p->krylov != 1;
   auto precond = [&](const double* vin, double* vout) -> fdi_status {
-    FDI_TRY(field_solve(p, FDI_FIELD_CELL, 0.0, 1.0, vin, vout, s));
+    p->single_pass = approx_precond;
+    const fdi_status pst = field_solve(p, FDI_FIELD_CELL, 0.0, 1.0, vin, vout, s);
+    p->single_pass = false;
+    FDI_TRY(pst);
     if (p->stokes_precond == 1) {
       k_axpy<<<vb, vt, 0, s>>>(vout, lambda, vin, Pc);
       FDI_LAUNCH_CHECK(p);
@@ -853,11 +869,11 @@ fdi_status stokes_solve(fdi_plan* p, double dt, double Re, const double* const f
     FDI_TRY(dots(p, b, b, nullptr, nullptr, Pc, KF_INIT, s));
     auto iteration = [&](int first) -> fdi_status {
       FDI_TRY(precond(r, z));
-      FDI_TRY(wdots(p, g, r, z, KF_CG_RHO, s));
+      FDI_TRY(wdots(p, g, r, z, first ? nullptr : v, KF_CG_RHO, s));
       k_cg_p<<<vb, vt, 0, s>>>(p->d_kry, pv, z, Pc, first);
       FDI_LAUNCH_CHECK(p);
       FDI_TRY(cmatvec(p, g, lambda, pv, v, s));
-      FDI_TRY(wdots(p, g, pv, v, KF_CG_ALPHA, s));
+      FDI_TRY(wdots(p, g, pv, v, nullptr, KF_CG_ALPHA, s));
       {
         FDI_KTIMER(p, "stokes_update", s);
         k_cg_xr<<<kDotBlocks, kDotThreads, 0, s>>>(p->d_kry, x, r, pv, v, Pc, p->kpartials);

@@ -214,10 +214,12 @@ def test_cg_matches_oracle(fdi, prec, tol, dt, precond):
     for c in range(3):
         assert rel(vel[c], vel_o[c]) <= 1e-7
     assert rel(p, p_o) <= 1e-6
-    # the same Krylov recurrence: iteration counts agree up to rounding effects
-    # (the paper's preconditioner alone needs many iterations at dt = 1 and
-    # stagnates at large dt, so that case is left out)
-    assert abs(it - it_o) <= max(2, it_o // 10), (it, it_o)
+    # the same Krylov method: the device applies the mixed plan's
+    # preconditioner as one unrefined direct solve, so it may take a few more
+    # iterations than the oracle with the exact preconditioner (the paper's
+    # preconditioner alone needs many iterations at dt = 1 and stagnates at
+    # large dt, so that case is left out)
+    assert it_o - 2 <= it <= it_o + max(3, it_o // 4), (it, it_o)
 
 
 def test_krylov_method_validated(fdi):
