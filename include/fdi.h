@@ -96,8 +96,15 @@ typedef enum { FDI_FIELD_CELL = 0, FDI_FIELD_U = 1, FDI_FIELD_V = 2, FDI_FIELD_W
  *   n[d]       cells per direction, 2 <= n[d] <= 256
  *   bc_lo/hi   wall type of each side of each direction (FDI_GRID_CELL only;
  *              ignored for FDI_GRID_MAC, whose walls are no-slip)
- *   thomas_axis 2: Thomas along z (TPT); -1: eigen decomposition in all three
- *              directions (TPF).  Other values: FDI_ERR_UNSUPPORTED.
+ *   thomas_axis 0, 1, 2: TPT with the Thomas sweeps along x, y or z; -2: along
+ *              the direction with the most cells (the paper's choice, Sec. 3;
+ *              ties go to z, then y); -1: eigen decomposition in all three
+ *              directions (TPF).  A cell plan with the Thomas axis x or y works
+ *              on a copy of each field with that axis outermost: every solve
+ *              permutes the right-hand side in and the solution out (two FP64
+ *              copies of the field, owned by the plan).  Staggered (MAC) plans
+ *              take 2 or -1.  Other values: FDI_ERR_UNSUPPORTED.  fdi_plan_eigen
+ *              and fdi_apply_transform take the caller's directions.
  * Synchronous.  On error *out is set to NULL. */
 fdi_status fdi_plan_create(const double* const faces[3], const int n[3], const fdi_bc bc_lo[3],
                            const fdi_bc bc_hi[3], fdi_grid grid, fdi_precision prec, int thomas_axis,

@@ -77,7 +77,14 @@ struct fdi_work_slot {
 struct fdi_plan {
   fdi_grid grid;
   fdi_precision prec;
-  int thomas_axis;
+  int thomas_axis;                  // internal: 2 (TPT along the internal z) or -1 (TPF)
+  // Thomas axis as the caller named it, and the external grid: a cell plan
+  // whose Thomas axis is x or y works on a permuted copy of its fields
+  // (internal axis d holds external axis perm[d]; see permute.cu)
+  int thomas_ext = 2;
+  int n_ext[3] = {0, 0, 0};
+  int perm[3] = {0, 1, 2};
+  double* tstage[2] = {nullptr, nullptr};  // right-hand side and solution in internal order
   int n[3];
   int device;
   std::vector<fdi::Axis*> axes;
@@ -188,6 +195,7 @@ void set_error(const std::string& msg);
 fdi_status solve_status(const fdi_plan* plan, const DevStatus& st, int kerr);
 void free_host_staging(fdi_plan* p);
 long long stokes_loop_launches(const fdi_plan* p);
+fdi_status launch_axis_permute(fdi_plan* p, const double* in, double* out, bool to_internal, cudaStream_t s);
 #define FDI_CUDA_TRY(expr)                                                      \
   do {                                                                          \
     cudaError_t _e = (expr);                                                    \

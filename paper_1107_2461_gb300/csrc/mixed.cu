@@ -1429,7 +1429,10 @@ extern "C" fdi_status fdi_apply_transform(fdi_plan* plan, fdi_field field, int d
     return FDI_ERR_UNSUPPORTED;
   }
   if (rows == 0) return FDI_OK;
-  const Axis* ax = plan->fields[(int)field].ax[d];
+  int di = d;  // internal axis holding external direction d
+  for (int q = 0; q < 3; ++q)
+    if (plan->perm[q] == d) di = q;
+  const Axis* ax = plan->fields[(int)field].ax[di];
   const MixedAxis* m = static_cast<const MixedAxis*>(ax->mixed);
   const int n = ax->n, pitch = pitch4(n);
   cudaStream_t s = (cudaStream_t)stream;

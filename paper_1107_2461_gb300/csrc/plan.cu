@@ -230,6 +230,10 @@ void free_plan(fdi_plan* p) {
   if (!p) return;
   invalidate_graph(p);
   free_host_staging(p);
+  for (double*& t : p->tstage) {
+    if (t) cudaFree(t);
+    t = nullptr;
+  }
   for (auto& t : p->pending) {
     cudaEventDestroy(t.e0);
     cudaEventDestroy(t.e1);
@@ -390,8 +394,18 @@ fdi_status fdi_plan_create(const double* const faces[3], const int n[3], const f
   if (grid != FDI_GRID_CELL && grid != FDI_GRID_MAC) return FDI_ERR_INVALID_ARG;
   if (prec < FDI_PREC_FP64 || prec > FDI_PREC_MIXED_F16) return FDI_ERR_INVALID_ARG;
   if (grid == FDI_GRID_CELL && (!bc_lo || !bc_hi)) return FDI_ERR_INVALID_ARG;
-  if (thomas_axis != 2 && thomas_axis != -1) {
-    set_error("thomas_axis must be 2 (z) or -1 (all-eigen TPF)");
+  if (thomas_axis < -2 || thomas_axis > 2) {
+    set_error("thomas_axis must be 0, 1, 2 (Thomas along x, y, z), -2 (the longest direction) or -1 (TPF)");
+    return FDI_ERR_UNSUPPORTED;
+  }
+  if (thomas_axis == -2) {
+    // the direction with the most cells (Sec. 3); ties go to z, then y
+    thomas_axis = 2;
+    if (n[1] > n[thomas_axis]) thomas_axis = 1;
+    if (n[0] > n[thomas_axis]) thomas_axis = 0;
+  }
+  if (grid == FDI_GRID_MAC && thomas_axis != 2 && thomas_axis != -1) {
+    set_error("a staggered (MAC) plan runs its Thomas sweeps along z (thomas_axis 2 or -1)");
     return FDI_ERR_UNSUPPORTED;
   }
   for (int d = 0; d < 3; ++d) {
@@ -415,8 +429,29 @@ fdi_status fdi_plan_create(const double* const faces[3], const int n[3], const f
   fdi_plan* p = new fdi_plan();
   p->grid = grid;
   p->prec = prec;
-  p->thomas_axis = thomas_axis;
-  for (int d = 0; d < 3; ++d) p->n[d] = n[d];
+  // Thomas along x or y: the plan is built on the grid with that axis moved to
+  // z (internal axis d is external axis perm[d])
+  p->thomas_ext = thomas_axis;
+  if (thomas_axis == 0) {
+    p->perm[0] = 2;
+    p->perm[2] = 0;
+  } else if (thomas_axis == 1) {
+    p->perm[1] = 2;
+    p->perm[2] = 1;
+  }
+  p->thomas_axis = thomas_axis == -1 ? -1 : 2;
+  const double* faces_i[3];
+  int n_i[3];
+  fdi_bc lo_i[3] = {FDI_BC_DIRICHLET, FDI_BC_DIRICHLET, FDI_BC_DIRICHLET};
+  fdi_bc hi_i[3] = {FDI_BC_DIRICHLET, FDI_BC_DIRICHLET, FDI_BC_DIRICHLET};
+  for (int d = 0; d < 3; ++d) {
+    faces_i[d] = faces[p->perm[d]];
+    n_i[d] = n[p->perm[d]];
+    if (bc_lo) lo_i[d] = bc_lo[p->perm[d]];
+    if (bc_hi) hi_i[d] = bc_hi[p->perm[d]];
+    p->n[d] = n_i[d];
+    p->n_ext[d] = n[d];
+  }
   if (cudaGetDevice(&p->device) != cudaSuccess) {
     delete p;
     set_error("no CUDA device");
@@ -437,7 +472,17 @@ fdi_status fdi_plan_create(const double* const faces[3], const int n[3], const f
     set_error("stream creation failed");
     return FDI_ERR_CUDA;
   }
-  fdi_status st = build_plan(p, faces, bc_lo, bc_hi, s);
+  fdi_status st = build_plan(p, faces_i, lo_i, hi_i, s);
+  if (st == FDI_OK && (thomas_axis == 0 || thomas_axis == 1)) {
+    const size_t P = (size_t)n[0] * n[1] * n[2];
+    for (double*& t : p->tstage) {
+      if (cudaMalloc(&t, P * sizeof(double)) != cudaSuccess) {
+        set_error("cudaMalloc of the permuted staging fields failed");
+        st = FDI_ERR_OUT_OF_MEMORY;
+        break;
+      }
+    }
+  }
   cudaError_t e = cudaStreamSynchronize(s);
   cudaStreamDestroy(s);
   if (st == FDI_OK && e != cudaSuccess) {
@@ -499,7 +544,10 @@ fdi_status fdi_last_result(const fdi_plan* plan, int* iters, int* refine_steps, 
 fdi_status fdi_plan_eigen(const fdi_plan* plan, fdi_field field, int d, double* lam, double* E,
                           double* Einv, int* m) {
   if (!plan || d < 0 || d > 2 || (int)field < 0 || (int)field >= plan->nfields) return FDI_ERR_INVALID_ARG;
-  const Axis* ax = plan->fields[(int)field].ax[d];
+  int di = d;  // internal axis holding external direction d
+  for (int q = 0; q < 3; ++q)
+    if (plan->perm[q] == d) di = q;
+  const Axis* ax = plan->fields[(int)field].ax[di];
   int n = ax->n;
   if (m) *m = n;
   if (lam) FDI_CUDA_TRY(cudaMemcpy(lam, ax->lam, n * 8, cudaMemcpyDeviceToHost));

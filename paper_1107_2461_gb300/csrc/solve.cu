@@ -78,10 +78,10 @@ fdi_status solve_once_f64(fdi_plan* p, const Field& f, double sigma, double lamb
 
 }  // namespace
 
-fdi_status field_solve(fdi_plan* p, int field, double sigma, double lambda, const double* rhs, double* out,
-                       cudaStream_t s) {
-  FDI_TRY(validate_field_args(p, field, sigma, lambda));
-  if (!rhs || !out) return FDI_ERR_INVALID_ARG;
+namespace {
+
+fdi_status field_solve_internal(fdi_plan* p, int field, double sigma, double lambda, const double* rhs, double* out,
+                                cudaStream_t s) {
   if (p->prec != FDI_PREC_FP64) return mixed_field_solve(p, field, sigma, lambda, rhs, out, s);
   const Field& f = p->fields[field];
   FDI_TRY(launch_reset_status(p, s));
@@ -103,6 +103,19 @@ fdi_status field_solve(fdi_plan* p, int field, double sigma, double lambda, cons
     FDI_TRY(launch_finish_residual(p, 0, false, 1, done, s));
   }
   return FDI_OK;
+}
+
+}  // namespace
+
+fdi_status field_solve(fdi_plan* p, int field, double sigma, double lambda, const double* rhs, double* out,
+                       cudaStream_t s) {
+  FDI_TRY(validate_field_args(p, field, sigma, lambda));
+  if (!rhs || !out) return FDI_ERR_INVALID_ARG;
+  if (p->tstage[0] == nullptr) return field_solve_internal(p, field, sigma, lambda, rhs, out, s);
+  // Thomas along x or y: solve on the copy with that axis outermost
+  FDI_TRY(launch_axis_permute(p, rhs, p->tstage[0], true, s));
+  FDI_TRY(field_solve_internal(p, field, sigma, lambda, p->tstage[0], p->tstage[1], s));
+  return launch_axis_permute(p, p->tstage[1], out, false, s);
 }
 
 // Autotuned transform / Thomas configurations per (grid shape, precision),

@@ -60,9 +60,13 @@ def test_invalid_arguments_rejected_without_touching_the_gpu(lib):
     with pytest.raises(fdi.FdiError) as e:
         fdi.plan_create(bad, (8, 8, 8))
     assert e.value.status == fdi.ERR_INVALID_ARG
-    # Thomas axis other than z
+    # Thomas axis out of range; a staggered plan with its Thomas axis not z
+    for axis in (3, -3):
+        with pytest.raises(fdi.FdiError) as e:
+            fdi.plan_create(faces, (8, 8, 8), thomas_axis=axis)
+        assert e.value.status == fdi.ERR_UNSUPPORTED
     with pytest.raises(fdi.FdiError) as e:
-        fdi.plan_create(faces, (8, 8, 8), thomas_axis=0)
+        fdi.plan_create(faces, (8, 8, 8), grid=fdi.GRID_MAC, thomas_axis=1)
     assert e.value.status == fdi.ERR_UNSUPPORTED
     # null plan handles
     assert lib.fdi_helmholtz_solve(None, 1.0, None, None, None) == fdi.ERR_INVALID_ARG
