@@ -214,7 +214,7 @@ def kernel_model(name, n, steps, K):
 
 def tensor_flops(name, n):
     P = float(n[0] * n[1] * n[2])
-    d = 0 if name.startswith("transform_x") else 1
+    d = {"x": 0, "y": 1, "z": 2}.get(name[len("transform_"):][:1], 1)
     return 6.0 * P * n[d] if name.endswith("_tc") else None
 
 
@@ -469,10 +469,11 @@ def main():
     for name in helm_names:
         prec, tol, taxis = helm_arms[name]
         try:
-            arms[name] = run_arm(fdi, torch, prec, n, K if taxis == 2 else max(3, K // 10), W, dev, rank, stream,
+            slow = name == "fp64_tpf"  # FP64-pipe bound: fewer solves
+            arms[name] = run_arm(fdi, torch, prec, n, max(3, K // 10) if slow else K, W, dev, rank, stream,
                                  args.cluster, thomas_axis=taxis,
                                  refine_tol=tol if name == "mixed_fp64tol" else None)
-            if taxis != 2:
+            if slow:
                 arms[name]["K"] = max(3, K // 10)
             arms[name]["tol"] = tol
             arms[name]["prec"] = prec
