@@ -50,16 +50,33 @@ def _compile(src: str, verbose: bool) -> str:
     return obj
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    """Compile every CUDA source and link libfdi.so; returns the library path."""
-    os.makedirs(BUILD, exist_ok=True)
-    srcs = sources()
-    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+def _up_to_date(srcs) -> bool:
+    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     deps.append(os.path.join(ROOT, "include", "fdi.h"))
-    if not force and os.path.exists(LIB):
-        lib_t = os.path.getmtime(LIB)
-        if all(os.path.getmtime(d) <= lib_t for d in deps):
-            return LIB
+    if not os.path.exists(LIB):
+        return False
+    lib_t = os.path.getmtime(LIB)
+    return all(os.path.getmtime(d) <= lib_t for d in deps)
+
+
+def build(verbose: bool = False, force: bool = False) -> str:
+    """Compile every CUDA source and link libfdi.so; returns the library path.
+    Processes that build at the same time (one per rank) take turns on a lock
+    file; the later ones find the library up to date."""
+    import fcntl
+    os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(verbose, force)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(verbose: bool, force: bool) -> str:
+    srcs = sources()
+    if not force and _up_to_date(srcs):
+        return LIB
     workers = min(len(srcs), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
