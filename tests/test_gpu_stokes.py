@@ -231,3 +231,37 @@ def test_krylov_method_validated(fdi):
                 fdi.set_krylov(plan, bad)
     finally:
         plan.destroy()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (3, 1e-7)])
+def test_newton_client_on_the_library(fdi, prec, tol):
+    # the time-stepper Newton solver (Sec. 2, Eq. 10-17) driving the library's
+    # Stokes inverse reaches the steady state the same solver finds with the
+    # oracle's direct Stokes solve
+    import torch
+    from paper_1107_2461_gb300.newton import TimeStepperNewton, library_stokes_inverse
+    faces = [tanh_faces(8, 1.5), tanh_faces(7, 1.5), tanh_faces(6, 2.0)]
+    dt, Re, gamma = 5.0, 50.0, 0.3
+    vs, ps = st.shapes(faces)
+    f = [rhs_gaussian(vs[c], 60 + c) for c in range(3)]
+    N = lambda u: [-gamma * x * x for x in u]  # noqa: E731
+    N_U = lambda u, v: [-2.0 * gamma * x * y for x, y in zip(u, v)]  # noqa: E731
+
+    def oracle_stokes(g):
+        vel, p = st.stokes_direct(faces, dt, Re, [np.asarray(x) for x in g])
+        return [np.asarray(v) for v in vel], p
+
+    ref = TimeStepperNewton(oracle_stokes, dt, N, N_U, f).solve([np.zeros(s) for s in vs], tol=1e-12,
+                                                                krylov_tol=1e-6)
+    plan = fdi.plan_create(faces, (8, 7, 6), grid=fdi.GRID_MAC, prec=prec)
+    try:
+        ft = [torch.from_numpy(x).cuda() for x in f]
+        res = TimeStepperNewton(library_stokes_inverse(plan, dt, Re), dt, N, N_U, ft).solve(
+            [torch.zeros_like(x) for x in ft], tol=tol, krylov_tol=1e-6)
+    finally:
+        plan.destroy()
+    assert ref.converged and res.converged, (ref.residuals, res.residuals)
+    assert res.iterations <= ref.iterations + 2
+    for c in range(3):
+        got = res.u[c].cpu().numpy()
+        assert np.abs(got - ref.u[c]).max() <= 100 * tol * np.abs(ref.u[c]).max()
