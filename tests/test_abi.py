@@ -73,3 +73,20 @@ def test_invalid_arguments_rejected_without_touching_the_gpu(lib):
     assert lib.fdi_plan_destroy(None) == fdi.ERR_INVALID_ARG
     assert lib.fdi_last_result(None, None, None, None) == fdi.ERR_INVALID_ARG
     assert lib.fdi_helmholtz_solve_batched(None, None, None, None, -1, None) == fdi.ERR_INVALID_ARG
+
+
+def test_stokes_plan_bytes_estimate_scales_with_the_grid(lib):
+    # host-only sizing used by the serving runtime's admission: grows with the
+    # number of cells (about x8 from 128^3 to 256^3), mixed plans hold the extra
+    # FP32 planes, and permuting the extents changes little
+    from paper_1107_2461_gb300 import fdi
+    est = fdi.stokes_plan_bytes_estimate
+    for prec in (fdi.PREC_FP64, fdi.PREC_MIXED_F16):
+        sizes = [est((n, n, n), prec) for n in (16, 32, 64, 128, 256)]
+        assert all(b > a for a, b in zip(sizes, sizes[1:]))
+        assert 7.0 < sizes[-1] / sizes[-2] < 8.5
+        a, b = est((64, 128, 256), prec), est((256, 128, 64), prec)
+        assert abs(a - b) <= 0.05 * max(a, b)
+    assert est((128, 128, 128), fdi.PREC_MIXED_F16) > est((128, 128, 128), fdi.PREC_FP64)
+    # 256^3 Stokes plans fit many times over in a GB300's 288 GB
+    assert est((256, 256, 256), fdi.PREC_MIXED_F16) < 16e9
