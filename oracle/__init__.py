@@ -16,8 +16,10 @@ Modules
   decomposition the Lynch eigenvalue decomposition solvers TPF (Eq. 25, 29) and
                 TPT (Thomas in one direction, Sec. 3), done naively
   stokes        the staggered (MAC) Stokes system (Eq. 8), its direct solve, the
-                three-step semi-direct inverse (Sec. 2) and BiCGstab on the
-                pressure matrix C (Eq. 9)
+                three-step semi-direct inverse (Sec. 2) and BiCGstab, BiCGstab(2)
+                or volume-weighted CG on the pressure matrix C (Eq. 9)
+  cylindrical   the Helmholtz operator in cylindrical coordinates and its TPT
+                (Eq. 44) and TPF (Eq. 45-46) inverses (Sec. 6)
 
 Every function names the passage it follows.  Parity: every function is
 pinned by a -m "not gpu" test against a closed form, an invariant, a brute-force
