@@ -73,6 +73,13 @@ def test_invalid_arguments_rejected_without_touching_the_gpu(lib):
     assert lib.fdi_plan_destroy(None) == fdi.ERR_INVALID_ARG
     assert lib.fdi_last_result(None, None, None, None) == fdi.ERR_INVALID_ARG
     assert lib.fdi_helmholtz_solve_batched(None, None, None, None, -1, None) == fdi.ERR_INVALID_ARG
+    assert lib.fdi_field_solve_host(None, 0, 1.0, 1.0, None, None, 1, None, None) == fdi.ERR_INVALID_ARG
+    assert lib.fdi_stokes_solve(None, 1.0, 1.0, None, None, None, None) == fdi.ERR_INVALID_ARG
+    for setter in ("fdi_plan_set_krylov", "fdi_plan_set_stokes_preconditioner", "fdi_plan_set_graphs",
+                   "fdi_plan_set_thomas_config", "fdi_plan_set_transform_config", "fdi_plan_enable_timing"):
+        assert getattr(lib, setter)(None, 0) == fdi.ERR_INVALID_ARG, setter
+    assert lib.fdi_plan_set_tolerances(None, 1e-10, 2, 1e-10, 10) == fdi.ERR_INVALID_ARG
+    assert lib.fdi_last_launch_count(None, None) == fdi.ERR_INVALID_ARG
 
 
 def test_stokes_plan_bytes_estimate_scales_with_the_grid(lib):
