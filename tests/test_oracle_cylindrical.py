@@ -113,3 +113,40 @@ def test_second_order_convergence_to_an_analytic_solution(axis):
     errs = [_manufactured_error(n, 1.0, 0.5, axis) for n in (8, 16, 32)]
     ratios = [errs[i] / errs[i + 1] for i in range(2)]
     assert errs[-1] < 5e-3 and all(r > 3.0 for r in ratios), (errs, ratios)
+
+
+def _mutant_no_face_radius(rfaces, bc_in=D, bc_out=D):
+    # planted mistake: Cartesian radial fluxes (the face radius dropped)
+    A, K, g = _ORIG_RADIAL(rfaces, bc_in, bc_out)
+    rho = np.asarray(rfaces, dtype=np.float64)
+    h = np.diff(rho)
+    c = 0.5 * (rho[1:] + rho[:-1])
+    n = h.size
+    K2 = np.zeros_like(K)
+    for i in range(n - 1):
+        w = 1.0 / (c[i + 1] - c[i])
+        K2[i, i + 1] = K2[i + 1, i] = w
+        K2[i, i] -= w
+        K2[i + 1, i + 1] -= w
+    if rho[0] > 0 and bc_in == D:
+        K2[0, 0] -= 2.0 / h[0]
+    if bc_out == D:
+        K2[n - 1, n - 1] -= 2.0 / h[n - 1]
+    return A, K2, g
+
+
+def _mutant_theta_sign(rfaces, bc_in=D, bc_out=D):
+    # planted mistake: the theta term with the wrong sign
+    A, K, g = _ORIG_RADIAL(rfaces, bc_in, bc_out)
+    return A, K, -g
+
+
+_ORIG_RADIAL = cy.radial_operator
+
+
+@pytest.mark.parametrize("mutant", [_mutant_no_face_radius, _mutant_theta_sign])
+def test_planted_mistakes_fail_the_convergence_pin(monkeypatch, mutant):
+    monkeypatch.setattr(cy, "radial_operator", mutant)
+    errs = [_manufactured_error(n, 1.0, 0.5, False) for n in (8, 16, 32)]
+    converges = errs[-1] < 5e-3 and all(errs[i] / errs[i + 1] > 3.0 for i in range(2))
+    assert not converges, errs
