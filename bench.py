@@ -165,6 +165,18 @@ def oracle_tpt_time(n, seed=0):
     return time.perf_counter() - t0
 
 
+def oracle_tpt_time_one_thread(n, timeout=180):
+    """The same oracle solve in a child process limited to one BLAS / OpenMP
+    thread (seconds; None if it could not be timed)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = f"import sys; sys.path.insert(0, {ROOT!r}); import bench; print(bench.oracle_tpt_time({tuple(n)!r}))"
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=timeout)
+        return float(out.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+
+
 def blas_threads():
     try:
         from threadpoolctl import threadpool_info
@@ -558,8 +570,10 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t = oracle_tpt_time(n)
+        t1 = oracle_tpt_time_one_thread(n)
         cpu = {"value": P / t, "unit": "grid-pts/s", "cores": blas_threads(), "kind": "oracle",
-               "sample": f"one full {args.n}^3 TPT solve by the NumPy FP64 oracle ({t:.2f} s)"}
+               "sample": f"one full {args.n}^3 TPT solve by the NumPy FP64 oracle ({t:.2f} s)",
+               "one_thread": ({"value": P / t1, "seconds": t1} if t1 else None)}
     if rank != 0:
         return 0
     line = {
