@@ -1039,7 +1039,7 @@ fdi_status mixed_setup(fdi_plan* p) {
     return FDI_ERR_UNSUPPORTED;
   }
   if (p->thomas_axis != 2) {
-    set_error("the mixed-precision path runs TPT with Thomas along z (thomas_axis = 2)");
+    set_error("the mixed-precision path runs TPT (thomas_axis 0, 1, 2 or -2), not TPF (-1)");
     return FDI_ERR_UNSUPPORTED;
   }
   cudaStream_t s;
