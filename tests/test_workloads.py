@@ -13,7 +13,7 @@ def test_tanh_faces_cluster_at_both_walls():
         assert x[0] == 0.0 and abs(x[-1] - 1.0) < 1e-15 and np.all(h > 0)
         # symmetric about the centre, smallest cells at the walls
         assert np.allclose(x + x[::-1], 1.0, atol=1e-15)
-        assert h[0] == h.min() and abs(h[n // 2 - 1] - h.max()) <= 1e-14
+        assert abs(h[0] - h.min()) <= 1e-15 and abs(h[n // 2 - 1] - h.max()) <= 1e-14
     # beta = 0: uniform
     assert np.allclose(np.diff(w.tanh_faces(8, 0.0)), 1.0 / 8)
 
