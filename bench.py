@@ -230,13 +230,11 @@ def tensor_flops(name, n):
     return 6.0 * P * n[d] if name.endswith("_tc") else None
 
 
-def run_arm(fdi, torch, prec, n, K, W, dev, rank, stream, cluster=None, thomas_axis=2, refine_tol=None):
+def run_arm(fdi, torch, prec, n, K, W, dev, rank, stream, thomas_axis=2, refine_tol=None):
     faces = workloads.box_faces(n, BETA)
     plan = fdi.plan_create(faces, n, prec=prec, thomas_axis=thomas_axis)
     if refine_tol is not None:
         plan.set_tolerances(refine_tol, 3)
-    if cluster is not None and prec != fdi.PREC_FP64:
-        fdi.set_transform_config(plan, cluster)
     f = workloads.rhs_uniform(n[::-1], rank)
     rhs = torch.from_numpy(f).to(dev)
     out = torch.empty_like(rhs)
@@ -419,7 +417,6 @@ def main():
     ap.add_argument("--arms", default="fp64,mixed")
     ap.add_argument("--no-tpf", action="store_true", help="skip the FP64 TPF arm")
     ap.add_argument("--no-fp64tol", action="store_true", help="skip the mixed arm refined to 1e-11")
-    ap.add_argument("--cluster", type=int, default=None, help="tensor-core transform cluster size (1, 2, 4)")
     ap.add_argument("--stokes-n", type=int, default=64, help="Stokes latency grid (0: skip)")
     ap.add_argument("--stokes-reps", type=int, default=10)
     ap.add_argument("--batch", type=int, default=64, help="batched uneven-grid solves per batch (0: skip)")
@@ -483,7 +480,7 @@ def main():
         try:
             slow = name == "fp64_tpf"  # FP64-pipe bound: fewer solves
             arms[name] = run_arm(fdi, torch, prec, n, max(3, K // 10) if slow else K, W, dev, rank, stream,
-                                 args.cluster, thomas_axis=taxis,
+                                 thomas_axis=taxis,
                                  refine_tol=tol if name == "mixed_fp64tol" else None)
             if slow:
                 arms[name]["K"] = max(3, K // 10)

@@ -34,8 +34,12 @@
  * Asynchrony: every solve is enqueued on `stream`.  Numerical results
  * (iterations, refinement steps, relative residual) are read with
  * fdi_last_result after the caller synchronises the stream.
- * fdi_stokes_solve reads one convergence flag back per Krylov iteration and so
- * synchronises `stream` internally.
+ * fdi_stokes_solve on a capturable (non-default) stream with timing off runs
+ * its Krylov loop on the device (a WHILE node of a CUDA graph repeats the
+ * iteration until a device-side convergence flag is set) and needs no host
+ * round trip; on the legacy default stream, or with per-kernel timing on, it
+ * reads the convergence flag back after every iteration and so synchronises
+ * `stream`.
  *
  * Threading: a plan owns one workspace.  Using one plan from two host threads,
  * or on two streams at once, is a data race.
@@ -76,12 +80,13 @@ typedef enum { FDI_GRID_CELL = 0, FDI_GRID_MAC = 1 } fdi_grid;
  * form hi*hi + hi*lo + lo*hi with FP32 accumulation, keep the intermediate
  * fields in FP32, run the Thomas sweep in FP32, and recover FP64 accuracy by
  * iterative refinement against a residual evaluated in double-float (about 48
- * significant bits) arithmetic. */
+ * significant bits) arithmetic.  Only the split-fp16 form is built: at FP32
+ * accumulation it converges like a TF32 split at twice the tensor rate. */
 typedef enum {
   FDI_PREC_FP64 = 0,
-  FDI_PREC_MIXED_TF32 = 1,
-  FDI_PREC_MIXED_BF16 = 2,
-  FDI_PREC_MIXED_F16 = 3
+  FDI_PREC_MIXED_TF32 = 1, /* reserved, not built: fdi_plan_create returns FDI_ERR_UNSUPPORTED */
+  FDI_PREC_MIXED_BF16 = 2, /* reserved, not built: fdi_plan_create returns FDI_ERR_UNSUPPORTED */
+  FDI_PREC_MIXED_F16 = 3   /* split fp16 (hi + lo), the built mixed mode */
 } fdi_precision;
 
 /* Fields of a plan.  FDI_FIELD_CELL is the cell-centred grid (for a MAC plan:
@@ -206,13 +211,6 @@ fdi_status fdi_plan_eigen(const fdi_plan* plan, fdi_field field, int d, double* 
 fdi_status fdi_apply_transform(fdi_plan* plan, fdi_field field, int d, int inverse, const float* in, float* out,
                                long long rows, fdi_stream_t stream);
 
-/* Launch shape of the tensor-core transforms of a mixed plan: `cluster` CTAs
- * (1, 2 or 4) form a thread-block cluster and share each chunk of the
- * transform matrix through TMA multicast, dividing its L2 reads by `cluster`.
- * A tuning knob (see fdi_plan_autotune); results are bitwise identical for
- * every value.  Default 1. */
-fdi_status fdi_plan_set_transform_config(fdi_plan* plan, int cluster);
-
 /* Allocation-free eigen decomposition of one 1D operator (the same kernel as
  * plan creation).  No counterpart in the paper: it exists for callers that may
  * not allocate device memory -- code that runs where cudaMalloc is forbidden or
@@ -224,18 +222,36 @@ fdi_status fdi_plan_set_transform_config(fdi_plan* plan, int cluster);
  * loads the library until the process exits.
  *   faces       host, n+1 ascending doubles; face_kind 0: n cell unknowns with
  *               the walls bc_lo / bc_hi; face_kind 1: the n-1 interior-face
- *               unknowns of a staggered velocity component (no-slip walls)
+ *               unknowns of a staggered velocity component (no-slip walls:
+ *               bc_lo and bc_hi must both be FDI_BC_DIRICHLET, anything else
+ *               is rejected with FDI_ERR_INVALID_ARG)
  *   lam, E, Einv device outputs: m, m*m, m*m doubles (m unknowns, row-major
  *               as fdi_plan_eigen)
  *   converged   optional host pointer: if given, the call synchronises `stream`
  *               and stores 1 if the QL iteration converged, else 0
  * Limits: 2 <= n <= 256 (3 <= n for face_kind 1); larger n is rejected with
  * FDI_ERR_INVALID_ARG.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Every call shares the one array and overwrites it (the flag is
- * cleared per call): calls that overlap on the GPU, on any stream, race. */
+ * address (cudaGetSymbolAddress).  Every call copies the operator from
+ * pageable host memory (and, with `converged`, synchronises `stream`), so no
+ * call may be made while `stream` is being captured into a CUDA graph: a
+ * capturing stream is rejected with FDI_ERR_INVALID_ARG.  Every call shares the
+ * one array and overwrites it (the flag is cleared per call): calls that
+ * overlap on the GPU, on any stream, race. */
 fdi_status fdi_eigen_noalloc(const double* faces, int n, int face_kind, fdi_bc bc_lo, fdi_bc bc_hi, double* lam,
                              double* E, double* Einv, int* converged, fdi_stream_t stream);
+
+/* Bound on every wait inside the tensor-core transform kernels of a mixed plan
+ * (a CTA's roles hand shared-memory stages to one another through mbarriers),
+ * in SM clock cycles; 0 restores the default of 4e9 cycles (about two seconds
+ * at 2 GHz).  A wait that runs out stops every role of its CTA, lets the
+ * asynchronous copies and MMAs already issued finish, frees its tensor memory
+ * and returns; the plan then records the failure in a flag that stays set, so
+ * fdi_last_result (and every later solve's result) reports FDI_ERR_TIMEOUT,
+ * until the next call of this function clears it.  The solution of a solve
+ * that timed out is undefined.  Synchronises the device (the flag is cleared
+ * once nothing runs); drops the plan's captured graphs.  FP64 plans accept
+ * the call and have no such waits.  cycles < 0: FDI_ERR_INVALID_ARG. */
+fdi_status fdi_plan_set_wait_limit(fdi_plan* plan, long long cycles);
 
 /* FP32 Thomas sweep of mixed plans: 64 or 128 lines (one per thread) per
  * CTA, or 2: two adjacent lines per thread, 64 threads per CTA (default 2).
@@ -244,23 +260,22 @@ fdi_status fdi_plan_set_thomas_config(fdi_plan* plan, int lines_per_cta);
 
 /* Autotuner for mixed plans: times `reps` complete Helmholtz solves
  * (sigma = 1, `lambda`, rhs -> out on `stream`, after one warm-up solve each)
- * for every transform cluster size (1, 2, 4) and Thomas configuration (2, 64,
- * 128),
- * keeps the fastest on the plan and records it for the plan's grid shape:
+ * for every Thomas configuration (2, 64, 128), keeps the fastest on the plan
+ * and records it for the plan's grid shape:
  * plans created later with the same shape and precision start with it.  Every
  * configuration computes bitwise-identical results.  rhs and out: device FP64
  * fields of the plan's cell shape, distinct; out is overwritten.  The chosen
- * values are written to *cluster_out and *thomas_tl_out (host, may be NULL).
+ * value is written to *thomas_tl_out (host, may be NULL).
  * Synchronises `stream`.  FP64 plans have nothing to tune (returns OK). */
 fdi_status fdi_plan_autotune(fdi_plan* plan, double lambda, const double* rhs, double* out, int reps,
-                             int* cluster_out, int* thomas_tl_out, fdi_stream_t stream);
+                             int* thomas_tl_out, fdi_stream_t stream);
 
 /* CUDA-graph replay of field solves (default on).  A Helmholtz / Laplace /
  * field solve whose arguments (field, sigma, lambda, rhs, out, stream) repeat
  * those of the previous call on this plan is captured into a CUDA graph on its
  * second occurrence and replayed as one graph launch from then on; results are
  * identical to the eager launch sequence.  The legacy default stream and plans
- * with timing on always run eagerly.  Changing tolerances or the transform
+ * with timing on always run eagerly.  Changing tolerances or the Thomas
  * configuration drops the captured graph.  on: 0 off, nonzero on. */
 fdi_status fdi_plan_set_graphs(fdi_plan* plan, int on);
 

@@ -230,6 +230,11 @@ extern "C" fdi_status fdi_eigen_noalloc(const double* faces, int n, int face_kin
   if (!faces || !lam || !E || !Einv) return FDI_ERR_INVALID_ARG;
   if (face_kind != 0 && face_kind != 1) return FDI_ERR_INVALID_ARG;
   if ((unsigned)bc_lo > 1u || (unsigned)bc_hi > 1u) return FDI_ERR_INVALID_ARG;
+  if (face_kind == 1 && (bc_lo != FDI_BC_DIRICHLET || bc_hi != FDI_BC_DIRICHLET)) {
+    set_error("fdi_eigen_noalloc: a face operator (face_kind 1) has no-slip walls; bc_lo and bc_hi must be "
+              "FDI_BC_DIRICHLET");
+    return FDI_ERR_INVALID_ARG;
+  }
   if (n < (face_kind ? 3 : 2) || n > kMaxN) {
     set_error("fdi_eigen_noalloc: n must lie in [2, 256] (cell) or [3, 256] (face); its scratch holds 256 unknowns");
     return FDI_ERR_INVALID_ARG;
@@ -298,6 +303,15 @@ extern "C" fdi_status fdi_eigen_noalloc(const double* faces, int n, int face_kin
   int* d_flag = reinterpret_cast<int*>(base + 3 * kMaxN + 8);
   const EigenJob job{u, zero_flux ? 1 : 0, d_m, d_kd, d_ko, lam, E, Einv};
   cudaStream_t s = (cudaStream_t)stream;
+  // the operator is copied from pageable host memory (the stack), which a
+  // stream capture cannot record: refuse instead of breaking the capture
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    set_error("fdi_eigen_noalloc: the stream is being captured; this call copies from pageable host memory and "
+              "must run outside stream capture");
+    return FDI_ERR_INVALID_ARG;
+  }
   // pageable-source copies return once the source has been staged, so the
   // stack arrays may go out of scope afterwards
   FDI_CUDA_TRY(cudaMemcpyAsync(d_m, m, u * sizeof(double), cudaMemcpyHostToDevice, s));

@@ -99,8 +99,8 @@ struct fdi_plan {
   float* wr1 = nullptr;             // mixed: first residual r_1 as (hi, lo) FP32 planes
   long long wr1_plane = 0;
   float* d_scales = nullptr;        // per refinement round: max |field| of the pass inputs
-  int* d_err = nullptr;             // nonzero: a tensor-core kernel hit a wait limit
-  int tc_cluster = 1;               // CTAs sharing each transform-matrix chunk by TMA multicast
+  int* d_err = nullptr;             // nonzero: a tensor-core kernel hit a wait limit (sticky)
+  long long wait_cycles = 0;        // bound of every tensor-core kernel wait, cycles (0: about 2 s)
   int thomas_tl = 2;                // FP32 Thomas: lines per CTA (64, 128) or 2 = two lines per thread
   float2* lam_w = nullptr;          // lambda-scaled double-float flux weights [3][3][kMaxN]
   unsigned* d_counter = nullptr;    // ticket counter of the fused last-block reductions (zero between launches)

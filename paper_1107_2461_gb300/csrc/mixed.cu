@@ -1456,9 +1456,14 @@ extern "C" fdi_status fdi_apply_transform(fdi_plan* plan, fdi_field field, int d
   return launch_tc_transform(plan, inverse ? m->fwd : m->bwd, t, inverse ? "transform_fwd_tc" : "transform_bwd_tc", s);
 }
 
-extern "C" fdi_status fdi_plan_set_transform_config(fdi_plan* plan, int cluster) {
-  if (!plan || (cluster != 1 && cluster != 2 && cluster != 4)) return FDI_ERR_INVALID_ARG;
-  plan->tc_cluster = cluster;
-  fdi::invalidate_graph(plan);
+extern "C" fdi_status fdi_plan_set_wait_limit(fdi_plan* plan, long long cycles) {
+  if (!plan || cycles < 0) return FDI_ERR_INVALID_ARG;
+  plan->wait_cycles = cycles;
+  fdi::invalidate_graph(plan);  // the limit is a kernel argument of captured launches
+  if (plan->d_err) {
+    // nothing of this plan may still run while its flag is cleared
+    FDI_CUDA_TRY(cudaDeviceSynchronize());
+    FDI_CUDA_TRY(cudaMemset(plan->d_err, 0, sizeof(int)));
+  }
   return FDI_OK;
 }

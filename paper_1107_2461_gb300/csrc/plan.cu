@@ -393,6 +393,10 @@ fdi_status fdi_plan_create(const double* const faces[3], const int n[3], const f
   if (!faces || !n) return FDI_ERR_INVALID_ARG;
   if (grid != FDI_GRID_CELL && grid != FDI_GRID_MAC) return FDI_ERR_INVALID_ARG;
   if (prec < FDI_PREC_FP64 || prec > FDI_PREC_MIXED_F16) return FDI_ERR_INVALID_ARG;
+  if (prec == FDI_PREC_MIXED_TF32 || prec == FDI_PREC_MIXED_BF16) {
+    set_error("fdi_plan_create: FDI_PREC_MIXED_TF32 and FDI_PREC_MIXED_BF16 are not built; use FDI_PREC_MIXED_F16");
+    return FDI_ERR_UNSUPPORTED;
+  }
   if (grid == FDI_GRID_CELL && (!bc_lo || !bc_hi)) return FDI_ERR_INVALID_ARG;
   if (thomas_axis < -2 || thomas_axis > 2) {
     set_error("thomas_axis must be 0, 1, 2 (Thomas along x, y, z), -2 (the longest direction) or -1 (TPF)");

@@ -118,7 +118,7 @@ fdi_status field_solve(fdi_plan* p, int field, double sigma, double lambda, cons
   return launch_axis_permute(p, p->tstage[1], out, false, s);
 }
 
-// Autotuned transform / Thomas configurations per (grid shape, precision),
+// Autotuned Thomas configurations per (grid shape, precision),
 // applied to plans created later with the same shape.
 namespace {
 struct TuneKey {
@@ -128,7 +128,7 @@ struct TuneKey {
   }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tune;
+std::map<TuneKey, int> g_tune;
 TuneKey tune_key(const fdi_plan* p) { return TuneKey{p->n[0], p->n[1], p->n[2], (int)p->prec, (int)p->grid}; }
 }  // namespace
 
@@ -136,16 +136,13 @@ void forget_batch_graph(const fdi_plan* p);
 
 void remember_tuning(const fdi_plan* p) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[tune_key(p)] = {p->tc_cluster, p->thomas_tl};
+  g_tune[tune_key(p)] = p->thomas_tl;
 }
 
 void apply_tuning(fdi_plan* p) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tune.find(tune_key(p));
-  if (it != g_tune.end()) {
-    p->tc_cluster = it->second.first;
-    p->thomas_tl = it->second.second;
-  }
+  if (it != g_tune.end()) p->thomas_tl = it->second;
 }
 
 void invalidate_graph(fdi_plan* p) {
@@ -451,24 +448,22 @@ fdi_status fdi_plan_set_thomas_config(fdi_plan* plan, int lines_per_cta) {
 }
 
 fdi_status fdi_plan_autotune(fdi_plan* plan, double lambda, const double* rhs, double* out, int reps,
-                             int* cluster_out, int* thomas_tl_out, fdi_stream_t stream) {
+                             int* thomas_tl_out, fdi_stream_t stream) {
   fdi_status st = validate_field_args(plan, FDI_FIELD_CELL, 1.0, lambda);
   if (st != FDI_OK) return st;
   if (!rhs || !out || rhs == out || reps < 1 || reps > 1000) return FDI_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (plan->prec != FDI_PREC_FP64) {
-    const int clusters[3] = {1, 2, 4};
     const int tls[3] = {2, 64, 128};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     FDI_CUDA_TRY(cudaEventCreate(&e0));
     FDI_CUDA_TRY(cudaEventCreate(&e1));
     float best = 0.f;
-    int best_c = plan->tc_cluster, best_t = plan->thomas_tl;
+    int best_t = plan->thomas_tl;
     const bool timing = plan->timing;
     plan->timing = false;
-    for (int ci = 0; ci < 3 && st == FDI_OK; ++ci) {
+    {
       for (int ti = 0; ti < 3 && st == FDI_OK; ++ti) {
-        plan->tc_cluster = clusters[ci];
         plan->thomas_tl = tls[ti];
         st = field_solve(plan, FDI_FIELD_CELL, 1.0, lambda, rhs, out, s);  // warm-up
         if (st != FDI_OK) break;
@@ -484,7 +479,6 @@ fdi_status fdi_plan_autotune(fdi_plan* plan, double lambda, const double* rhs, d
         cudaEventElapsedTime(&ms, e0, e1);
         if (best == 0.f || ms < best) {
           best = ms;
-          best_c = clusters[ci];
           best_t = tls[ti];
         }
       }
@@ -492,13 +486,11 @@ fdi_status fdi_plan_autotune(fdi_plan* plan, double lambda, const double* rhs, d
     plan->timing = timing;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    plan->tc_cluster = best_c;
     plan->thomas_tl = best_t;
     invalidate_graph(plan);
     if (st != FDI_OK) return st;
     remember_tuning(plan);
   }
-  if (cluster_out) *cluster_out = plan->tc_cluster;
   if (thomas_tl_out) *thomas_tl_out = plan->thomas_tl;
   return FDI_OK;
 }

@@ -18,14 +18,14 @@
 // column in the epilogue) and streamed by TMA.
 //
 // Warp roles of the persistent CTA (one per SM, 480 threads):
-//   warp 0      TMA producer of the B chunks
+//   warp 0      TMA producer of the B chunks (each CTA loads its own copy; L2-resident)
 //   warp 1      TMEM allocator and single-thread MMA issuer
 //   warps 2-9   converters: read FP32 rows of A from shared memory, scale,
 //               split to fp16 hi/lo, store them in the 64-byte swizzled
 //               K-major layout of the MMA stage
 //   warps 10-13 epilogue: TMEM -> registers -> unscale -> global store
 //   warp 14     TMA producer of the FP32 A chunks (128 rows x 32 columns)
-// Three MMA stages of K = 32, four FP32 A slots ahead of them (64 KB of input
+// Three MMA stages of K = 32, three FP32 A slots ahead of them (48 KB of input
 // in flight per SM), two TMEM accumulators of N_pad columns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -75,7 +75,6 @@ __device__ __forceinline__ float scale_from_max(float mx) {
 }
 
 
-template <int C>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_transform(const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmA,
                    const __grid_constant__ CUtensorMap tmO, TcArgs a) {
@@ -92,16 +91,17 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + BAR_OFF);
   uint64_t* full_b = bars;                  // B chunk landed (TMA transaction bytes)
   uint64_t* conv = bars + STAGES;           // A chunk converted (NCONV warp arrivals)
-  uint64_t* empty = bars + 2 * STAGES;      // stage consumed by the MMAs (C commits)
+  uint64_t* empty = bars + 2 * STAGES;      // stage consumed by the MMAs (one commit)
   uint64_t* accf = bars + 3 * STAGES;       // accumulator complete
   uint64_t* acce = bars + 3 * STAGES + 2;   // accumulator drained by the epilogue
   uint64_t* a_full = bars + 3 * STAGES + 4;          // FP32 A chunk landed (TMA bytes)
   uint64_t* a_empty = bars + 3 * STAGES + 4 + NA32;  // FP32 A chunk read (NCONV warp arrivals)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * STAGES + 4 + 2 * NA32);
+  uint64_t* mma_drain = bars + 3 * STAGES + 4 + 2 * NA32 + 1;  // MMAs issued before a failure completed
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const uint32_t rank = (C > 1) ? tc::cluster_ctarank() : 0u;
+  const long long wl = a.wait_cycles > 0 ? a.wait_cycles : tc::kWaitCycles;
   const int N_pad = a.N_pad;
   uint32_t tmem_cols = 32;
   while (tmem_cols < (uint32_t)(2 * N_pad)) tmem_cols <<= 1;
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int s = 0; s < STAGES; ++s) {
       tc::mbar_init(&full_b[s], 1);
       tc::mbar_init(&conv[s], NCONV);
-      tc::mbar_init(&empty[s], C);
+      tc::mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&accf[b], 1);
@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       tc::mbar_init(&a_full[b], 1);
       tc::mbar_init(&a_empty[b], NCONV);
     }
+    tc::mbar_init(mma_drain, 1);
     s_abort = 0;
     tc::fence_mbar_init();
   }
@@ -139,57 +140,37 @@ __global__ void __launch_bounds__(THREADS, 1)
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  if (C > 1) tc::cluster_sync();
   const uint32_t tmem_base = *tmem_slot;
 
   const long long num_tiles = (a.R + BM - 1) / BM;
-  const long long iters_all = (num_tiles + gridDim.x - 1) / gridDim.x;
-  const long long my_iters =
-      (C > 1) ? iters_all
-              : (blockIdx.x < num_tiles ? (num_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0);
+  const long long my_iters = blockIdx.x < num_tiles ? (num_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int nK = a.nK;
 
   if (warp == 0) {
     // ---------------- TMA producer (B) ----------------
     if (lane == 0) {
       const uint32_t bbytes = (uint32_t)(2 * N_pad * ROWB);
-      const int rows_per = N_pad / C;
-      const int r0 = (int)rank * rows_per;
       uint32_t g = 0;
       for (long long it = 0; it < my_iters && !s_abort; ++it) {
         for (int kc = 0; kc < nK; ++kc, ++g) {
           const int s = g % STAGES;
           const uint32_t ph = (g / STAGES) & 1;
-          if (!tc::mbar_wait(&empty[s], ph ^ 1, &s_abort)) {
+          if (!tc::mbar_wait(&empty[s], ph ^ 1, &s_abort, wl)) {
             s_abort = 1;
             atomicExch(a.err, 1);
             break;
           }
           tc::mbar_expect_tx(&full_b[s], bbytes);
           uint8_t* st = smem + s * STAGE_BYTES;
-          const uint32_t dhi = tc::smem_u32(st + 2 * A_BYTES) + r0 * ROWB;
-          const uint32_t dlo = tc::smem_u32(st + 2 * A_BYTES + B_BYTES) + r0 * ROWB;
-          if (C == 1) {
-            tc::tma_load_2d(dhi, &tmB, kc * BK, r0, &full_b[s]);
-            tc::tma_load_2d(dlo, &tmB, kc * BK, N_pad + r0, &full_b[s]);
-          } else {
-            const uint16_t mask = (uint16_t)((1u << C) - 1u);
-            tc::tma_load_2d_mc(dhi, &tmB, kc * BK, r0, &full_b[s], mask);
-            tc::tma_load_2d_mc(dlo, &tmB, kc * BK, N_pad + r0, &full_b[s], mask);
-          }
+          tc::tma_load_2d(tc::smem_u32(st + 2 * A_BYTES), &tmB, kc * BK, 0, &full_b[s]);
+          tc::tma_load_2d(tc::smem_u32(st + 2 * A_BYTES + B_BYTES), &tmB, kc * BK, N_pad, &full_b[s]);
         }
       }
-      if (C > 1 && !s_abort) {
-        // every CTA's commits for the last stages must have reached this CTA's
-        // barriers before the cluster may retire
-        const uint32_t total = (uint32_t)(my_iters * nK);
-        for (uint32_t g2 = (total > STAGES ? total - STAGES : 0); g2 < total; ++g2) {
-          if (!tc::mbar_wait(&empty[g2 % STAGES], (g2 / STAGES) & 1, &s_abort)) {
-            atomicExch(a.err, 1);
-            break;
-          }
-        }
-      }
+      // the last STAGES loads issued may still be writing shared memory (after
+      // a failure nobody consumes them); their phases complete regardless, and
+      // a consumed one has completed already
+      for (uint32_t g2 = g > STAGES ? g - STAGES : 0; g2 < g; ++g2)
+        tc::mbar_drain(&full_b[g2 % STAGES], (g2 / STAGES) & 1);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
@@ -199,7 +180,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (long long it = 0; it < my_iters && !s_abort; ++it) {
         const int buf = (int)(it & 1);
         const uint32_t aph = (uint32_t)((it >> 1) & 1);
-        if (!tc::mbar_wait(&acce[buf], aph ^ 1, &s_abort)) {
+        if (!tc::mbar_wait(&acce[buf], aph ^ 1, &s_abort, wl)) {
           s_abort = 1;
           atomicExch(a.err, 2);
           break;
@@ -210,7 +191,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int kc = 0; kc < nK; ++kc, ++g) {
           const int s = g % STAGES;
           const uint32_t ph = (g / STAGES) & 1;
-          if (!tc::mbar_wait(&full_b[s], ph, &s_abort) || !tc::mbar_wait(&conv[s], ph, &s_abort)) {
+          if (!tc::mbar_wait(&full_b[s], ph, &s_abort, wl) || !tc::mbar_wait(&conv[s], ph, &s_abort, wl)) {
             ok = false;
             break;
           }
@@ -226,10 +207,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc::mma_f16(d, tc::sdesc_k_sw64(ahi + off), tc::sdesc_k_sw64(blo + off), idesc, 1u);
             tc::mma_f16(d, tc::sdesc_k_sw64(alo + off), tc::sdesc_k_sw64(bhi + off), idesc, 1u);
           }
-          if (C == 1)
-            tc::mma_commit(&empty[s]);
-          else
-            tc::mma_commit_mc(&empty[s], (uint16_t)((1u << C) - 1u));
+          tc::mma_commit(&empty[s]);
         }
         if (!ok) {
           s_abort = 1;
@@ -238,6 +216,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         tc::mma_commit(&accf[buf]);
       }
+      // every MMA issued has completed before TMEM and the stages are released
+      // (also when another role gave up waiting for them)
+      tc::mma_commit(mma_drain);
+      tc::mbar_drain(mma_drain, 0);
     }
   } else if (warp < 2 + NCONV) {
     // ---------------- converters ----------------
@@ -262,7 +244,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t pa = (g / NA32) & 1;
       const int s = g % STAGES;
       const uint32_t ph = (g / STAGES) & 1;
-      if (!tc::mbar_wait(&a_full[sa], pa, &s_abort)) {
+      if (!tc::mbar_wait(&a_full[sa], pa, &s_abort, wl)) {
         atomicExch(a.err, 4);
         break;
       }
@@ -285,7 +267,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int e = 0; e < 8; ++e) v[q][e] = sf[(kofs_q[q] + e) * BM + row_q[q]];
       }
-      if (!tc::mbar_wait(&empty[s], ph ^ 1, &s_abort)) {
+      if (!tc::mbar_wait(&empty[s], ph ^ 1, &s_abort, wl)) {
         atomicExch(a.err, 4);
         break;
       }
@@ -329,7 +311,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int kc = 0; kc < nK; ++kc, ++g) {
           const int sa = g % NA32;
           const uint32_t pa = (g / NA32) & 1;
-          if (!tc::mbar_wait(&a_empty[sa], pa ^ 1, &s_abort)) {
+          if (!tc::mbar_wait(&a_empty[sa], pa ^ 1, &s_abort, wl)) {
             s_abort = 1;
             atomicExch(a.err, 6);
             break;
@@ -345,6 +327,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
       }
+      for (uint32_t g2 = g > NA32 ? g - NA32 : 0; g2 < g; ++g2)
+        tc::mbar_drain(&a_full[g2 % NA32], (g2 / NA32) & 1);
     }
   } else {
     // ---------------- epilogue ----------------
@@ -368,7 +352,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const long long tile = blockIdx.x + it * gridDim.x;
       const int buf = (int)(it & 1);
       const uint32_t aph = (uint32_t)((it >> 1) & 1);
-      if (!tc::mbar_wait(&accf[buf], aph, &s_abort)) {
+      if (!tc::mbar_wait(&accf[buf], aph, &s_abort, wl)) {
         atomicExch(a.err, 5);
         break;
       }
@@ -570,7 +554,6 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   tc::tc_fence_before();
   __syncthreads();
-  if (C > 1) tc::cluster_sync();
   if (warp == 1) {
     tc::tc_fence_after();
     tc::tmem_dealloc(tmem_base, tmem_cols);
@@ -634,13 +617,13 @@ fdi_status tc_prepare_matrix(fdi_plan* p, const double* T, int n, TcMatrix* m, c
     set_error("cuTensorMapEncodeTiled entry point unavailable");
     return FDI_ERR_CUDA;
   }
-  const int Cs[3] = {1, 2, 4};
-  for (int ci = 0; ci < 3; ++ci) {
+  {
+    // B chunks: N_pad rows x 32 fp16 (one half, hi or lo, of a stage's B operand)
     cuuint64_t dims[2] = {(cuuint64_t)m->K_pad, (cuuint64_t)(2 * m->N_pad)};
     cuuint64_t strides[1] = {(cuuint64_t)m->K_pad * sizeof(__half)};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)(m->N_pad / Cs[ci])};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)m->N_pad};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(reinterpret_cast<CUtensorMap*>(m->tmap[ci]), CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, m->B, dims,
+    CUresult r = enc(reinterpret_cast<CUtensorMap*>(m->tmap), CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, m->B, dims,
                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -658,36 +641,29 @@ void tc_free_matrix(TcMatrix* m) {
   m->col_scale = nullptr;
 }
 
-template <int C>
-fdi_status launch_cluster(fdi_plan* p, const TcMatrix& m, const CUtensorMap& mapA, const CUtensorMap& mapO,
-                          const TcArgs& args, long long tiles, cudaStream_t s) {
+fdi_status launch_kernel(fdi_plan* p, const TcMatrix& m, const CUtensorMap& mapA, const CUtensorMap& mapO,
+                         const TcArgs& args, long long tiles, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
-    FDI_CUDA_TRY(cudaFuncSetAttribute(k_tc_transform<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    FDI_CUDA_TRY(cudaFuncSetAttribute(k_tc_transform, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     attr_set = true;
   }
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-  long long grid = tiles < sms ? tiles : sms;
-  grid = (grid + C - 1) / C * C;
-  if (grid > sms) grid = sms / C * C;
+  const long long grid = tiles < sms ? tiles : sms;
   CUtensorMap map;
-  memcpy(&map, m.tmap[tc_cluster_index(C)], sizeof(CUtensorMap));
+  memcpy(&map, m.tmap, sizeof(CUtensorMap));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3(THREADS);
   cfg.dynamicSmemBytes = SMEM_BYTES;
   cfg.stream = s;
-  cudaLaunchAttribute attr[2];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = C;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = args.pdl ? 2 : 1;
-  FDI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_transform<C>, map, mapA, mapO, args));
+  cfg.numAttrs = args.pdl ? 1 : 0;
+  FDI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_transform, map, mapA, mapO, args));
   FDI_LAUNCH_CHECK(p);
   return FDI_OK;
 }
@@ -696,6 +672,7 @@ fdi_status launch_tc_transform(fdi_plan* p, const TcMatrix& m, TcArgs args, cons
   FDI_KTIMER(p, name, s);
   args.N_pad = m.N_pad;
   args.nK = (args.K + BK - 1) / BK;
+  args.wait_cycles = p->wait_cycles;
   args.col_scale = m.col_scale;
   const long long tiles = (args.R + BM - 1) / BM;
   if (args.R > 0x7fffffffLL - BM || args.in_pitch % 4 != 0 || (reinterpret_cast<uintptr_t>(args.in) & 15u) != 0) {
@@ -760,11 +737,7 @@ fdi_status launch_tc_transform(fdi_plan* p, const TcMatrix& m, TcArgs args, cons
         args.tma_store = 2;
     }
   }
-  switch (p->tc_cluster) {
-    case 2: return launch_cluster<2>(p, m, mapA, mapO, args, tiles, s);
-    case 4: return launch_cluster<4>(p, m, mapA, mapO, args, tiles, s);
-    default: return launch_cluster<1>(p, m, mapA, mapO, args, tiles, s);
-  }
+  return launch_kernel(p, m, mapA, mapO, args, tiles, s);
 }
 
 }  // namespace fdi

@@ -18,13 +18,9 @@ struct TcMatrix {
   int n = 0, N_pad = 0, K_pad = 0;
   void* B = nullptr;
   float* col_scale = nullptr;
-  // TMA descriptors of B for clusters of 1, 2 and 4 CTAs (each CTA of a cluster
-  // loads N_pad / C rows of every chunk and multicasts them to the others)
-  alignas(64) unsigned char tmap[3][128];
+  // TMA descriptor of B (boxes of N_pad rows x 32 columns)
+  alignas(64) unsigned char tmap[128];
 };
-
-// cluster sizes the transform kernel is built for
-inline int tc_cluster_index(int c) { return c == 4 ? 2 : (c == 2 ? 1 : 0); }
 
 struct TcArgs {
   // input: rows of K contiguous FP32 values, row r at in + r * in_pitch
@@ -54,6 +50,7 @@ struct TcArgs {
   const int* skip = nullptr;
   int* err = nullptr;
   int pdl = 0;                      // launch with programmatic stream serialization
+  long long wait_cycles = 0;        // bound of every wait (cycles); 0: the default
   // filled by the launcher
   int N_pad = 0, nK = 0;
   const float* col_scale = nullptr;

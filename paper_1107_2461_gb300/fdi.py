@@ -60,13 +60,13 @@ SIGNATURES = {
     "fdi_plan_eigen": (_i, [_vp, _i, _i, C.POINTER(_d), C.POINTER(_d), C.POINTER(_d), C.POINTER(_i)]),
     "fdi_last_launch_count": (_i, [_vp, C.POINTER(C.c_longlong)]),
     "fdi_apply_transform": (_i, [_vp, _i, _i, _i, _vp, _vp, C.c_longlong, _vp]),
-    "fdi_plan_set_transform_config": (_i, [_vp, _i]),
     "fdi_plan_set_stokes_preconditioner": (_i, [_vp, _i]),
     "fdi_plan_set_krylov": (_i, [_vp, _i]),
     "fdi_eigen_noalloc": (_i, [C.POINTER(_d), _i, _i, _i, _i, _vp, _vp, _vp, C.POINTER(_i), _vp]),
     "fdi_plan_set_graphs": (_i, [_vp, _i]),
     "fdi_plan_set_thomas_config": (_i, [_vp, _i]),
-    "fdi_plan_autotune": (_i, [_vp, _d, _vp, _vp, _i, C.POINTER(_i), C.POINTER(_i), _vp]),
+    "fdi_plan_set_wait_limit": (_i, [_vp, C.c_longlong]),
+    "fdi_plan_autotune": (_i, [_vp, _d, _vp, _vp, _i, C.POINTER(_i), _vp]),
     "fdi_plan_enable_timing": (_i, [_vp, _i]),
     "fdi_plan_kernel_times": (_i, [_vp, _i, C.POINTER(C.c_char_p), C.POINTER(_d), C.POINTER(C.c_longlong),
                                    C.POINTER(_i)]),
@@ -308,8 +308,10 @@ def set_stokes_preconditioner(plan: Plan, mode: int):
     _check(load().fdi_plan_set_stokes_preconditioner(plan.handle, int(mode)), "fdi_plan_set_stokes_preconditioner")
 
 
-def set_transform_config(plan: Plan, cluster: int):
-    _check(load().fdi_plan_set_transform_config(plan.handle, int(cluster)), "fdi_plan_set_transform_config")
+def set_wait_limit(plan: Plan, cycles: int):
+    """Bound (SM cycles, 0 = default) on the waits inside the tensor-core
+    kernels; also clears the plan's sticky wait-limit flag."""
+    _check(load().fdi_plan_set_wait_limit(plan.handle, int(cycles)), "fdi_plan_set_wait_limit")
 
 
 def set_thomas_config(plan: Plan, lines_per_cta: int):
@@ -317,12 +319,12 @@ def set_thomas_config(plan: Plan, lines_per_cta: int):
 
 
 def autotune(plan: Plan, lam, rhs, out, reps=3, stream=None):
-    """Time the transform / Thomas configurations on this plan, keep the fastest;
-    returns (cluster, thomas_lines_per_cta)."""
-    c, t = C.c_int(0), C.c_int(0)
-    _check(load().fdi_plan_autotune(plan.handle, float(lam), _ptr(rhs), _ptr(out), int(reps), C.byref(c), C.byref(t),
+    """Time the Thomas configurations on this plan, keep the fastest; returns the
+    chosen lines per CTA (2, 64 or 128)."""
+    t = C.c_int(0)
+    _check(load().fdi_plan_autotune(plan.handle, float(lam), _ptr(rhs), _ptr(out), int(reps), C.byref(t),
                                     _stream(stream)), "fdi_plan_autotune")
-    return c.value, t.value
+    return t.value
 
 
 def set_graphs(plan: Plan, on=True):

@@ -68,6 +68,11 @@ def test_invalid_arguments_rejected_without_touching_the_gpu(lib):
     with pytest.raises(fdi.FdiError) as e:
         fdi.plan_create(faces, (8, 8, 8), grid=fdi.GRID_MAC, thomas_axis=1)
     assert e.value.status == fdi.ERR_UNSUPPORTED
+    # the two reserved precision modes are not built and are refused at creation
+    for prec in (fdi.PREC_MIXED_TF32, fdi.PREC_MIXED_BF16):
+        with pytest.raises(fdi.FdiError) as e:
+            fdi.plan_create(faces, (8, 8, 8), prec=prec)
+        assert e.value.status == fdi.ERR_UNSUPPORTED
     # null plan handles
     assert lib.fdi_helmholtz_solve(None, 1.0, None, None, None) == fdi.ERR_INVALID_ARG
     assert lib.fdi_plan_destroy(None) == fdi.ERR_INVALID_ARG
@@ -76,7 +81,7 @@ def test_invalid_arguments_rejected_without_touching_the_gpu(lib):
     assert lib.fdi_field_solve_host(None, 0, 1.0, 1.0, None, None, 1, None, None) == fdi.ERR_INVALID_ARG
     assert lib.fdi_stokes_solve(None, 1.0, 1.0, None, None, None, None) == fdi.ERR_INVALID_ARG
     for setter in ("fdi_plan_set_krylov", "fdi_plan_set_stokes_preconditioner", "fdi_plan_set_graphs",
-                   "fdi_plan_set_thomas_config", "fdi_plan_set_transform_config", "fdi_plan_enable_timing"):
+                   "fdi_plan_set_thomas_config", "fdi_plan_enable_timing"):
         assert getattr(lib, setter)(None, 0) == fdi.ERR_INVALID_ARG, setter
     assert lib.fdi_plan_set_tolerances(None, 1e-10, 2, 1e-10, 10) == fdi.ERR_INVALID_ARG
     assert lib.fdi_last_launch_count(None, None) == fdi.ERR_INVALID_ARG

@@ -150,3 +150,36 @@ def test_stokes_non_finite_forcing_is_invalid_argument(fdi, which):
     with pytest.raises(fdi.FdiError) as e:
         stokes(fdi, faces, f, prec)
     assert e.value.status == fdi.ERR_INVALID_ARG
+
+
+def test_wait_limit_runs_out_then_plan_recovers(fdi):
+    # The tensor-core transform's roles hand shared-memory stages to one
+    # another through bounded waits.  A limit of one cycle makes the first
+    # wait for a TMA load run out: the kernel drains its issued copies and MMAs,
+    # frees its tensor memory, returns, and the solve reports FDI_ERR_TIMEOUT
+    # (no fault; the context stays usable).  With the default limit restored,
+    # the same plan solves to its tolerance.
+    n = (64, 64, 24)
+    faces = [tanh_faces(n[d], 1.5) for d in range(3)]
+    ops = asm.cell_ops(faces, (D, D, D), (D, D, D))
+    f = rhs_uniform(n[::-1], 5)
+    plan = fdi.plan_create(faces, n, prec=fdi.PREC_MIXED_F16)
+    try:
+        fdi.set_wait_limit(plan, 1)
+        for _ in range(2):  # the flag stays set until the limit is set again
+            with pytest.raises(fdi.FdiError) as e:
+                solve(fdi, plan, 1.0, 1.0, f)
+            assert e.value.status == fdi.ERR_TIMEOUT
+        fdi.set_wait_limit(plan, 0)
+        got, steps, rel, status = solve(fdi, plan, 1.0, 1.0, f)
+        assert status == 0 and rel <= 1e-10, (steps, rel)
+        assert asm.relative_residual(ops, got, f, 1.0) <= 1e-10
+    finally:
+        plan.destroy()
+    plan = fdi.plan_create(faces, n)
+    try:
+        with pytest.raises(fdi.FdiError) as e:
+            fdi.set_wait_limit(plan, -1)
+        assert e.value.status == fdi.ERR_INVALID_ARG
+    finally:
+        plan.destroy()

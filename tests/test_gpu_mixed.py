@@ -149,48 +149,6 @@ def test_bench_workload_256_mixed(fdi):
     assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("cluster", [2, 4])
-@pytest.mark.parametrize("n,rows", [(64, 1000), (256, 300), (100, 130)])
-def test_clustered_transform_matches_fp64(fdi, cluster, n, rows):
-    # the same pass with the transform matrix multicast across a CTA cluster
-    import torch
-    faces = [tanh_faces(n, 1.5), tanh_faces(8, 1.0), tanh_faces(8, 1.0)]
-    plan = fdi.plan_create(faces, (n, 8, 8), prec=fdi.PREC_MIXED_F16)
-    fdi.set_transform_config(plan, cluster)
-    lam, E, Einv = plan.eigen(fdi.FIELD_CELL, 0)
-    p = pitch4(n)
-    x = np.zeros((rows, p), dtype=np.float32)
-    x[:, :n] = np.random.default_rng(3 * n + rows).uniform(-1, 1, (rows, n)).astype(np.float32)
-    xin = torch.from_numpy(x).cuda()
-    out = torch.zeros_like(xin)
-    fdi.apply_transform(plan, fdi.FIELD_CELL, 0, 1, xin, out, rows)
-    torch.cuda.synchronize()
-    got = out.cpu().numpy()[:, :n].astype(np.float64)
-    ref = x[:, :n].astype(np.float64) @ Einv.T
-    scale = np.abs(x[:, :n]).astype(np.float64) @ np.abs(Einv).T
-    plan.destroy()
-    assert (np.abs(got - ref) / scale).max() < 2e-6
-
-
-@pytest.mark.parametrize("cluster", [2, 4])
-def test_clustered_mixed_solve(fdi, cluster):
-    import torch
-    n = (96, 64, 40)
-    faces = box_faces(n, 1.5)
-    ops = asm.cell_ops(faces, (D, D, D), (D, D, D))
-    f = rhs_uniform(n[::-1], 11)
-    plan = fdi.plan_create(faces, n, prec=fdi.PREC_MIXED_F16)
-    fdi.set_transform_config(plan, cluster)
-    rhs = torch.from_numpy(f).cuda()
-    out = torch.empty_like(rhs)
-    fdi.helmholtz_solve(plan, 1.0, rhs, out)
-    torch.cuda.synchronize()
-    _, steps, rel, st = fdi.last_result(plan)
-    plan.destroy()
-    assert st == 0 and rel <= MIXED_TOL
-    assert asm.relative_residual(ops, out.cpu().numpy(), f, 1.0) <= MIXED_TOL
-
-
 def test_mixed_refined_to_fp64_tolerance(fdi):
     # the mixed path with one more refinement step reaches the FP64 path's
     # tolerance (1e-11): 128^3, tanh 2.0, the three Helmholtz lambdas and the

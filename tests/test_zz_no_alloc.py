@@ -25,7 +25,7 @@ def fdi():
     return pkg
 
 
-def _noalloc(fdi, faces, face_kind, bc_lo, bc_hi):
+def _noalloc(fdi, faces, face_kind, bc_lo, bc_hi, with_flag=True):
     import torch
     n = len(faces) - 1
     m = n - 1 if face_kind else n
@@ -35,11 +35,16 @@ def _noalloc(fdi, faces, face_kind, bc_lo, bc_hi):
     f = np.ascontiguousarray(faces, dtype=np.float64)
     conv = C.c_int(-1)
     lib = fdi.fdi.load()
+    stream = torch.cuda.current_stream()
     st = lib.fdi_eigen_noalloc(f.ctypes.data_as(C.POINTER(C.c_double)), n, face_kind, bc_lo, bc_hi,
-                               lam.data_ptr(), E.data_ptr(), Einv.data_ptr(), C.byref(conv),
-                               torch.cuda.current_stream().cuda_stream)
+                               lam.data_ptr(), E.data_ptr(), Einv.data_ptr(), C.byref(conv) if with_flag else None,
+                               stream.cuda_stream)
     assert st == 0, fdi.status_string(st)
-    assert conv.value == 1
+    if with_flag:
+        assert conv.value == 1
+    else:
+        # without the flag the call returns at once; the caller synchronises
+        stream.synchronize()
     return lam.cpu().numpy(), E.cpu().numpy().reshape(m, m), Einv.cpu().numpy().reshape(m, m)
 
 
@@ -76,4 +81,27 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(fdi):
     lib = fdi.fdi.load()
     f = np.linspace(0.0, 1.0, 258)
     st = lib.fdi_eigen_noalloc(f.ctypes.data_as(C.POINTER(C.c_double)), 257, 0, 0, 0, 1, 1, 1, None, None)
+    assert st == fdi.fdi.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("bc,with_flag", [((0, 0), True), ((0, 1), False), ((1, 0), True)])
+def test_noalloc_eigen_wall_kinds(fdi, bc, with_flag):
+    # Dirichlet walls on both sides, and mixed walls (one side zero-flux), of a
+    # cell operator: the wall terms of the operator assembled by the call; the
+    # second case passes no convergence flag and synchronises afterwards
+    n = 97
+    fx = tanh_faces(n, 1.7)
+    faces = [fx, tanh_faces(4, 1.0), tanh_faces(4, 1.0)]
+    plan = fdi.plan_create(faces, (n, 4, 4), (bc[0], 0, 0), (bc[1], 0, 0))
+    ref = plan.eigen(fdi.FIELD_CELL, 0)
+    plan.destroy()
+    for _ in range(2):
+        _compare(_noalloc(fdi, fx, 0, bc[0], bc[1], with_flag), ref)
+
+
+def test_noalloc_rejects_walls_of_a_face_operator(fdi):
+    # the staggered velocity operator has no-slip walls only
+    lib = fdi.fdi.load()
+    f = np.linspace(0.0, 1.0, 11)
+    st = lib.fdi_eigen_noalloc(f.ctypes.data_as(C.POINTER(C.c_double)), 10, 1, 1, 0, 1, 1, 1, None, None)
     assert st == fdi.fdi.ERR_INVALID_ARG
