@@ -367,42 +367,73 @@ def run_batch(fdi, torch, prec, count, reps, stream):
             "points": pts, "worst_rel_residual": worst, "all_converged": ok, "reps": reps}
 
 
+def pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, int(q * len(v)))] if v else None
+
+
 def run_serving(fdi, prec, count, rate_hz, max_n, slots):
     """Serving trace: Poisson arrivals (rate_hz, seed 0) of Stokes-inverse
     requests on stretched no-slip boxes (beta 1.5), cubic n uniform over
     {48, 64, 96, 128, 160, 192, 256} up to max_n, dt log-uniform in [1e-2, 1e3],
-    Re in {100, 1000, 5000}, Gaussian forcing; host arrays in and out.  Requests
-    are submitted at their arrival times into a server with `slots` workers and
-    a 64 GB device budget; p50 / p99 latency (arrival to completion) and
-    throughput."""
+    Re in {100, 1000, 5000}; host arrays in and out, submitted at their
+    arrival times into a server with `slots` workers and a 64 GB device budget.
+    Host memory stays bounded: the Gaussian forcing is one seeded set per grid
+    size, shared read-only by that size's requests, and the outputs come from a
+    pool of buffers per size; a request whose pool buffer is still held by an
+    unfinished request waits for it before submission (counted).  Reported:
+    end-to-end latency (arrival to completion), queueing delay (arrival to
+    start) and service latency (start to completion), overall and per size,
+    and the completion rate over the trace (the sustainable rate when the
+    arrivals exceed it)."""
     rng = np.random.default_rng(0)
     sizes = [v for v in (48, 64, 96, 128, 160, 192, 256) if v <= max_n]
     arrivals = workloads.poisson_arrivals(count, rate_hz, 0)
-    reqs = []
-    for q in range(count):
-        nn = int(rng.choice(sizes))
-        dt = float(10.0 ** rng.uniform(-2.0, 3.0))
-        Re = float(rng.choice([100.0, 1000.0, 5000.0]))
+    draws = [(int(rng.choice(sizes)), float(10.0 ** rng.uniform(-2.0, 3.0)), float(rng.choice([100.0, 1000.0, 5000.0])))
+             for _ in range(count)]
+    pool_len = {256: 6, 192: 8, 160: 12, 128: 16}
+    forcing, pools, owner, used = {}, {}, {}, {}
+    for nn in sorted({d[0] for d in draws}):
         sh = workloads.mac_shapes((nn, nn, nn))
-        f = [np.ascontiguousarray(workloads.rhs_gaussian(sh[c], 3 * q + i)) for i, c in enumerate("uvw")]
-        u = [np.zeros(sh[c]) for c in "uvw"]
-        p = np.zeros(sh["p"])
-        reqs.append(((nn, nn, nn), dt, Re, f, u, p))
+        forcing[nn] = [np.ascontiguousarray(workloads.rhs_gaussian(sh[c], 1000 * nn + i)) for i, c in enumerate("uvw")]
+        pools[nn] = [([np.zeros(sh[c]) for c in "uvw"], np.zeros(sh["p"])) for _ in range(pool_len.get(nn, 32))]
+        used[nn] = 0
     srv = fdi.Server(64 << 30, slots)
     t0 = time.perf_counter()
-    tickets = []
-    for q, (nn, dt, Re, f, u, p) in enumerate(reqs):
+    tickets, waits = [], 0
+    for q, (nn, dt, Re) in enumerate(draws):
         wait = arrivals[q] - (time.perf_counter() - t0)
         if wait > 0:
             time.sleep(wait)
-        tickets.append(srv.submit(nn, 1.5, dt, Re, f, u, p, prec=prec))
+        k = used[nn] % len(pools[nn])
+        used[nn] += 1
+        prev = owner.get((nn, k))
+        if prev is not None and srv.poll(prev)["state"] != 2:
+            srv.poll(prev, wait=True)
+            waits += 1
+        u, p = pools[nn][k]
+        t = srv.submit((nn, nn, nn), 1.5, dt, Re, forcing[nn], u, p, prec=prec)
+        owner[(nn, k)] = t
+        tickets.append(t)
     srv.drain()
+    wall = time.perf_counter() - t0
     res = [srv.poll(t) for t in tickets]
     st = srv.stats()
     srv.close()
-    return {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "throughput_rps": st["throughput_rps"],
-            "completed": st["completed"], "all_converged": all(r["status"] == 0 for r in res),
-            "worst_rel_residual": max(r["rel_residual"] for r in res), "plans_created": st["plans_created"],
+    lat = [r["latency_ms"] for r in res]
+    que = [r["queue_ms"] for r in res]
+    svc = [r["latency_ms"] - r["queue_ms"] for r in res]
+    per = {}
+    for nn in sorted(forcing):
+        s_n = [svc[q] for q in range(count) if draws[q][0] == nn]
+        per[f"{nn}^3"] = {"requests": len(s_n), "service_p50_ms": pct(s_n, 0.5), "service_p99_ms": pct(s_n, 0.99)}
+    return {"completed": st["completed"], "all_converged": all(r["status"] == 0 for r in res),
+            "worst_rel_residual": max(r["rel_residual"] for r in res),
+            "latency_p50_ms": pct(lat, 0.5), "latency_p99_ms": pct(lat, 0.99),
+            "queue_p50_ms": pct(que, 0.5), "queue_p99_ms": pct(que, 0.99),
+            "service_p50_ms": pct(svc, 0.5), "service_p99_ms": pct(svc, 0.99),
+            "completion_rate_rps": st["throughput_rps"], "offered_rate_rps": rate_hz, "trace_s": wall,
+            "submissions_waiting_for_a_buffer": waits, "per_size": per, "plans_created": st["plans_created"],
             "peak_gb": st["peak_bytes"] / 1e9}
 
 
@@ -420,8 +451,10 @@ def main():
     ap.add_argument("--stokes-n", type=int, default=64, help="Stokes latency grid (0: skip)")
     ap.add_argument("--stokes-reps", type=int, default=10)
     ap.add_argument("--batch", type=int, default=64, help="batched uneven-grid solves per batch (0: skip)")
-    ap.add_argument("--serve", type=int, default=40, help="serving-trace requests (0: skip)")
-    ap.add_argument("--serve-max-n", type=int, default=128, help="largest cubic grid in the serving sample")
+    ap.add_argument("--serve", type=int, default=2000, help="serving-trace requests, mixed precision (0: skip)")
+    ap.add_argument("--serve-fp64", type=int, default=200,
+                    help="serving-trace requests of the FP64 arm (the first ones of the same trace; 0: skip)")
+    ap.add_argument("--serve-max-n", type=int, default=256, help="largest cubic grid in the serving trace")
     ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
     n = (args.n, args.n, args.n)
@@ -555,13 +588,16 @@ def main():
                 batch[name] = {"error": str(e)}
     serving = None
     if args.serve > 0:
-        serving = {"config": f"{args.serve} Stokes-inverse requests, Poisson arrivals at 200/s (seed 0), cubic n "
-                             f"from {{48..256}} up to {args.serve_max_n}, dt log-uniform [1e-2,1e3], "
-                             f"Re in {{100,1000,5000}}, beta 1.5, {args.serve_slots} slots, 64 GB budget"}
+        serving = {"config": f"Stokes-inverse requests ({args.serve} mixed, the first {args.serve_fp64} of the "
+                             f"same trace FP64), Poisson arrivals at 200/s (seed 0), cubic n from {{48..256}} up to "
+                             f"{args.serve_max_n}, dt log-uniform [1e-2,1e3], Re in {{100,1000,5000}}, beta 1.5, "
+                             f"{args.serve_slots} slots, 64 GB budget, tolerance 1e-10 (mixed) / 1e-11 (FP64)"}
         for name in args.arms.split(","):
+            count = args.serve if name == "mixed" else args.serve_fp64
+            if count <= 0:
+                continue
             try:
-                serving[name] = run_serving(fdi, precs[name][0], args.serve, 200.0, args.serve_max_n,
-                                            args.serve_slots)
+                serving[name] = run_serving(fdi, precs[name][0], count, 200.0, args.serve_max_n, args.serve_slots)
             except fdi.FdiError as e:
                 serving[name] = {"error": str(e)}
     cpu = None

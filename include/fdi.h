@@ -115,6 +115,38 @@ fdi_status fdi_plan_create(const double* const faces[3], const int n[3], const f
                            const fdi_bc bc_hi[3], fdi_grid grid, fdi_precision prec, int thomas_axis,
                            fdi_plan** out);
 
+/* Create a plan on a cylindrical grid (Sec. 6, Eq. 41-46): the Helmholtz /
+ * Poisson operator sigma*I - lambda*(D_rr + (1/r^2) D_thth + D_zz) in finite
+ * volumes, on cells (r_i, theta_j, z_k) of an annulus or a full cylinder.
+ *   rfaces   host, nr+1 ascending radial faces, rfaces[0] >= 0; rfaces[0] = 0
+ *            makes the inner face the axis (a face of zero area: no flux, and
+ *            bc_r_in is ignored)
+ *   ntheta   uniform cells on the full circle, periodic
+ *   zfaces   host, nz+1 ascending axial faces
+ *   bc_*     wall types of the inner / outer radius and the two ends
+ *   tpf      0: TPT, eigen transforms along theta and z and the Thomas
+ *            algorithm along r per pair of modes (Eq. 42-44); 1: TPF, one
+ *            radial eigen decomposition per theta mode (Eq. 45) and a divide
+ *            (Eq. 46), FP64 plans only (else FDI_ERR_UNSUPPORTED)
+ * Finite-volume reading (the paper prints no stencil): annular cell areas
+ * A_i = (rho_{i+1}^2 - rho_i^2)/2, radial flux through rho_{i+1} equal to
+ * rho_{i+1} (u_{i+1} - u_i) / (c_{i+1} - c_i) with c_i the cell centres, a
+ * Dirichlet wall at half a cell, and the 1/r^2 of Eq. 41 as
+ * g_i = (rho_{i+1} - rho_i) / (c_i A_i) per radial cell.  The theta
+ * eigenbasis is the discrete Fourier basis in closed form; the z and r ones
+ * are computed on the GPU as for fdi_plan_create.
+ * Fields are FP64, C order [nz][ntheta][nr] (r fastest).  Limits:
+ * 2 <= nr, nz <= 256, 3 <= ntheta <= 256.  Solves: fdi_helmholtz_solve,
+ * fdi_laplace_solve and fdi_field_solve (FDI_FIELD_CELL) and their host and
+ * batched forms; the singular zero-flux Laplacian (axis or zero-flux inner
+ * wall, zero-flux outer wall and ends, sigma = 0) returns
+ * FDI_ERR_UNSUPPORTED.  fdi_plan_eigen takes d = 0 (r), 1 (theta), 2 (z).
+ * prec: FDI_PREC_FP64 or FDI_PREC_MIXED_F16.  Synchronous; *out = NULL on
+ * error. */
+fdi_status fdi_plan_create_cyl(const double* rfaces, int nr, int ntheta, const double* zfaces, int nz,
+                               fdi_bc bc_r_in, fdi_bc bc_r_out, fdi_bc bc_z_lo, fdi_bc bc_z_hi, fdi_precision prec,
+                               int tpf, fdi_plan** out);
+
 /* Release every device buffer of the plan (synchronises the device first). */
 fdi_status fdi_plan_destroy(fdi_plan* plan);
 

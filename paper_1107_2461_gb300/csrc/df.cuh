@@ -62,6 +62,21 @@ __device__ __forceinline__ double f2d(float f) {
   return __longlong_as_double((long long)d);
 }
 
+// The same conversion for code that a whole warp executes together (every
+// lane must call it): no per-lane branch for normal numbers and zero, whose 31
+// exponent-and-significand bits are rebased from bias 127 to 1023 by one
+// 64-bit add and shifted into place; a warp holding a subnormal, infinite or
+// NaN value takes the FP64-pipe conversion on every lane.
+__device__ __forceinline__ double f2d_warp(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t mag = b & 0x7fffffffu;
+  const uint32_t e = mag >> 23;
+  if (__any_sync(0xffffffffu, (e == 0u && mag != 0u) || e == 255u)) return (double)f;
+  const uint64_t sign = (uint64_t)(b & 0x80000000u) << 32;
+  const uint64_t d = (((uint64_t)mag + (896ull << 23)) << 29) | sign;
+  return __longlong_as_double((long long)(mag == 0u ? sign : d));
+}
+
 // hi + lo as the nearest FP64 (one FP64 add)
 __device__ __forceinline__ double to_f64(F2 a) { return f2d(a.hi) + f2d(a.lo); }
 

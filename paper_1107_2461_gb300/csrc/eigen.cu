@@ -178,10 +178,31 @@ __global__ void __launch_bounds__(kEigThreads) k_eigen(const EigenJob* jobs, int
 
 }  // namespace
 
+namespace {
+fdi_status run_jobs(const std::vector<EigenJob>& jobs, cudaStream_t s, int* d_err);
+}
+
 fdi_status eigen_decompose_all(const std::vector<Axis*>& axes, cudaStream_t s, int* d_err) {
   std::vector<EigenJob> jobs;
   for (Axis* ax : axes)
-    jobs.push_back(EigenJob{ax->n, ax->zero_flux ? 1 : 0, ax->m, ax->kd, ax->ko, ax->lam, ax->E, ax->Einv});
+    if (!ax->periodic)
+      jobs.push_back(EigenJob{ax->n, ax->zero_flux ? 1 : 0, ax->m, ax->kd, ax->ko, ax->lam, ax->E, ax->Einv});
+  return run_jobs(jobs, s, d_err);
+}
+
+fdi_status eigen_decompose_batch(int count, int n, const double* m, const double* kd_all, const double* ko,
+                                 bool zero_flux0, double* lam_all, double* E_all, double* Einv_all, cudaStream_t s,
+                                 int* d_err) {
+  std::vector<EigenJob> jobs;
+  for (int q = 0; q < count; ++q)
+    jobs.push_back(EigenJob{n, (q == 0 && zero_flux0) ? 1 : 0, m, kd_all + (size_t)q * n, ko,
+                            lam_all + (size_t)q * n, E_all + (size_t)q * n * n, Einv_all + (size_t)q * n * n});
+  return run_jobs(jobs, s, d_err);
+}
+
+namespace {
+fdi_status run_jobs(const std::vector<EigenJob>& jobs, cudaStream_t s, int* d_err) {
+  if (jobs.empty()) return FDI_OK;
   EigenJob* d_jobs = nullptr;
   FDI_CUDA_TRY(cudaMalloc(&d_jobs, jobs.size() * sizeof(EigenJob)));
   cudaError_t e = cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(EigenJob),
@@ -198,6 +219,7 @@ fdi_status eigen_decompose_all(const std::vector<Axis*>& axes, cudaStream_t s, i
   }
   return FDI_OK;
 }
+}  // namespace
 
 // ---------------------------------------------------------------------------
 // Allocation-free variant of the eigen decomposition.

@@ -32,6 +32,7 @@ struct KryState;     // Krylov scalars of the Stokes pressure solve (stokes.cu)
 struct Axis {
   int n = 0;
   bool zero_flux = false;           // both walls zero-flux: Lambda_0 = 0 exactly
+  bool periodic = false;            // uniform periodic direction (cylindrical theta): closed-form eigenbasis
   // device arrays
   double* m = nullptr;              // M diagonal (control-volume widths), n
   double* kd = nullptr;             // K diagonal, n
@@ -119,6 +120,17 @@ struct fdi_plan {
   int nextra = 0;
   cudaStream_t sstream[3] = {nullptr, nullptr, nullptr};  // streams of those solves
   cudaEvent_t sfork = nullptr, sjoin[3] = {nullptr, nullptr, nullptr};
+  // cylindrical plans (Sec. 6, Eq. 41-46): internal x = z, y = theta
+  // (periodic), z = r; the theta eigenvalue carries the radial factor g_i (the
+  // discrete 1/r^2) in the Thomas sweep and in the residual
+  bool cyl = false;
+  double* cyl_wy = nullptr;         // FP64 [n_r]: A_i g_i, Thomas weight of the theta eigenvalue
+  double* cyl_wres = nullptr;       // FP64 [n_r]: g_i / h_theta^2, theta flux weight of radial cell i
+  float* cyl_wy_f = nullptr;        // FP32 copy of cyl_wy (mixed Thomas sweep)
+  float2* cyl_wres_df = nullptr;    // double-float copy of cyl_wres (mixed residual)
+  double* cyl_Er = nullptr;         // TPF: per theta mode j the radial E_{r,j} [n_theta][n_r][n_r] (Eq. 45)
+  double* cyl_Eri = nullptr;        //      and E_{r,j}^{-1}
+  double* cyl_lr = nullptr;         //      and its eigenvalues [n_theta][n_r]
   int stokes_precond = 1;           // 0: L_p^{-1} (paper), 1: L_p^{-1} - lambda I
   int krylov = 0;                   // 0: BiCGstab, 1: BiCGstab(2) (the paper's solver)
   double* kpartials = nullptr;
@@ -282,13 +294,24 @@ fdi_status batch_solve(fdi_plan* const* plans, const double* lambdas, const doub
                        int count, cudaStream_t s);
 
 // plan-time eigen decomposition of the symmetric tridiagonal M^{-1/2} K M^{-1/2}
+// (periodic axes are skipped: their eigenbasis is set in closed form)
 fdi_status eigen_decompose_all(const std::vector<Axis*>& axes, cudaStream_t s, int* d_err);
+// `count` operators of size n sharing M and the off-diagonal of K, diagonal
+// kd_all + q n for operator q; outputs at lam_all + q n, E_all / Einv_all + q n^2;
+// operator 0 is given the exact null pair when zero_flux0
+fdi_status eigen_decompose_batch(int count, int n, const double* m, const double* kd_all, const double* ko,
+                                 bool zero_flux0, double* lam_all, double* E_all, double* Einv_all, cudaStream_t s,
+                                 int* d_err);
 
 // FP64 path launchers (kernels_f64.cu)
 fdi_status launch_lines_f64(fdi_plan* p, const double* in, double* out, const double* T, int nin,
                             int nout, long long lines, bool accumulate, const int* skip, cudaStream_t s);
 fdi_status launch_slab_f64(fdi_plan* p, const double* in, double* out, const double* T, int nin,
                            int nout, long long ncols, int batch, const int* skip, cudaStream_t s);
+fdi_status launch_modes_f64(fdi_plan* p, const double* in, double* out, const double* T_all, int n, int nx,
+                            int ny, const int* skip, cudaStream_t s);
+fdi_status launch_divide_modes_f64(fdi_plan* p, const Field& f, double sigma, double lambda, double* data,
+                                  const int* skip, cudaStream_t s);
 fdi_status launch_thomas_f64(fdi_plan* p, const Field& f, double sigma, double lambda, const double* in,
                              double* out, double* scratch, const int* skip, cudaStream_t s);
 fdi_status launch_divide_f64(fdi_plan* p, const Field& f, double sigma, double lambda, double* data,

@@ -82,15 +82,22 @@ __global__ void __launch_bounds__(256) k_lines_f64(const double* __restrict__ A,
   }
 }
 
+// Element (j, c) of the input of batch b at A[b * zin + j * rs + c], of the
+// output C[b * zout + k * rs + c]; the matrix of batch b is T + b * tz (tz = 0:
+// one matrix for every batch).  A y pass over z-slabs has rs = ncols, zin =
+// nin * ncols; a per-mode transform (cylindrical TPF: one radial matrix per
+// theta mode) has batch = mode, rs = the row stride of the field, tz = nin * nout.
 __global__ void __launch_bounds__(256) k_slab_f64(const double* __restrict__ A, double* __restrict__ C,
                                                   const double* __restrict__ T, int nin, int nout,
-                                                  long long ncols, const int* __restrict__ skip) {
+                                                  long long ncols, long long rs, long long zin, long long zout,
+                                                  long long tz, const int* __restrict__ skip) {
   if (skip && *skip) return;
   __shared__ double As[TK][TB + 1];  // T tile [j][k]
   __shared__ double Bs[TK][TB + 1];  // data tile [j][c]
   const long long b = blockIdx.z;
-  A += b * (long long)nin * ncols;
-  C += b * (long long)nout * ncols;
+  A += b * zin;
+  C += b * zout;
+  T += b * tz;
   const long long c0 = (long long)blockIdx.x * TB;
   const int k0 = blockIdx.y * TB;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -108,7 +115,7 @@ __global__ void __launch_bounds__(256) k_slab_f64(const double* __restrict__ A, 
       int cc = threadIdx.x % TB, jr = threadIdx.x / TB + 4 * r;
       long long col = c0 + cc;
       int j2 = j0 + jr;
-      Bs[jr][cc] = (col < ncols && j2 < nin) ? A[(long long)j2 * ncols + col] : 0.0;
+      Bs[jr][cc] = (col < ncols && j2 < nin) ? A[(long long)j2 * rs + col] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -133,7 +140,7 @@ __global__ void __launch_bounds__(256) k_slab_f64(const double* __restrict__ A, 
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       long long col = c0 + tx + 16 * c;
-      if (col < ncols) C[(long long)k * ncols + col] = acc[q][c];
+      if (col < ncols) C[(long long)k * rs + col] = acc[q][c];
     }
   }
 }
@@ -148,6 +155,7 @@ struct ThomasArgs {
   const double* mz;
   const double* kdz;
   const double* koz;
+  const double* wy;  // per z: weight of the y eigenvalue (cylindrical theta: A_i g_i); null: M_z
   double sigma, lambda;
   int singular_possible;  // sigma == 0 and zero-flux walls everywhere
 };
@@ -159,7 +167,10 @@ __global__ void __launch_bounds__(128) k_thomas_f64(ThomasArgs a, const int* __r
   if (l >= NL) return;
   const int i = (int)(l % a.nx), j = (int)(l / a.nx);
   const double lab = a.lamx[i] + a.lamy[j];
-  const double s = a.sigma - a.lambda * lab;
+  // the y eigenvalue takes its own weight on cylindrical plans (Eq. 44: the
+  // theta eigenvalue multiplies the discrete 1/r^2 of the radial cell)
+  const double s = a.sigma - a.lambda * (a.wy ? a.lamx[i] : lab);
+  const double ly = a.wy ? a.lambda * a.lamy[j] : 0.0;
   const int nz = a.nz;
   const double lam = a.lambda;
   if (!(a.singular_possible && lab == 0.0)) {
@@ -168,6 +179,7 @@ __global__ void __launch_bounds__(128) k_thomas_f64(ThomasArgs a, const int* __r
       double lo = (k > 0) ? -lam * a.koz[k - 1] : 0.0;
       double up = (k + 1 < nz) ? -lam * a.koz[k] : 0.0;
       double di = s * a.mz[k] - lam * a.kdz[k];
+      if (a.wy) di -= ly * a.wy[k];
       double inv = 1.0 / (di - lo * cprev);
       cprev = up * inv;
       dprev = (a.mz[k] * a.in[k * NL + l] - lo * dprev) * inv;
@@ -228,12 +240,29 @@ __global__ void k_divide_f64(double* __restrict__ data, int nx, int ny, int nz, 
   }
 }
 
+// cylindrical TPF (Eq. 46): data [k][j][i] with k the radial mode of theta
+// mode j; u /= sigma - lam (Lx_i + Lr_{j,k})
+__global__ void k_divide_modes_f64(double* __restrict__ data, int nx, int ny, int nz, const double* __restrict__ lx,
+                                   const double* __restrict__ lr, double sigma, double lambda,
+                                   const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const long long P = (long long)nx * ny * nz;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < P;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(p % nx);
+    const long long t = p / nx;
+    const int j = (int)(t % ny), k = (int)(t / ny);
+    data[p] = data[p] / (sigma - lambda * (lx[i] + lr[(long long)j * nz + k]));
+  }
+}
+
 struct StencilArgs {
   int nx, ny, nz;
   const double* wp[3];
   const double* wm[3];
   const double* w0[3];
   const double* m[3];
+  const double* wyk;  // periodic y with the flux weight wyk[k] of plane k (cylindrical theta); null otherwise
 };
 
 __device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
@@ -278,11 +307,18 @@ __global__ void __launch_bounds__(kResThreads) k_residual_f64(StencilArgs g, con
     long long t = p / nx;
     int j = (int)(t % ny), k = (int)(t / ny);
     double uc = u[p];
-    double lx = g.w0[0][i] * uc, ly = g.w0[1][j] * uc, lz = g.w0[2][k] * uc;
+    double lx = g.w0[0][i] * uc, ly = 0.0, lz = g.w0[2][k] * uc;
     if (i + 1 < nx) lx += g.wp[0][i] * (u[p + sx] - uc);
     if (i > 0) lx += g.wm[0][i] * (u[p - sx] - uc);
-    if (j + 1 < ny) ly += g.wp[1][j] * (u[p + sy] - uc);
-    if (j > 0) ly += g.wm[1][j] * (u[p - sy] - uc);
+    if (g.wyk) {
+      const long long pn = j + 1 < ny ? p + sy : p - (ny - 1) * sy;
+      const long long ps = j > 0 ? p - sy : p + (ny - 1) * sy;
+      ly = g.wyk[k] * ((u[pn] - uc) + (u[ps] - uc));
+    } else {
+      ly = g.w0[1][j] * uc;
+      if (j + 1 < ny) ly += g.wp[1][j] * (u[p + sy] - uc);
+      if (j > 0) ly += g.wm[1][j] * (u[p - sy] - uc);
+    }
     if (k + 1 < nz) lz += g.wp[2][k] * (u[p + sz] - uc);
     if (k > 0) lz += g.wm[2][k] * (u[p - sz] - uc);
     double bb = b[p] - mb;
@@ -384,6 +420,7 @@ StencilArgs stencil_args(const Field& f) {
     g.w0[d] = f.ax[d]->w0;
     g.m[d] = f.ax[d]->m;
   }
+  g.wyk = nullptr;
   return g;
 }
 
@@ -405,7 +442,19 @@ fdi_status launch_slab_f64(fdi_plan* p, const double* in, double* out, const dou
                            long long ncols, int batch, const int* skip, cudaStream_t s) {
   FDI_KTIMER(p, batch > 1 ? "transform_y_f64" : "transform_z_f64", s);
   dim3 grid((unsigned)((ncols + TB - 1) / TB), (unsigned)((nout + TB - 1) / TB), (unsigned)batch);
-  k_slab_f64<<<grid, 256, 0, s>>>(in, out, T, nin, nout, ncols, skip);
+  k_slab_f64<<<grid, 256, 0, s>>>(in, out, T, nin, nout, ncols, ncols, (long long)nin * ncols,
+                                  (long long)nout * ncols, 0LL, skip);
+  FDI_LAUNCH_CHECK(p);
+  return FDI_OK;
+}
+
+fdi_status launch_modes_f64(fdi_plan* p, const double* in, double* out, const double* T_all, int n, int nx,
+                            int ny, const int* skip, cudaStream_t s) {
+  // field [n][ny][nx]; for every y index j (a theta mode) the n x n matrix
+  // T_all + j n^2 contracts the outer index
+  FDI_KTIMER(p, "transform_r_modes_f64", s);
+  dim3 grid((unsigned)((nx + TB - 1) / TB), (unsigned)((n + TB - 1) / TB), (unsigned)ny);
+  k_slab_f64<<<grid, 256, 0, s>>>(in, out, T_all, n, n, nx, (long long)nx * ny, nx, nx, (long long)n * n, skip);
   FDI_LAUNCH_CHECK(p);
   return FDI_OK;
 }
@@ -425,6 +474,7 @@ fdi_status launch_thomas_f64(fdi_plan* p, const Field& f, double sigma, double l
   a.mz = f.ax[2]->m;
   a.kdz = f.ax[2]->kd;
   a.koz = f.ax[2]->ko;
+  a.wy = p->cyl_wy;
   a.sigma = sigma;
   a.lambda = lambda;
   a.singular_possible = (sigma == 0.0 && f.zero_flux_all) ? 1 : 0;
@@ -444,12 +494,23 @@ fdi_status launch_divide_f64(fdi_plan* p, const Field& f, double sigma, double l
   return FDI_OK;
 }
 
+fdi_status launch_divide_modes_f64(fdi_plan* p, const Field& f, double sigma, double lambda, double* data,
+                                  const int* skip, cudaStream_t s) {
+  FDI_KTIMER(p, "divide_f64", s);
+  k_divide_modes_f64<<<152 * 8, 256, 0, s>>>(data, f.n[0], f.n[1], f.n[2], f.ax[0]->lam, p->cyl_lr, sigma, lambda,
+                                            skip);
+  FDI_LAUNCH_CHECK(p);
+  return FDI_OK;
+}
+
 fdi_status launch_residual_f64(fdi_plan* p, const Field& f, double sigma, double lambda, const double* b,
                                const double* u, double* r, bool subtract_mean, const int* skip,
                                cudaStream_t s) {
   FDI_KTIMER(p, "residual_f64", s);
-  k_residual_f64<<<kResBlocks, kResThreads, 0, s>>>(stencil_args(f), b, u, r, sigma, lambda, p->d_status,
-                                                    subtract_mean ? 1 : 0, p->partials, skip);
+  StencilArgs g = stencil_args(f);
+  g.wyk = p->cyl_wres;
+  k_residual_f64<<<kResBlocks, kResThreads, 0, s>>>(g, b, u, r, sigma, lambda, p->d_status, subtract_mean ? 1 : 0,
+                                                    p->partials, skip);
   FDI_LAUNCH_CHECK(p);
   return FDI_OK;
 }

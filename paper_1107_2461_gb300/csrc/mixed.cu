@@ -67,6 +67,8 @@ struct ResidArgs {
   const float2* wm[3];
   const float2* w0[3];
   const float2* m[3];
+  const float2* wy;     // periodic-y plans: lambda-scaled y flux weight per plane (null otherwise)
+  double fast_limit;    // MODE 1: plain FP32 body when ||r_1|| / ||b|| <= fast_limit (0: never)
   float2 sigma, lambda;
   int sig_mode;         // 0: sigma = 0, 1: sigma = 1, 2: general sigma
   const double* b;
@@ -95,21 +97,34 @@ __device__ __forceinline__ df::F2 ld2(const float2* p) {
   return df::make(v.x, v.y);
 }
 
-// z-marching residual: a block covers a 32 (x) x 8 (y) tile of columns and a
-// range of planes; each thread keeps x at k-1, k, k+1 in registers (the loads
-// of the next plane are issued before the current one is computed) and reuses
-// the exact z difference of the face below from the previous plane.  Work per
-// block is fixed, so the reduction order is too.
+// z-marching residual: a block of 32 (x) x 8 (y) threads covers 64 x 8
+// columns; each thread a pair of x-neighbours (i0, i0 + 1) of one row j, over a
+// range of planes.  Per plane a thread holds its pair at planes k and k + 1 and
+// the pairs of rows j - 1 and j + 1 at plane k (the loads of the next plane
+// are issued before the current one is computed; with VEC one 8-byte access
+// per pair); the x face inside the pair is differenced once for both points,
+// the z face below is the previous plane's upper face, and the x neighbours
+// outside the pair come from the neighbouring lanes.  Walls need no branch:
+// the flux weights are zero across a wall and the clamped neighbour index
+// gives an exact zero difference there; only the Dirichlet wall term (nonzero
+// next to a wall) is added under a per-thread flag.  Work per block is fixed,
+// so the reduction order is too.
 //
 // Arithmetic: x = xh + xl (double-float).  With the flux weights already
 // multiplied by lambda (w' = lambda w, double-float), lambda L x = L'xh + L'xl;
-// L'xh is formed exactly term by term (two-difference of the float values, FMA
-// two-product with the double-float weight) and summed with two-sum, the
-// rounding errors and low parts deferred to an FP32 companion; L'xl is plain
-// FP32 (it is 2^-24 smaller).  b and -sigma x enter the same accumulator, and
-// the FP32 residual is its rounded value: r is stored in FP32, so only the
-// cancellation inside the sum needs the extra precision.
+// each flux of L'xh is formed exactly (two-difference of the float values,
+// FMA two-product with the weight's high part) and its high part summed with
+// two-sum; the rounding errors, the products with the weights' low parts and
+// with the differences' low parts go straight into the FP32 companion sum by
+// FMA; L'xl is plain FP32 (it is 2^-24 smaller).  b and -sigma x enter the
+// same accumulator, and the FP32 residual is its rounded value: r is stored in
+// FP32, so only the cancellation inside the sum needs the extra precision.
+//
+// CYL: the y direction is periodic (rows wrap around) and its flux weight is
+// one value per plane, wy[k] (the cylindrical theta direction, whose flux
+// carries the radial factor of the plane).
 constexpr int kResTX = 32, kResTY = 8, kResZChunk = 16;  // planes per block (at most)
+constexpr int kResBX = 2 * kResTX;                       // x columns per block
 
 struct Acc {
   float h, l;  // unnormalised double-float accumulator
@@ -133,11 +148,76 @@ __device__ __forceinline__ Diff two_diff(float a, float c) {
   return Diff{d, (a - (d - bb)) - (c + bb)};
 }
 
-// s += w * (d + dl) for a double-float weight w
+__device__ __forceinline__ Diff neg(Diff t) { return Diff{-t.d, -t.dl}; }
+
+// s += w * (d + dl) for a double-float weight w: the high product enters by
+// two-sum, its exact rounding error and the two small cross products by FMA
+// into the low part
 __device__ __forceinline__ void acc_flux(Acc& s, float2 w, Diff t) {
   const float p = w.x * t.d;
-  const float e = fmaf(w.x, t.d, -p) + fmaf(w.x, t.dl, w.y * t.d);
-  acc_add(s, p, e);
+  const float e = fmaf(w.x, t.d, -p);
+  const float tt = s.h + p;
+  const float bb = tt - s.h;
+  float l = fmaf(w.x, t.dl, s.l);
+  l = fmaf(w.y, t.d, l);
+  s.l = l + (((s.h - (tt - bb)) + (p - bb)) + e);
+  s.h = tt;
+}
+
+// Plain FP32 forms of the same steps, for the correction residual when the
+// first residual is small (FAST): the difference rounded once, the flux
+// product added by FMA to the high part, other terms added in FP32.
+template <bool FAST>
+__device__ __forceinline__ Diff diff_of(float a, float c) {
+  if (FAST) return Diff{a - c, 0.f};
+  return two_diff(a, c);
+}
+
+template <bool FAST>
+__device__ __forceinline__ void flux_of(Acc& s, float2 w, Diff t) {
+  if (FAST)
+    s.h = fmaf(w.x, t.d, s.h);
+  else
+    acc_flux(s, w, t);
+}
+
+template <bool FAST>
+__device__ __forceinline__ void add_of(Acc& s, float ph, float pl) {
+  if (FAST) {
+    s.h += ph;
+    s.l += pl;
+  } else {
+    acc_add(s, ph, pl);
+  }
+}
+
+// one x pair of FP32 values (hi) and, for LO, of the low plane
+struct Pair {
+  float a, b;     // points i0, i0 + 1
+  float la, lb;   // low parts (LO only)
+};
+
+template <bool VEC, bool LO>
+__device__ __forceinline__ Pair ld_pair(const float* hi, const float* lo, int o, int d1) {
+  Pair v{0.f, 0.f, 0.f, 0.f};
+  if (VEC) {
+    const float2 h = *reinterpret_cast<const float2*>(hi + o);
+    v.a = h.x;
+    v.b = h.y;
+    if (LO) {
+      const float2 l = *reinterpret_cast<const float2*>(lo + o);
+      v.la = l.x;
+      v.lb = l.y;
+    }
+  } else {
+    v.a = hi[o];
+    v.b = hi[o + d1];
+    if (LO) {
+      v.la = lo[o];
+      v.lb = lo[o + d1];
+    }
+  }
+  return v;
 }
 
 // Two residual passes share this body.
@@ -150,172 +230,304 @@ __device__ __forceinline__ void acc_flux(Acc& s, float2 w, Diff t) {
 // SIG: 0 sigma = 0, 1 sigma = 1, 2 general sigma.  MEAN: zero-flux Laplace
 // problem (MODE 0 subtracts the volume-weighted mean of b; volume-weighted
 // sums of the solution H (+ L) are reduced).  OUT: write the FP64 solution
-// H + L.
-// INT: every column of the block has both x and both y neighbours and no
-// x / y wall term (blocks away from the side walls), so the per-column
-// neighbour tests drop out.
-template <int MODE, int SIG, bool LO, bool MEAN, bool OUT, bool INT>
+// H + L.  VEC: nx even and 16-byte aligned FP64 arrays, pairs moved by vector
+// accesses.
+template <int MODE, int SIG, bool LO, bool MEAN, bool OUT, bool CYL, bool VEC, bool FAST>
 __device__ __forceinline__ void resid_body(const ResidArgs& a, double* sh) {
   const int nx = a.nx, ny = a.ny, nz = a.nz;
-  const long long sy = nx, sz = (long long)nx * ny;
   const int lane = threadIdx.x, wy = threadIdx.y;
-  const int i = blockIdx.x * kResTX + lane, j = blockIdx.y * kResTY + wy;
+  const int i0 = 2 * (blockIdx.x * kResTX + lane);
+  const int j = blockIdx.y * kResTY + wy;
   const int k0 = blockIdx.z * a.zchunk, k1 = min(nz, k0 + a.zchunk);
-  const bool act = i < nx && j < ny;
-  const int ic = min(i, nx - 1), jc = min(j, ny - 1);
+  const bool act0 = j < ny && i0 < nx, act1 = j < ny && i0 + 1 < nx;
+  // clamped indices keep every load in bounds; a clamped neighbour is the
+  // point itself (zero difference) and its flux weight is zero (a wall)
+  const int ia = VEC ? min(i0, nx - 2) : min(i0, nx - 1);
+  const int d1 = (VEC || ia + 1 < nx) ? 1 : 0;  // second point of the pair (scalar path)
+  const int jc = min(j, ny - 1);
+  const int js = jc > 0 ? jc - 1 : (CYL ? ny - 1 : 0);
+  const int jn = jc + 1 < ny ? jc + 1 : (CYL ? 0 : ny - 1);
+  // x of the value lane 31 needs east of its pair and lane 0 west of its pair
+  const int ie = lane == kResTX - 1 ? min(i0 + 2, nx - 1) : (lane == 0 ? max(i0 - 1, 0) : ia);
+  const long long oc = (long long)jc * nx + ia, os = (long long)js * nx + ia, on = (long long)jn * nx + ia;
+  const long long oe = (long long)jc * nx + ie;
+  const long long orr_ = (long long)jc * a.r_pitch + ia;
   float mean_h = 0.f, mean_l = 0.f;
   if (MODE == 0 && MEAN) {
     const df::F2 mb = df::from_f64(a.st->mean_b);
     mean_h = -mb.hi;
     mean_l = -mb.lo;
   }
-  const float2 wpx = a.wp[0][ic], wmx = a.wm[0][ic], wpy = a.wp[1][jc], wmy = a.wm[1][jc];
-  const float2 w0x = a.w0[0][ic], w0y = a.w0[1][jc];
-  const bool wall_xy = !INT && (w0x.x != 0.f || w0y.x != 0.f);
-  df::F2 Vxy = df::make(0.f, 0.f);
-  if (MEAN) Vxy = df::mul(ld2(a.m[0] + ic), ld2(a.m[1] + jc));
-  const bool hx = INT || i + 1 < nx, lx = INT || i > 0, hy = INT || j + 1 < ny, ly = INT || j > 0;
-  const bool ex = lane == kResTX - 1 && hx, wx = lane == 0 && lx;
+  const int ib = ia + d1;
+  const float2 wpxa = a.wp[0][ia], wmxa = a.wm[0][ia], wpxb = a.wp[0][ib], wmxb = a.wm[0][ib];
+  float2 wpy = make_float2(0.f, 0.f), wmy = wpy;
+  float2 w0y = make_float2(0.f, 0.f);
+  if (!CYL) {
+    wpy = a.wp[1][jc];
+    wmy = a.wm[1][jc];
+    w0y = a.w0[1][jc];
+  }
+  const float2 w0xa = a.w0[0][ia], w0xb = a.w0[0][ib];
+  const bool wall_xy = w0xa.x != 0.f || w0xb.x != 0.f || w0y.x != 0.f;
+  df::F2 Va = df::make(0.f, 0.f), Vb = Va;
+  if (MEAN) {
+    const df::F2 my = ld2(a.m[1] + jc);
+    Va = df::mul(ld2(a.m[0] + ia), my);
+    Vb = df::mul(ld2(a.m[0] + ib), my);
+  }
   float srr = 0.f, sbb = 0.f, rmax = 0.f;
   df::F2 svb = df::make(0.f, 0.f), sv = df::make(0.f, 0.f);
-  const float2 z2 = make_float2(0.f, 0.f);
-  const long long col = (long long)jc * nx + ic;
-  // the field the stencil acts on: H (MODE 0) or L (MODE 1), as (hi, lo)
-  const float* uq = (MODE == 0 ? a.xh : a.xl) + (long long)k0 * sz + col;
-  const float* uql = (MODE == 1 && LO) ? a.xll + (long long)k0 * sz + col : nullptr;
-  auto ldu = [&](long long o) { return make_float2(uq[o], (MODE == 1 && LO) ? uql[o] : 0.f); };
-  const float* hq = (MODE == 1 && (OUT || MEAN)) ? a.xh + (long long)k0 * sz + col : nullptr;
-  const double* bq = MODE == 0 ? a.b + (long long)k0 * sz + col : nullptr;
-  const long long rp0 = ((long long)k0 * ny + jc) * a.r_pitch + ic;
-  const float* r1h = MODE == 1 ? a.r1 + rp0 : nullptr;
-  const float* r1l = MODE == 1 ? a.r1_lo + rp0 : nullptr;
-  float* rq = a.r + rp0;
-  float* rql = MODE == 0 ? a.r_lo + rp0 : nullptr;
-  const long long rstep = (long long)ny * a.r_pitch;
-  double* oq = OUT ? a.out + (long long)k0 * sz + col : nullptr;
+  // Per-row base pointers and 32-bit plane offsets (every field has fewer
+  // than 2^31 elements): each access is one wide multiply-add.
+  const int szi = nx * ny;           // plane stride of the [z][y][x] fields
+  const int rsi = ny * a.r_pitch;    // plane stride of the residual planes
+  // the field the stencil acts on: H (MODE 0) or L (MODE 1), (hi, lo) planes
+  const float* uh = MODE == 0 ? a.xh : a.xl;
+  const float* ul = (MODE == 1 && LO) ? a.xll : uh;
+  const float* uhc = uh + oc;
+  const float* uhs = uh + os;
+  const float* uhn = uh + on;
+  const float* uhe = uh + oe;
+  const float* ulc = ul + oc;
+  const float* uls = ul + os;
+  const float* uln = ul + on;
+  const float* ule = ul + oe;
+  const double* bc = MODE == 0 ? a.b + oc : nullptr;
+  const float* q1h = MODE == 1 ? a.r1 + orr_ : nullptr;
+  const float* q1l = MODE == 1 ? a.r1_lo + orr_ : nullptr;
+  const float* hc = (MODE == 1 && (OUT || MEAN)) ? a.xh + oc : nullptr;
+  float* rc = a.r + orr_;
+  float* rlc = MODE == 0 ? a.r_lo + orr_ : nullptr;
+  double* outc = OUT ? a.out + oc : nullptr;
+  constexpr bool LOM = MODE == 1 && LO;
+  auto ldp = [&](const float* h, const float* l, int o) { return ld_pair<VEC, LOM>(h, l, o, d1); };
+  auto lde = [&](int o, float& l) {
+    if (LOM) l = ule[o];
+    return uhe[o];
+  };
+  // plane k's right-hand side part: b (MODE 0, FP64) or r_1 (MODE 1, hi and lo)
+  auto ldb = [&](int o, double& b0, double& b1) {
+    if (VEC) {
+      const double2 v = *reinterpret_cast<const double2*>(bc + o);
+      b0 = v.x;
+      b1 = v.y;
+    } else {
+      b0 = bc[o];
+      b1 = bc[o + d1];
+    }
+  };
+  auto ldr1 = [&](int o, Pair& q) { q = ld_pair<VEC, true>(q1h, q1l, o, d1); };
+  auto ldh = [&](int o, float& h0, float& h1) {
+    const Pair q = ld_pair<VEC, false>(hc, nullptr, o, d1);
+    h0 = q.a;
+    h1 = q.b;
+  };
+  // pipeline: pair C at plane k and P at k + 1, rows below (S) and above (N)
+  // and the edge value E at plane k, and the right-hand side parts of plane k
+  int ok = k0 * szi;                                 // plane k of the fields
+  int rk = k0 * rsi;                                 // plane k of the residual planes
+  Pair C = ldp(uhc, ulc, ok);
+  Pair P = ldp(uhc, ulc, min(k0 + 1, nz - 1) * szi);
+  Pair S = ldp(uhs, uls, ok), N = ldp(uhn, uln, ok);
+  float El = 0.f;
+  float E = lde(ok, El);
+  double b0 = 0.0, b1 = 0.0;
+  Pair Q{0.f, 0.f, 0.f, 0.f};
+  float h0 = 0.f, h1 = 0.f;
+  if (MODE == 0) ldb(ok, b0, b1);
+  if (MODE == 1) ldr1(rk, Q);
+  if (MODE == 1 && (OUT || MEAN)) ldh(ok, h0, h1);
+  // exact z differences of the faces below plane k (u_{k-1} - u_k) and the
+  // low parts of plane k-1 (LO); at k = 0 the clamped plane gives zero
+  Diff dza, dzb;
+  float mla = 0.f, mlb = 0.f;
+  {
+    const Pair M = ldp(uhc, ulc, max(k0 - 1, 0) * szi);
+    dza = diff_of<FAST>(M.a, C.a);
+    dzb = diff_of<FAST>(M.b, C.b);
+    mla = M.la;
+    mlb = M.lb;
+  }
   const float2* wpz = a.wp[2];
   const float2* wmz = a.wm[2];
   const float2* w0z = a.w0[2];
-  // pipeline registers: values of plane k and the loads of plane k+1
-  float2 xc = z2, xm = z2, xp = z2, xn = z2, xs = z2;
-  double bnow = 0.0;
-  float2 rnow = z2;
-  float hnow = 0.f;
-  if (k0 < k1) {
-    xc = ldu(0);
-    if (k0 > 0) xm = ldu(-sz);
-    if (k0 + 1 < nz) xp = ldu(sz);
-    xn = hy ? ldu(sy) : xc;
-    xs = ly ? ldu(-sy) : xc;
-    if (MODE == 0) bnow = bq[0];
-    if (MODE == 1) rnow = make_float2(r1h[0], r1l[0]);
-    if (MODE == 1 && (OUT || MEAN)) hnow = hq[0];
-  }
-  // exact z difference of the face below plane k (u_{k-1} - u_k)
-  Diff dzm = two_diff(xm.x, xc.x);
-#pragma unroll 2
+  // two planes per loop pass let the register pipeline rotate without moves;
+  // the exact and low-plane correction bodies keep one (their registers would
+  // spill at the correction kernel's occupancy)
+  constexpr int kUnroll = (MODE == 1 && (LO || !FAST)) ? 1 : 2;
+#pragma unroll kUnroll
   for (int k = k0; k < k1; ++k) {
-    float2 xp2 = z2, xn2 = z2, xs2 = z2, rnext = z2;
-    double bnext = 0.0;
-    float hnext = 0.f;
+    // loads of the next plane (block-uniform guard)
+    Pair P2 = P, S2 = S, N2 = N, Q2 = Q;
+    float E2 = E, E2l = El;
+    double b02 = 0.0, b12 = 0.0;
+    float h02 = 0.f, h12 = 0.f;
     if (k + 1 < k1) {
-      if (k + 2 < nz) xp2 = ldu(2 * sz);
-      xn2 = hy ? ldu(sz + sy) : xp;
-      xs2 = ly ? ldu(sz - sy) : xp;
-      if (MODE == 0) bnext = bq[sz];
-      if (MODE == 1) rnext = make_float2(r1h[rstep], r1l[rstep]);
-      if (MODE == 1 && (OUT || MEAN)) hnext = hq[sz];
+      const int o1 = ok + szi;
+      P2 = ldp(uhc, ulc, k + 2 < nz ? o1 + szi : o1);
+      S2 = ldp(uhs, uls, o1);
+      N2 = ldp(uhn, uln, o1);
+      E2 = lde(o1, E2l);
+      if (MODE == 0) ldb(o1, b02, b12);
+      if (MODE == 1) ldr1(rk + rsi, Q2);
+      if (MODE == 1 && (OUT || MEAN)) ldh(o1, h02, h12);
     }
-    float2 xe, xw;
-    xe.x = __shfl_down_sync(0xffffffffu, xc.x, 1);
-    xe.y = __shfl_down_sync(0xffffffffu, xc.y, 1);
-    xw.x = __shfl_up_sync(0xffffffffu, xc.x, 1);
-    xw.y = __shfl_up_sync(0xffffffffu, xc.y, 1);
-    if (ex) xe = ldu(1);
-    if (wx) xw = ldu(-1);
-    Acc S;
-    df::F2 bb = df::make(0.f, 0.f);
-    if (MODE == 0) {
-      bb = df::from_f64(bnow);
-      S = Acc{bb.hi, bb.lo};
-      if (MEAN) acc_add(S, mean_h, mean_l);
-    } else {
-      S = Acc{rnow.x, rnow.y};
-    }
-    if (MEAN && act) {
-      const df::F2 V = df::mul(Vxy, ld2(a.m[2] + k));
-      df::F2 xv = df::make(xc.x, 0.f);
-      if (MODE == 1) {
-        xv = df::two_sum(hnow, xc.x);
-        xv = df::fast_two_sum(xv.hi, xv.lo + xc.y);
-      }
-      svb = df::add(svb, df::mul(V, xv));
-      sv = df::add(sv, V);
-    }
-    float sl = 0.f;  // lambda L applied to the low parts, FP32
-    const Diff dzp = two_diff(xp.x, xc.x);
-    if (hx) acc_flux(S, wpx, two_diff(xe.x, xc.x));
-    if (lx) acc_flux(S, wmx, two_diff(xw.x, xc.x));
-    if (hy) acc_flux(S, wpy, two_diff(xn.x, xc.x));
-    if (ly) acc_flux(S, wmy, two_diff(xs.x, xc.x));
-    if (k + 1 < nz) acc_flux(S, wpz[k], dzp);
-    if (k > 0) acc_flux(S, wmz[k], dzm);
+    // x neighbours outside the pair: from the neighbouring lanes, or the edge value
+    const float sd = __shfl_down_sync(0xffffffffu, C.a, 1);
+    const float su = __shfl_up_sync(0xffffffffu, C.b, 1);
+    const float eb = lane == kResTX - 1 ? E : sd;   // east of point b
+    const float wa = lane == 0 ? E : su;            // west of point a
+    float ebl = 0.f, wal = 0.f;
     if (MODE == 1 && LO) {
-      if (hx) sl = fmaf(wpx.x, xe.y - xc.y, sl);
-      if (lx) sl = fmaf(wmx.x, xw.y - xc.y, sl);
-      if (hy) sl = fmaf(wpy.x, xn.y - xc.y, sl);
-      if (ly) sl = fmaf(wmy.x, xs.y - xc.y, sl);
-      if (k + 1 < nz) sl = fmaf(wpz[k].x, xp.y - xc.y, sl);
-      if (k > 0) sl = fmaf(wmz[k].x, xm.y - xc.y, sl);
+      const float sdl = __shfl_down_sync(0xffffffffu, C.la, 1);
+      const float sul = __shfl_up_sync(0xffffffffu, C.lb, 1);
+      ebl = lane == kResTX - 1 ? El : sdl;
+      wal = lane == 0 ? El : sul;
+    }
+    Acc Sa, Sb;
+    df::F2 ba = df::make(0.f, 0.f), bb = ba;
+    if (MODE == 0) {
+      ba = df::from_f64(b0);
+      bb = df::from_f64(b1);
+      Sa = Acc{ba.hi, ba.lo};
+      Sb = Acc{bb.hi, bb.lo};
+      if (MEAN) {
+        add_of<FAST>(Sa, mean_h, mean_l);
+        add_of<FAST>(Sb, mean_h, mean_l);
+      }
+    } else {
+      Sa = Acc{Q.a, Q.la};
+      Sb = Acc{Q.b, Q.lb};
+    }
+    if (MEAN) {
+      const df::F2 mz = ld2(a.m[2] + k);
+      const df::F2 Vka = df::mul(Va, mz), Vkb = df::mul(Vb, mz);
+      df::F2 xa = df::make(C.a, 0.f), xb = df::make(C.b, 0.f);
+      if (MODE == 1) {
+        xa = df::two_sum(h0, C.a);
+        xa = df::fast_two_sum(xa.hi, xa.lo + C.la);
+        xb = df::two_sum(h1, C.b);
+        xb = df::fast_two_sum(xb.hi, xb.lo + C.lb);
+      }
+      if (act0) {
+        svb = df::add(svb, df::mul(Vka, xa));
+        sv = df::add(sv, Vka);
+      }
+      if (act1) {
+        svb = df::add(svb, df::mul(Vkb, xb));
+        sv = df::add(sv, Vkb);
+      }
+    }
+    const float2 wpzk = wpz[k], wmzk = wmz[k];
+    if (CYL) {
+      wpy = a.wy[k];
+      wmy = wpy;
+    }
+    // point a: east (the pair's inner face), west, south, north, up, down
+    const Diff dab = diff_of<FAST>(C.b, C.a);
+    const Diff dua = diff_of<FAST>(P.a, C.a), dub = diff_of<FAST>(P.b, C.b);
+    flux_of<FAST>(Sa, wpxa, dab);
+    flux_of<FAST>(Sa, wmxa, diff_of<FAST>(wa, C.a));
+    flux_of<FAST>(Sa, wmy, diff_of<FAST>(S.a, C.a));
+    flux_of<FAST>(Sa, wpy, diff_of<FAST>(N.a, C.a));
+    flux_of<FAST>(Sa, wpzk, dua);
+    flux_of<FAST>(Sa, wmzk, dza);
+    // point b
+    flux_of<FAST>(Sb, wpxb, diff_of<FAST>(eb, C.b));
+    flux_of<FAST>(Sb, wmxb, neg(dab));
+    flux_of<FAST>(Sb, wmy, diff_of<FAST>(S.b, C.b));
+    flux_of<FAST>(Sb, wpy, diff_of<FAST>(N.b, C.b));
+    flux_of<FAST>(Sb, wpzk, dub);
+    flux_of<FAST>(Sb, wmzk, dzb);
+    float sla = 0.f, slb = 0.f;  // lambda L applied to the low parts, FP32
+    if (MODE == 1 && LO) {
+      sla = fmaf(wpxa.x, C.lb - C.la, sla);
+      sla = fmaf(wmxa.x, wal - C.la, sla);
+      sla = fmaf(wmy.x, S.la - C.la, sla);
+      sla = fmaf(wpy.x, N.la - C.la, sla);
+      sla = fmaf(wpzk.x, P.la - C.la, sla);
+      sla = fmaf(wmzk.x, mla - C.la, sla);
+      slb = fmaf(wpxb.x, ebl - C.lb, slb);
+      slb = fmaf(wmxb.x, C.la - C.lb, slb);
+      slb = fmaf(wmy.x, S.lb - C.lb, slb);
+      slb = fmaf(wpy.x, N.lb - C.lb, slb);
+      slb = fmaf(wpzk.x, P.lb - C.lb, slb);
+      slb = fmaf(wmzk.x, mlb - C.lb, slb);
     }
     const float2 w0k = w0z[k];
     if (wall_xy || w0k.x != 0.f) {  // wall term: only next to a Dirichlet wall
-      const df::F2 w0 = df::add(df::add(df::make(w0x.x, w0x.y), df::make(w0y.x, w0y.y)), df::make(w0k.x, w0k.y));
-      const df::F2 t = df::mul(w0, df::make(xc.x, xc.y));
-      acc_add(S, t.hi, t.lo);
+      const df::F2 wyz = df::add(df::make(w0y.x, w0y.y), df::make(w0k.x, w0k.y));
+      const df::F2 ta = df::mul(df::add(df::make(w0xa.x, w0xa.y), wyz), df::make(C.a, C.la));
+      const df::F2 tb = df::mul(df::add(df::make(w0xb.x, w0xb.y), wyz), df::make(C.b, C.lb));
+      add_of<FAST>(Sa, ta.hi, ta.lo);
+      add_of<FAST>(Sb, tb.hi, tb.lo);
     }
     if (SIG == 1) {
-      acc_add(S, -xc.x, -xc.y);
+      add_of<FAST>(Sa, -C.a, -C.la);
+      add_of<FAST>(Sb, -C.b, -C.lb);
     } else if (SIG == 2) {
-      const df::F2 t = df::mul(df::make(a.sigma.x, a.sigma.y), df::make(xc.x, xc.y));
-      acc_add(S, -t.hi, -t.lo);
+      const df::F2 sg = df::make(a.sigma.x, a.sigma.y);
+      const df::F2 ta = df::mul(sg, df::make(C.a, C.la));
+      const df::F2 tb = df::mul(sg, df::make(C.b, C.lb));
+      add_of<FAST>(Sa, -ta.hi, -ta.lo);
+      add_of<FAST>(Sb, -tb.hi, -tb.lo);
     }
     // S.h + S.l: the rounding errors in S.l may exceed the cancelled S.h, so
     // the pair is rounded with a full two-sum
-    const df::F2 rr = df::two_sum(S.h, S.l + sl);
-    if (act) {
+    const df::F2 ra = FAST ? df::make(Sa.h + (Sa.l + sla), 0.f) : df::two_sum(Sa.h, Sa.l + sla);
+    const df::F2 rb = FAST ? df::make(Sb.h + (Sb.l + slb), 0.f) : df::two_sum(Sb.h, Sb.l + slb);
+    // stores: the pair at once where both points exist
+    {
+      double oa = 0.0, ob = 0.0;
       if (OUT) {
-        // H + L in FP64: one FP64 addition (exact while the exponents of H and
-        // L differ by at most 29) on integer-built operands; the FP64 pipe is
-        // otherwise idle here
-        *oq = df::f2d(hnow) + (LO ? df::to_f64(df::make(xc.x, xc.y)) : df::f2d(xc.x));
+        // every lane of the warp runs this (f2d_warp votes)
+        oa = df::f2d_warp(h0) + (LO ? df::f2d_warp(C.a) + df::f2d_warp(C.la) : df::f2d_warp(C.a));
+        ob = df::f2d_warp(h1) + (LO ? df::f2d_warp(C.b) + df::f2d_warp(C.lb) : df::f2d_warp(C.b));
       }
-      *rq = rr.hi;
-      if (MODE == 0) *rql = rr.lo;
-      srr = fmaf(rr.hi, rr.hi, srr);
+      if (VEC && act0) {  // VEC: act0 implies act1
+        *reinterpret_cast<float2*>(rc + rk) = make_float2(ra.hi, rb.hi);
+        if (MODE == 0) *reinterpret_cast<float2*>(rlc + rk) = make_float2(ra.lo, rb.lo);
+        if (OUT) *reinterpret_cast<double2*>(outc + ok) = make_double2(oa, ob);
+      } else if (!VEC) {
+        if (act0) {
+          rc[rk] = ra.hi;
+          if (MODE == 0) rlc[rk] = ra.lo;
+          if (OUT) outc[ok] = oa;
+        }
+        if (act1) {
+          rc[rk + 1] = rb.hi;
+          if (MODE == 0) rlc[rk + 1] = rb.lo;
+          if (OUT) outc[ok + 1] = ob;
+        }
+      }
+    }
+    if (act0) {
+      srr = fmaf(ra.hi, ra.hi, srr);
+      if (MODE == 0) sbb = MEAN ? fmaf(ba.hi + mean_h, ba.hi + mean_h, sbb) : fmaf(ba.hi, ba.hi, sbb);
+      rmax = fmaxf(rmax, fabsf(ra.hi));
+    }
+    if (act1) {
+      srr = fmaf(rb.hi, rb.hi, srr);
       if (MODE == 0) sbb = MEAN ? fmaf(bb.hi + mean_h, bb.hi + mean_h, sbb) : fmaf(bb.hi, bb.hi, sbb);
-      rmax = fmaxf(rmax, fabsf(rr.hi));
+      rmax = fmaxf(rmax, fabsf(rb.hi));
     }
-    dzm = Diff{-dzp.d, -dzp.dl};
-    xm = xc;
-    xc = xp;
-    xp = xp2;
-    xn = xn2;
-    xs = xs2;
-    bnow = bnext;
-    rnow = rnext;
-    hnow = hnext;
-    uq += sz;
-    if (MODE == 1 && LO) uql += sz;
-    if (MODE == 1 && (OUT || MEAN)) hq += sz;
-    if (MODE == 0) bq += sz;
-    if (MODE == 1) {
-      r1h += rstep;
-      r1l += rstep;
-    }
-    rq += rstep;
-    if (MODE == 0) rql += rstep;
-    if (OUT) oq += sz;
+    dza = neg(dua);
+    dzb = neg(dub);
+    mla = C.la;
+    mlb = C.lb;
+    C = P;
+    P = P2;
+    S = S2;
+    N = N2;
+    E = E2;
+    El = E2l;
+    b0 = b02;
+    b1 = b12;
+    Q = Q2;
+    h0 = h02;
+    h1 = h12;
+    ok += szi;
+    rk += rsi;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -344,37 +556,53 @@ __device__ __forceinline__ void resid_body(const ResidArgs& a, double* sh) {
   }
 }
 
-template <int MODE, int SIG, bool LO, bool MEAN, bool OUT>
-// occupancy: 4 CTAs per SM for the first check, 5 for the correction checks
-// (measured best; the latter spills a few registers to L1)
-__global__ void __launch_bounds__(kResTX * kResTY, MODE == 1 ? 5 : 4) k_resid_df(ResidArgs a, const int* __restrict__ skip) {
+// The correction residual (MODE 1) takes the plain FP32 body when the first
+// residual of this solve was small enough for the tolerance (a.fast_limit,
+// set by the host; the first check records ||r_1|| / ||b|| in st->scal[1]);
+// the choice is uniform over the grid.
+template <int MODE, int SIG, bool LO, bool MEAN, bool OUT, bool CYL, bool VEC>
+// occupancy: 3 CTAs per SM (80 registers) for the first residual; 4 (64) for
+// the correction residual, whose usual body is the plain FP32 one (latency
+// bound: more warps in flight), its exact body spilling a little
+__global__ void __launch_bounds__(kResTX * kResTY, MODE == 1 ? 4 : 3) k_resid_df(ResidArgs a,
+                                                                              const int* __restrict__ skip) {
   pdl_wait();
   if (skip && *skip) return;
   __shared__ double sh[4 * kResTY];
-  const bool interior = blockIdx.x > 0 && (int)(blockIdx.x + 1) * kResTX < a.nx && blockIdx.y > 0 &&
-                        (int)(blockIdx.y + 1) * kResTY < a.ny;
-  if (interior)
-    resid_body<MODE, SIG, LO, MEAN, OUT, true>(a, sh);
+  if (MODE == 1 && !MEAN && a.fast_limit > 0.0 && a.st->scal[1] <= a.fast_limit)
+    resid_body<MODE, SIG, LO, MEAN, OUT, CYL, VEC, true>(a, sh);
   else
-    resid_body<MODE, SIG, LO, MEAN, OUT, false>(a, sh);
+    resid_body<MODE, SIG, LO, MEAN, OUT, CYL, VEC, false>(a, sh);
   finish_if_last(a.fin, threadIdx.y * kResTX + threadIdx.x, kResTX * kResTY);
 }
 
 using ResidKernel = void (*)(ResidArgs, const int*);
 
-template <int SIG>
+template <int SIG, bool CYL, bool VEC>
 ResidKernel resid_kernel_s(int mode, bool lo, bool mean, bool out) {
-  if (mode == 0) return mean ? k_resid_df<0, SIG, false, true, false> : k_resid_df<0, SIG, false, false, false>;
-  if (mean) return lo ? k_resid_df<1, SIG, true, true, false> : k_resid_df<1, SIG, false, true, false>;
-  if (out) return lo ? k_resid_df<1, SIG, true, false, true> : k_resid_df<1, SIG, false, false, true>;
-  return lo ? k_resid_df<1, SIG, true, false, false> : k_resid_df<1, SIG, false, false, false>;
+  if (mode == 0)
+    return mean ? k_resid_df<0, SIG, false, true, false, false, VEC> : k_resid_df<0, SIG, false, false, false, CYL, VEC>;
+  if (mean)
+    return lo ? k_resid_df<1, SIG, true, true, false, false, VEC> : k_resid_df<1, SIG, false, true, false, false, VEC>;
+  if (out) return lo ? k_resid_df<1, SIG, true, false, true, CYL, VEC> : k_resid_df<1, SIG, false, false, true, CYL, VEC>;
+  return lo ? k_resid_df<1, SIG, true, false, false, CYL, VEC> : k_resid_df<1, SIG, false, false, false, CYL, VEC>;
 }
 
-// mode 0: r_1 = b - A H;  mode 1: r = r_1 - A L (lo: L has a low plane)
-ResidKernel resid_kernel(int sig_mode, int mode, bool lo, bool mean, bool out) {
-  if (sig_mode == 0) return resid_kernel_s<0>(mode, lo, mean, out);
-  if (sig_mode == 1) return resid_kernel_s<1>(mode, lo, mean, out);
-  return resid_kernel_s<2>(mode, lo, mean, out);
+template <bool CYL, bool VEC>
+ResidKernel resid_kernel_c(int sig_mode, int mode, bool lo, bool mean, bool out) {
+  if (sig_mode == 0) return resid_kernel_s<0, CYL, VEC>(mode, lo, mean, out);
+  if (sig_mode == 1) return resid_kernel_s<1, CYL, VEC>(mode, lo, mean, out);
+  return resid_kernel_s<2, CYL, VEC>(mode, lo, mean, out);
+}
+
+// mode 0: r_1 = b - A H;  mode 1: r = r_1 - A L (lo: L has a low plane);
+// cyl: periodic y with per-plane y weights (never singular, so no mean);
+// vec: pairs moved by vector accesses (nx even, FP64 arrays 16-byte aligned)
+ResidKernel resid_kernel(int sig_mode, int mode, bool lo, bool mean, bool out, bool cyl, bool vec) {
+  if (cyl) return vec ? resid_kernel_c<true, true>(sig_mode, mode, lo, mean, out)
+                      : resid_kernel_c<true, false>(sig_mode, mode, lo, mean, out);
+  return vec ? resid_kernel_c<false, true>(sig_mode, mode, lo, mean, out)
+             : resid_kernel_c<false, false>(sig_mode, mode, lo, mean, out);
 }
 
 // FP64 solution from the double-float accumulator (minus the volume-weighted
@@ -525,8 +753,17 @@ __global__ void k_scale_weights(const float2* __restrict__ wp0, const float2* __
                                 const float2* __restrict__ w00, int n0, const float2* __restrict__ wp1,
                                 const float2* __restrict__ wm1, const float2* __restrict__ w01, int n1,
                                 const float2* __restrict__ wp2, const float2* __restrict__ wm2,
-                                const float2* __restrict__ w02, int n2, float2 lam, float2* __restrict__ out) {
-  // out layout: [3 directions][3 kinds (p, m, 0)][kMaxN]
+                                const float2* __restrict__ w02, int n2, const float2* __restrict__ wc, int nc,
+                                float2 lam, float2* __restrict__ out) {
+  // out layout: [3 directions][3 kinds (p, m, 0)][kMaxN], then (cylindrical
+  // plans, block 9) the theta flux weight per radial cell
+  if (blockIdx.x == 9) {
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+      const df::F2 v = df::mul(df::make(lam.x, lam.y), ld2(wc + t));
+      out[9 * kMaxN + t] = make_float2(v.hi, v.lo);
+    }
+    return;
+  }
   const int d = blockIdx.x / 3, kind = blockIdx.x % 3;
   const int n = d == 0 ? n0 : (d == 1 ? n1 : n2);
   const float2* src = d == 0 ? (kind == 0 ? wp0 : kind == 1 ? wm0 : w00)
@@ -538,18 +775,18 @@ __global__ void k_scale_weights(const float2* __restrict__ wp0, const float2* __
   }
 }
 
-// Residual grid: 32 x 8 columns per block, `zchunk` planes marched per block.
-// Long marches amortise the loads of the planes above and below; grids with
-// fewer blocks than SMs halve the march (down to 4 planes) until every SM has
-// a block.  (Filling the SMs several times over made a lone small solve a
-// little faster but concurrent small solves slower.)  The order of the
-// reduction is fixed by the grid, which depends on the shape only.
+// Residual grid: 64 x 8 columns per block (x pairs), `zchunk` planes marched
+// per block.  Long marches amortise the loads of the planes above and below;
+// grids with fewer blocks than SMs halve the march (down to 4 planes) until
+// every SM has a block.  (Filling the SMs several times over made a lone
+// small solve a little faster but concurrent small solves slower.)  The order
+// of the reduction is fixed by the grid, which depends on the shape only.
 dim3 resid_grid(int nx, int ny, int nz, int* zchunk) {
-  const long long cols = (long long)((nx + kResTX - 1) / kResTX) * ((ny + kResTY - 1) / kResTY);
+  const long long cols = (long long)((nx + kResBX - 1) / kResBX) * ((ny + kResTY - 1) / kResTY);
   int zc = kResZChunk;
   while (zc > 4 && cols * ((nz + zc - 1) / zc) < 152) zc /= 2;
   *zchunk = zc;
-  return dim3((unsigned)((nx + kResTX - 1) / kResTX), (unsigned)((ny + kResTY - 1) / kResTY),
+  return dim3((unsigned)((nx + kResBX - 1) / kResBX), (unsigned)((ny + kResTY - 1) / kResTY),
               (unsigned)((nz + zc - 1) / zc));
 }
 
@@ -613,10 +850,12 @@ __device__ void finish_block(const double* __restrict__ partials, int nblocks, D
   // the first check (r_1 = b - A H) also measures ||b||; later checks reuse it
   const double bn2 = kind == 1 ? tt[1] : st->bnorm2;
   const double rel = bn2 > 0.0 ? sqrt(tt[0] / bn2) : sqrt(tt[0]);
-  if (kind == 1)
+  if (kind == 1) {
     st->refine_steps = 0;
-  else
+    st->scal[1] = rel;  // ||r_1|| / ||b||: bounds the FP32 correction residual's error
+  } else {
     st->refine_steps += 1;
+  }
   if (want_mean) st->scal[0] = tt[2] / tt[3];  // volume-weighted mean of the current solution
   st->rel_res = rel;
   st->bnorm2 = bn2;
@@ -649,12 +888,6 @@ __device__ void finish_if_last(const FinishArgs& f, int t, int nt) {
   }
 }
 
-__global__ void k_finish_mixed(const double* __restrict__ partials, int nblocks, DevStatus* st, double tol,
-                               int kind, int want_mean, const int* __restrict__ skip) {
-  if (skip && *skip) return;
-  finish_block(partials, nblocks, st, tol, kind, want_mean, threadIdx.x, blockDim.x);
-}
-
 struct Thomas32Args {
   float* f;           // in/out, element (z, i, j) at z*plane + i*pitch + j
   float* cs;          // scratch c'_k, same layout
@@ -665,10 +898,19 @@ struct Thomas32Args {
   const float* mz;
   const float* kdz;
   const float* koz;
+  const float* wy;    // cylindrical plans: per z weight of the y (theta) eigenvalue, A_i g_i
   double sigma, lambda;
   int singular_possible;
   float* fmax;
 };
+
+// diagonal of step k of the line sweep: s M_k - lambda Kd_k, and on
+// cylindrical plans also ly * swy_k with ly = -Lambda_y of the line and
+// swy_k = lambda wy_k (s then holds sigma - lambda Lambda_x only)
+template <bool CYL>
+__device__ __forceinline__ float thomas_diag(float s, float ly, float4 co, const float* swy, int k) {
+  return CYL ? fmaf(s, co.x, fmaf(ly, swy[k], -co.y)) : fmaf(s, co.x, -co.y);
+}
 
 constexpr int kTB = 16;   // Thomas block of planes: c' checkpoint interval and copy group
 constexpr int kNBR = 3;   // blocks of kTB planes in flight per line
@@ -703,7 +945,7 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // TL: lines per CTA (one thread per line; a tuning knob).  FULL: nz is a
 // multiple of kTB (no partial block of planes)
-template <int TL, bool FULL>
+template <int TL, bool FULL, bool CYL>
 __global__ void __launch_bounds__(TL) k_thomas_f32(Thomas32Args a, const int* __restrict__ skip) {
   constexpr int kTL = TL;
   pdl_wait();
@@ -715,6 +957,7 @@ __global__ void __launch_bounds__(TL) k_thomas_f32(Thomas32Args a, const int* __
   __shared__ float s_m[kMaxN], s_lkd[kMaxN], s_lko[kMaxN + 1];
   __shared__ float ring[kNBR * kTB][kTL];
   __shared__ float ckp[kMaxN / kTB][kTL];
+  __shared__ float s_wy[CYL ? kMaxN : 1];
   const int nz = a.nz;
   const float lam = (float)a.lambda;
   for (int k = threadIdx.x; k < nz; k += blockDim.x) {
@@ -724,6 +967,7 @@ __global__ void __launch_bounds__(TL) k_thomas_f32(Thomas32Args a, const int* __
     s_m[k] = a.mz[k];
     s_lkd[k] = lam * a.kdz[k];
     s_lko[k] = lko_k;
+    if (CYL) s_wy[k] = lam * a.wy[k];
   }
   __syncthreads();
   const int tid = threadIdx.x;
@@ -733,7 +977,8 @@ __global__ void __launch_bounds__(TL) k_thomas_f32(Thomas32Args a, const int* __
     const int i = (int)(t / a.ny), j = (int)(t % a.ny);
     const int pl = (int)a.plane;  // plane stride in elements (< 2^31 / kMaxN)
     const double lab = a.lamx[i] + a.lamy[j];
-    const float s = (float)(a.sigma - a.lambda * lab);
+    const float s = (float)(a.sigma - a.lambda * (CYL ? a.lamx[i] : lab));
+    const float ly = CYL ? (float)(-a.lamy[j]) : 0.f;
     float* f = a.f + (long long)i * a.pitch + j;
     if (!(a.singular_possible && lab == 0.0)) {
       const int nb = (nz + kTB - 1) / kTB;
@@ -764,7 +1009,7 @@ __global__ void __launch_bounds__(TL) k_thomas_f32(Thomas32Args a, const int* __
         for (int e = 0; e < kTB; ++e) {
           if (FULL || k0 + e < nz) {
             const float4 co = s_co[k0 + e];
-            const float inv = rcp_fast(fmaf(-co.z, cp, fmaf(s, co.x, -co.y)));
+            const float inv = rcp_fast(fmaf(-co.z, cp, thomas_diag<CYL>(s, ly, co, s_wy, k0 + e)));
             cp = co.w * inv;
             dp = fmaf(co.x, rs[e * kTL], -co.z * dp) * inv;
             fo[e * pl] = dp;
@@ -787,7 +1032,7 @@ __global__ void __launch_bounds__(TL) k_thomas_f32(Thomas32Args a, const int* __
         for (int e = 0; e < kTB; ++e) {
           if (FULL || k0 + e < nz) {
             const float4 co = s_co[k0 + e];
-            c = co.w * rcp_fast(fmaf(-co.z, c, fmaf(s, co.x, -co.y)));
+            c = co.w * rcp_fast(fmaf(-co.z, c, thomas_diag<CYL>(s, ly, co, s_wy, k0 + e)));
           }
           cpb[e] = c;
         }
@@ -851,19 +1096,21 @@ __device__ __forceinline__ void cp_async8(unsigned dst, const float2* src) {
 // Laplacian is left to k_thomas_f32 (launched over that pair only).  When ny
 // is odd the last pair's second line is a padding column of the row: it is
 // swept with a valid eigenvalue and excluded from the scale.
-template <int TL, bool FULL>
+template <int TL, bool FULL, bool CYL>
 __global__ void __launch_bounds__(TL) k_thomas2_f32(Thomas32Args a, const int* __restrict__ skip) {
   pdl_wait();
   if (skip && *skip) return;
   __shared__ float4 s_co[kMaxN];
   __shared__ float2 ring[kNBR * kTB][TL];
   __shared__ float2 ckp[kMaxN / kTB][TL];
+  __shared__ float s_wy[CYL ? kMaxN : 1];
   const int nz = a.nz;
   const float lam = (float)a.lambda;
   for (int k = threadIdx.x; k < nz; k += blockDim.x) {
     const float lko_k = (k + 1 < nz) ? lam * a.koz[k] : 0.f;
     const float lko_m = (k > 0) ? lam * a.koz[k - 1] : 0.f;
     s_co[k] = make_float4(a.mz[k], lam * a.kdz[k], -lko_m, -lko_k);
+    if (CYL) s_wy[k] = lam * a.wy[k];
   }
   __syncthreads();
   const int tid = threadIdx.x;
@@ -877,7 +1124,10 @@ __global__ void __launch_bounds__(TL) k_thomas2_f32(Thomas32Args a, const int* _
     const double lab0 = a.lamx[i] + a.lamy[j0];
     const double lab1 = a.lamx[i] + a.lamy[second ? j0 + 1 : j0];
     if (!(a.singular_possible && (lab0 == 0.0 || lab1 == 0.0))) {
-      const float s0 = (float)(a.sigma - a.lambda * lab0), s1 = (float)(a.sigma - a.lambda * lab1);
+      const float s0 = (float)(a.sigma - a.lambda * (CYL ? a.lamx[i] : lab0));
+      const float s1 = (float)(a.sigma - a.lambda * (CYL ? a.lamx[i] : lab1));
+      const float ly0 = CYL ? (float)(-a.lamy[j0]) : 0.f;
+      const float ly1 = CYL ? (float)(-a.lamy[second ? j0 + 1 : j0]) : 0.f;
       float2* f = reinterpret_cast<float2*>(a.f + (long long)i * a.pitch + j0);
       const int nb = (nz + kTB - 1) / kTB;
       const unsigned ring0 = (unsigned)__cvta_generic_to_shared(&ring[0][tid]);
@@ -906,8 +1156,8 @@ __global__ void __launch_bounds__(TL) k_thomas2_f32(Thomas32Args a, const int* _
           if (FULL || k0 + e < nz) {
             const float4 co = s_co[k0 + e];
             const float2 fv = rs[e * TL];
-            const float inv0 = rcp_fast(fmaf(-co.z, cp0, fmaf(s0, co.x, -co.y)));
-            const float inv1 = rcp_fast(fmaf(-co.z, cp1, fmaf(s1, co.x, -co.y)));
+            const float inv0 = rcp_fast(fmaf(-co.z, cp0, thomas_diag<CYL>(s0, ly0, co, s_wy, k0 + e)));
+            const float inv1 = rcp_fast(fmaf(-co.z, cp1, thomas_diag<CYL>(s1, ly1, co, s_wy, k0 + e)));
             cp0 = co.w * inv0;
             cp1 = co.w * inv1;
             dp0 = fmaf(co.x, fv.x, -co.z * dp0) * inv0;
@@ -929,8 +1179,8 @@ __global__ void __launch_bounds__(TL) k_thomas2_f32(Thomas32Args a, const int* _
         for (int e = 0; e < kTB; ++e) {
           if (FULL || k0 + e < nz) {
             const float4 co = s_co[k0 + e];
-            c0 = co.w * rcp_fast(fmaf(-co.z, c0, fmaf(s0, co.x, -co.y)));
-            c1 = co.w * rcp_fast(fmaf(-co.z, c1, fmaf(s1, co.x, -co.y)));
+            c0 = co.w * rcp_fast(fmaf(-co.z, c0, thomas_diag<CYL>(s0, ly0, co, s_wy, k0 + e)));
+            c1 = co.w * rcp_fast(fmaf(-co.z, c1, thomas_diag<CYL>(s1, ly1, co, s_wy, k0 + e)));
           }
           cpb0[e] = c0;
           cpb1[e] = c1;
@@ -1075,9 +1325,54 @@ fdi_status mixed_alloc_workspace(fdi_plan* p) {
   FDI_CUDA_TRY(cudaMalloc(&p->wr1, szr * 2 * sizeof(float)));              // r_1 as (hi, lo) planes
   p->wr1_plane = (long long)szr;
   FDI_CUDA_TRY(cudaMalloc(&p->d_scales, (size_t)(kMaxRefineCap + 2) * 4 * sizeof(float)));
-  FDI_CUDA_TRY(cudaMalloc(&p->lam_w, (size_t)9 * kMaxN * sizeof(float2)));
+  FDI_CUDA_TRY(cudaMalloc(&p->lam_w, (size_t)10 * kMaxN * sizeof(float2)));
   FDI_CUDA_TRY(cudaMalloc(&p->d_counter, 4 * sizeof(unsigned)));
   FDI_CUDA_TRY(cudaMemset(p->d_counter, 0, 4 * sizeof(unsigned)));
+  return FDI_OK;
+}
+
+// FP32 Thomas sweep in the configuration of the plan (thomas_tl)
+template <bool CYL>
+fdi_status launch_thomas32(fdi_plan* p, const Thomas32Args& ta, bool pdl, bool singular, const int* skip,
+                           cudaStream_t s) {
+  const long long lines = (long long)ta.nx * ta.ny;
+  const bool full = ta.nz % kTB == 0;
+  if (p->thomas_tl == 2) {
+    // two lines per thread, 64 threads (128 lines) per CTA
+    const long long pairs = (long long)ta.nx * ((ta.ny + 1) / 2);
+    const unsigned g = (unsigned)((pairs + 63) / 64);
+    if (full)
+      FDI_CUDA_TRY(launch_pdl(pdl, k_thomas2_f32<64, true, CYL>, dim3(g), dim3(64), 0, s, ta, skip));
+    else
+      FDI_CUDA_TRY(launch_pdl(pdl, k_thomas2_f32<64, false, CYL>, dim3(g), dim3(64), 0, s, ta, skip));
+    FDI_LAUNCH_CHECK(p);
+    if (singular) {
+      // the null line (0, 0) and its pair partner, one line per thread
+      Thomas32Args t1 = ta;
+      t1.nx = 1;
+      t1.ny = std::min(ta.ny, 2);
+      if (full)
+        k_thomas_f32<64, true, CYL><<<1, 64, 0, s>>>(t1, skip);
+      else
+        k_thomas_f32<64, false, CYL><<<1, 64, 0, s>>>(t1, skip);
+      FDI_LAUNCH_CHECK(p);
+    }
+    return FDI_OK;
+  }
+  if (p->thomas_tl == 64) {
+    const unsigned g = (unsigned)((lines + 63) / 64);
+    if (full)
+      FDI_CUDA_TRY(launch_pdl(pdl, k_thomas_f32<64, true, CYL>, dim3(g), dim3(64), 0, s, ta, skip));
+    else
+      FDI_CUDA_TRY(launch_pdl(pdl, k_thomas_f32<64, false, CYL>, dim3(g), dim3(64), 0, s, ta, skip));
+  } else {
+    const unsigned g = (unsigned)((lines + 127) / 128);
+    if (full)
+      FDI_CUDA_TRY(launch_pdl(pdl, k_thomas_f32<128, true, CYL>, dim3(g), dim3(128), 0, s, ta, skip));
+    else
+      FDI_CUDA_TRY(launch_pdl(pdl, k_thomas_f32<128, false, CYL>, dim3(g), dim3(128), 0, s, ta, skip));
+  }
+  FDI_LAUNCH_CHECK(p);
   return FDI_OK;
 }
 
@@ -1124,8 +1419,9 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
   // flux weights multiplied by lambda for this solve
   {
     FDI_KTIMER(p, "reduce", s);
-    k_scale_weights<<<9, 256, 0, s>>>(mx->wp, mx->wm, mx->w0, nx, my->wp, my->wm, my->w0, ny, mz->wp, mz->wm, mz->w0,
-                                      nz, split_host(lambda), p->lam_w);
+    k_scale_weights<<<p->cyl ? 10 : 9, 256, 0, s>>>(mx->wp, mx->wm, mx->w0, nx, my->wp, my->wm, my->w0, ny, mz->wp,
+                                                    mz->wm, mz->w0, nz, p->cyl_wres_df, nz, split_host(lambda),
+                                                    p->lam_w);
     FDI_LAUNCH_CHECK(p);
   }
   ResidArgs ra{};
@@ -1139,6 +1435,10 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     ra.w0[d] = p->lam_w + (d * 3 + 2) * kMaxN;
     ra.m[d] = m->m_df;
   }
+  ra.wy = p->cyl ? p->lam_w + 9 * kMaxN : nullptr;
+  // FP32 correction residual: its error is at most about 16 u ||r_1|| (u =
+  // 2^-24; measured near u ||r_1||), kept below tol / 4 of ||b||
+  ra.fast_limit = p->tol / (4.0 * 16.0 * 5.9604644775390625e-8);
   ra.sigma = split_host(sigma);
   ra.lambda = split_host(lambda);
   ra.sig_mode = sigma == 0.0 ? 0 : (sigma == 1.0 ? 1 : 2);
@@ -1240,41 +1540,11 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
       ta.lambda = lambda;
       ta.singular_possible = singular ? 1 : 0;
       ta.fmax = sc + 2;
-      const long long lines = (long long)nx * ny;
-      const bool full = nz % kTB == 0;
-      if (p->thomas_tl == 2) {
-        // two lines per thread, 64 threads (128 lines) per CTA
-        const long long pairs = (long long)nx * ((ny + 1) / 2);
-        const unsigned g = (unsigned)((pairs + 63) / 64);
-        if (full)
-          FDI_CUDA_TRY(launch_pdl(pdl, k_thomas2_f32<64, true>, dim3(g), dim3(64), 0, s, ta, skip));
-        else
-          FDI_CUDA_TRY(launch_pdl(pdl, k_thomas2_f32<64, false>, dim3(g), dim3(64), 0, s, ta, skip));
-        FDI_LAUNCH_CHECK(p);
-        if (singular) {
-          // the null line (0, 0) and its pair partner, one line per thread
-          Thomas32Args t1 = ta;
-          t1.nx = 1;
-          t1.ny = std::min(ny, 2);
-          if (full)
-            k_thomas_f32<64, true><<<1, 64, 0, s>>>(t1, skip);
-          else
-            k_thomas_f32<64, false><<<1, 64, 0, s>>>(t1, skip);
-        }
-      } else if (p->thomas_tl == 64) {
-        const unsigned g = (unsigned)((lines + 63) / 64);
-        if (full)
-          FDI_CUDA_TRY(launch_pdl(pdl, k_thomas_f32<64, true>, dim3(g), dim3(64), 0, s, ta, skip));
-        else
-          FDI_CUDA_TRY(launch_pdl(pdl, k_thomas_f32<64, false>, dim3(g), dim3(64), 0, s, ta, skip));
-      } else {
-        const unsigned g = (unsigned)((lines + 127) / 128);
-        if (full)
-          FDI_CUDA_TRY(launch_pdl(pdl, k_thomas_f32<128, true>, dim3(g), dim3(128), 0, s, ta, skip));
-        else
-          FDI_CUDA_TRY(launch_pdl(pdl, k_thomas_f32<128, false>, dim3(g), dim3(128), 0, s, ta, skip));
-      }
-      FDI_LAUNCH_CHECK(p);
+      ta.wy = p->cyl ? p->cyl_wy_f : nullptr;
+      if (p->cyl)
+        FDI_TRY(launch_thomas32<true>(p, ta, pdl, singular, skip, s));
+      else
+        FDI_TRY(launch_thomas32<false>(p, ta, pdl, singular, skip, s));
     }
     // back y: F2 [z][i][j] -> F4
     t.in = F2;
@@ -1340,7 +1610,9 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
       ak.fin = FinishArgs{p->d_counter, p->partials, p->d_status, p->tol, round == 0 ? 1 : 2, singular ? 1 : 0,
                           next_round};
       const bool write_out = !singular && round > 0;
-      ResidKernel kern = resid_kernel(ra.sig_mode, round == 0 ? 0 : 1, round >= 2, singular, write_out);
+      const bool vec = nx % 2 == 0 && (reinterpret_cast<uintptr_t>(b) & 15u) == 0 &&
+                       (reinterpret_cast<uintptr_t>(out) & 15u) == 0;
+      ResidKernel kern = resid_kernel(ra.sig_mode, round == 0 ? 0 : 1, round >= 2, singular, write_out, p->cyl, vec);
       FDI_CUDA_TRY(launch_pdl(pdl, kern, rgrid, dim3(kResTX, kResTY), 0, s, ak, skip));
       FDI_LAUNCH_CHECK(p);
     }

@@ -132,24 +132,27 @@ fdi_status dev_alloc(T** p, size_t count) {
     if (_s != FDI_OK) return _s;      \
   } while (0)
 
+// periodic: ko[n-1] couples the last cell with the first (the flux weights
+// wrap around and there is no wall term)
 fdi_status make_axis(Axis** out, const std::vector<double>& m, const std::vector<double>& kd,
-                     const std::vector<double>& ko, bool zero_flux, cudaStream_t s) {
+                     const std::vector<double>& ko, bool zero_flux, cudaStream_t s, bool periodic = false) {
   Axis* ax = new Axis();
   *out = ax;
   int n = (int)m.size();
   ax->n = n;
   ax->zero_flux = zero_flux;
+  ax->periodic = periodic;
   ax->h_m = m;
   ax->h_kd = kd;
   ax->h_ko = ko;
   std::vector<double> wp(n, 0.0), wm(n, 0.0), w0(n, 0.0);
   for (int i = 0; i < n; ++i) {
-    double kp = (i + 1 < n) ? ko[i] : 0.0;
-    double km = (i > 0) ? ko[i - 1] : 0.0;
+    double kp = (i + 1 < n || periodic) ? ko[i] : 0.0;
+    double km = (i > 0) ? ko[i - 1] : (periodic ? ko[n - 1] : 0.0);
     wp[i] = kp / m[i];
     wm[i] = km / m[i];
     // wall term: nonzero only in the first and last cell (interior cells have none)
-    w0[i] = (i == 0 || i == n - 1) ? (kd[i] + kp + km) / m[i] : 0.0;
+    w0[i] = (!periodic && (i == 0 || i == n - 1)) ? (kd[i] + kp + km) / m[i] : 0.0;
   }
   FDI_TRY(dev_alloc(&ax->m, n));
   FDI_TRY(dev_alloc(&ax->kd, n));
@@ -258,12 +261,31 @@ void free_plan(fdi_plan* p) {
     if (p->mac_ih[d]) cudaFree(p->mac_ih[d]);
     if (p->mac_idc[d]) cudaFree(p->mac_idc[d]);
   }
+  for (void* q : {(void*)p->cyl_wy, (void*)p->cyl_wres, (void*)p->cyl_wy_f, (void*)p->cyl_wres_df, (void*)p->cyl_Er,
+                  (void*)p->cyl_Eri, (void*)p->cyl_lr})
+    if (q) cudaFree(q);
   if (p->d_kry) cudaFree(p->d_kry);
   if (p->kpartials) cudaFree(p->kpartials);
   if (p->d_err) cudaFree(p->d_err);
   if (p->h_flag) cudaFreeHost(p->h_flag);
   delete p;
 }
+
+fdi_status check_eigen_flag(const int* d_err) {
+  int h_err = 0;
+  cudaError_t e = cudaMemcpy(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    set_error(std::string("eigen status copy: ") + cudaGetErrorString(e));
+    return FDI_ERR_CUDA;
+  }
+  if (h_err != 0) {
+    set_error("plan eigen decomposition did not converge");
+    return FDI_ERR_NOT_CONVERGED;
+  }
+  return FDI_OK;
+}
+
+fdi_status finish_plan(fdi_plan* p, cudaStream_t s);
 
 fdi_status build_plan(fdi_plan* p, const double* const faces[3], const fdi_bc bc_lo[3],
                       const fdi_bc bc_hi[3], cudaStream_t s) {
@@ -315,20 +337,16 @@ fdi_status build_plan(fdi_plan* p, const double* const faces[3], const fdi_bc bc
     }
     p->nfields = 4;
   }
-  int h_err = 0;
   if (st == FDI_OK) st = eigen_decompose_all(p->axes, s, d_err);
-  if (st == FDI_OK) {
-    cudaError_t e = cudaMemcpy(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) {
-      set_error(std::string("eigen status copy: ") + cudaGetErrorString(e));
-      st = FDI_ERR_CUDA;
-    } else if (h_err != 0) {
-      set_error("plan eigen decomposition did not converge");
-      st = FDI_ERR_NOT_CONVERGED;
-    }
-  }
+  if (st == FDI_OK) st = check_eigen_flag(d_err);
   cudaFree(d_err);
   if (st != FDI_OK) return st;
+  return finish_plan(p, s);
+}
+
+// field sizes and volumes, workspaces, mixed-precision and Stokes set-up of a
+// plan whose axes, fields and eigen data are in place
+fdi_status finish_plan(fdi_plan* p, cudaStream_t s) {
   for (int fi = 0; fi < p->nfields; ++fi) {
     Field& f = p->fields[fi];
     f.P = (long long)f.n[0] * f.n[1] * f.n[2];
@@ -358,6 +376,167 @@ fdi_status build_plan(fdi_plan* p, const double* const faces[3], const fdi_bc bc
       FDI_CUDA_TRY(cudaEventCreateWithFlags(&p->sjoin[c], cudaEventDisableTiming));
     }
     FDI_CUDA_TRY(cudaEventCreateWithFlags(&p->sfork, cudaEventDisableTiming));
+  }
+  return FDI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Cylindrical grids (Sec. 6, Eq. 41-46), finite-volume reading: cells
+// (r_i, theta_j, z_k); radial faces rho_0 < ... < rho_n (rho_0 = 0: the axis,
+// a face of zero area that no flux crosses), centres c_i, annular areas
+// A_i = (rho_{i+1}^2 - rho_i^2) / 2 = h_i c_i; radial flux through rho_{i+1}
+// rho_{i+1} (u_{i+1} - u_i) / (c_{i+1} - c_i); a Dirichlet wall at rho_0 > 0 or
+// rho_n over half a cell.  So D_rr = diag(A)^{-1} K_r, and the 1/r^2 of Eq. 41
+// becomes per radial cell g_i = h_i / (c_i A_i) (the arc flux of the cell over
+// its volume).  theta: M uniform cells on the full circle, periodic.
+
+void radial_op(const double* rho, int n, int bc_in, int bc_out, std::vector<double>& A, std::vector<double>& kd,
+               std::vector<double>& ko, std::vector<double>& g) {
+  A.assign(n, 0.0);
+  kd.assign(n, 0.0);
+  ko.assign(n, 0.0);
+  g.assign(n, 0.0);
+  std::vector<double> c(n);
+  for (int i = 0; i < n; ++i) {
+    const double h = rho[i + 1] - rho[i];
+    c[i] = 0.5 * (rho[i] + rho[i + 1]);
+    A[i] = h * c[i];
+    g[i] = h / (c[i] * A[i]);
+  }
+  for (int i = 0; i + 1 < n; ++i) {
+    const double w = rho[i + 1] / (c[i + 1] - c[i]);
+    ko[i] = w;
+    kd[i] -= w;
+    kd[i + 1] -= w;
+  }
+  if (rho[0] > 0.0 && bc_in == FDI_BC_DIRICHLET) kd[0] -= rho[0] / (0.5 * (rho[1] - rho[0]));
+  if (bc_out == FDI_BC_DIRICHLET) kd[n - 1] -= rho[n] / (0.5 * (rho[n] - rho[n - 1]));
+}
+
+// Eigenbasis of the periodic second difference on M uniform cells (h = 2 pi / M,
+// D = K / h with K = circ(-2, 1, 1) / h), in closed form: the discrete Fourier
+// modes cos(2 pi k j / M) and sin(2 pi k j / M), eigenvalue -(4 / h^2) sin^2(pi k / M),
+// normalised so that E^T diag(h) E = I.  Column order: the constant mode, then
+// (cos k, sin k) for k = 1 .. (M-1)/2, then the alternating mode k = M/2 for
+// even M (eigenvalues descending from 0, like the tridiagonal decompositions).
+void periodic_eigen(int M, std::vector<double>& lam, std::vector<double>& E, std::vector<double>& Einv) {
+  const double pi = 3.14159265358979323846;
+  const double h = 2.0 * pi / M;
+  lam.assign(M, 0.0);
+  E.assign((size_t)M * M, 0.0);
+  Einv.assign((size_t)M * M, 0.0);
+  auto column = [&](int q, int k, bool sine) {
+    const double sk = std::sin(pi * k / M);
+    lam[q] = -4.0 / (h * h) * sk * sk;
+    const double norm = (k == 0 || 2 * k == M) ? 1.0 / std::sqrt(M * h) : std::sqrt(2.0 / (M * h));
+    for (int j = 0; j < M; ++j) {
+      const double ang = 2.0 * pi * (double)(((long long)k * j) % M) / M;  // reduced exactly
+      E[(size_t)j * M + q] = norm * (sine ? std::sin(ang) : std::cos(ang));
+    }
+  };
+  column(0, 0, false);
+  for (int k = 1; 2 * k < M; ++k) {
+    column(2 * k - 1, k, false);
+    column(2 * k, k, true);
+  }
+  if (M % 2 == 0) column(M - 1, M / 2, false);
+  for (int j = 0; j < M; ++j)
+    for (int q = 0; q < M; ++q) Einv[(size_t)q * M + j] = E[(size_t)j * M + q] * h;
+}
+
+template <typename T>
+fdi_status upload(T** dst, const std::vector<T>& v) {
+  FDI_TRY(dev_alloc(dst, v.size()));
+  FDI_CUDA_TRY(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return FDI_OK;
+}
+
+// Internal order [r][theta][z]: x = z, y = theta, z = r, so the Thomas sweeps
+// run along r (Eq. 44) and the x / y eigen transforms along z and theta.
+fdi_status build_cyl_plan(fdi_plan* p, const double* rho, int nr, int M, const double* zf, int nz, fdi_bc bc_r_in,
+                          fdi_bc bc_r_out, fdi_bc bc_z_lo, fdi_bc bc_z_hi, cudaStream_t s) {
+  std::vector<double> m, kd, ko;
+  Axis* az = nullptr;
+  Axis* at = nullptr;
+  Axis* ar = nullptr;
+  cell_op(zf, nz, bc_z_lo, bc_z_hi, m, kd, ko);
+  FDI_TRY(make_axis(&az, m, kd, ko, bc_z_lo == FDI_BC_NEUMANN && bc_z_hi == FDI_BC_NEUMANN, s));
+  p->axes.push_back(az);
+  const double pi = 3.14159265358979323846;
+  const double h = 2.0 * pi / M;
+  m.assign(M, h);
+  kd.assign(M, -2.0 / h);
+  ko.assign(M, 1.0 / h);
+  FDI_TRY(make_axis(&at, m, kd, ko, true, s, true));
+  p->axes.push_back(at);
+  std::vector<double> A, g;
+  radial_op(rho, nr, bc_r_in, bc_r_out, A, kd, ko, g);
+  const bool r_closed = (rho[0] == 0.0 || bc_r_in == FDI_BC_NEUMANN) && bc_r_out == FDI_BC_NEUMANN;
+  FDI_TRY(make_axis(&ar, A, kd, ko, r_closed, s));
+  p->axes.push_back(ar);
+  Field& f = p->fields[0];
+  f.ax[0] = az;
+  f.ax[1] = at;
+  f.ax[2] = ar;
+  for (int d = 0; d < 3; ++d) f.n[d] = f.ax[d]->n;
+  p->nfields = 1;
+  // closed-form theta eigenbasis, then the tridiagonal ones on the GPU
+  {
+    std::vector<double> lam, E, Einv;
+    periodic_eigen(M, lam, E, Einv);
+    FDI_CUDA_TRY(cudaMemcpy(at->lam, lam.data(), M * sizeof(double), cudaMemcpyHostToDevice));
+    FDI_CUDA_TRY(cudaMemcpy(at->E, E.data(), E.size() * sizeof(double), cudaMemcpyHostToDevice));
+    FDI_CUDA_TRY(cudaMemcpy(at->Einv, Einv.data(), Einv.size() * sizeof(double), cudaMemcpyHostToDevice));
+    // weights of the theta eigenvalue (Thomas) and of the theta flux (residual)
+    std::vector<double> wy(nr), wres(nr);
+    for (int i = 0; i < nr; ++i) {
+      wy[i] = A[i] * g[i];
+      wres[i] = g[i] / (h * h);
+    }
+    FDI_TRY(upload(&p->cyl_wy, wy));
+    FDI_TRY(upload(&p->cyl_wres, wres));
+    if (p->thomas_axis == -1) {
+      // Eq. 45: per theta mode j, D_rr + lambda_th,j g = E_{r,j} Lambda E_{r,j}^{-1},
+      // i.e. K_r + lambda_th,j diag(A g) with the same diag(A)
+      std::vector<double> kd_all((size_t)M * nr);
+      for (int q = 0; q < M; ++q)
+        for (int i = 0; i < nr; ++i) kd_all[(size_t)q * nr + i] = kd[i] + lam[q] * A[i] * g[i];
+      double* d_kd = nullptr;
+      FDI_TRY(upload(&d_kd, kd_all));
+      fdi_status st = dev_alloc(&p->cyl_lr, (size_t)M * nr);
+      if (st == FDI_OK) st = dev_alloc(&p->cyl_Er, (size_t)M * nr * nr);
+      if (st == FDI_OK) st = dev_alloc(&p->cyl_Eri, (size_t)M * nr * nr);
+      int* d_err = nullptr;
+      if (st == FDI_OK) st = dev_alloc(&d_err, 1);
+      if (st == FDI_OK && cudaMemset(d_err, 0, sizeof(int)) != cudaSuccess) st = FDI_ERR_CUDA;
+      if (st == FDI_OK)
+        st = eigen_decompose_batch(M, nr, ar->m, d_kd, ar->ko, r_closed, p->cyl_lr, p->cyl_Er, p->cyl_Eri, s, d_err);
+      if (st == FDI_OK) st = check_eigen_flag(d_err);
+      if (d_err) cudaFree(d_err);
+      cudaFree(d_kd);
+      FDI_TRY(st);
+    }
+  }
+  int* d_err = nullptr;
+  FDI_TRY(dev_alloc(&d_err, 1));
+  FDI_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+  fdi_status st = eigen_decompose_all(p->axes, s, d_err);
+  if (st == FDI_OK) st = check_eigen_flag(d_err);
+  cudaFree(d_err);
+  FDI_TRY(st);
+  FDI_TRY(finish_plan(p, s));
+  if (p->prec != FDI_PREC_FP64) {
+    std::vector<float> wyf(nr);
+    std::vector<float2> wdf(nr);
+    for (int i = 0; i < nr; ++i) {
+      const double w = A[i] * g[i];
+      wyf[i] = (float)w;
+      const double v = g[i] / (h * h);
+      const float vh = (float)v;
+      wdf[i] = make_float2(vh, (float)(v - (double)vh));
+    }
+    FDI_TRY(upload(&p->cyl_wy_f, wyf));
+    FDI_TRY(upload(&p->cyl_wres_df, wdf));
   }
   return FDI_OK;
 }
@@ -499,6 +678,103 @@ fdi_status fdi_plan_create(const double* const faces[3], const int n[3], const f
     return st;
   }
   apply_tuning(p);  // a configuration autotuned earlier for this grid shape
+  *out = p;
+  return FDI_OK;
+}
+
+fdi_status fdi_plan_create_cyl(const double* rfaces, int nr, int ntheta, const double* zfaces, int nz,
+                               fdi_bc bc_r_in, fdi_bc bc_r_out, fdi_bc bc_z_lo, fdi_bc bc_z_hi, fdi_precision prec,
+                               int tpf, fdi_plan** out) {
+  if (!out) return FDI_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!rfaces || !zfaces) return FDI_ERR_INVALID_ARG;
+  if (nr < 2 || nr > kMaxN || nz < 2 || nz > kMaxN || ntheta < 3 || ntheta > kMaxN) {
+    set_error("a cylindrical plan needs 2 <= n_r, n_z <= 256 and 3 <= n_theta <= 256 cells");
+    return FDI_ERR_INVALID_ARG;
+  }
+  if (!(rfaces[0] >= 0.0)) {
+    set_error("radial faces must be non-negative (rfaces[0] = 0 places the axis)");
+    return FDI_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < nr; ++i)
+    if (!(rfaces[i + 1] > rfaces[i]) || !std::isfinite(rfaces[i + 1])) {
+      set_error("radial faces must be finite and strictly ascending");
+      return FDI_ERR_INVALID_ARG;
+    }
+  for (int i = 0; i < nz; ++i)
+    if (!(zfaces[i + 1] > zfaces[i]) || !std::isfinite(zfaces[i]) || !std::isfinite(zfaces[i + 1])) {
+      set_error("axial faces must be finite and strictly ascending");
+      return FDI_ERR_INVALID_ARG;
+    }
+  for (fdi_bc b : {bc_r_in, bc_r_out, bc_z_lo, bc_z_hi})
+    if ((unsigned)b > 1u) return FDI_ERR_INVALID_ARG;
+  if (tpf != 0 && tpf != 1) return FDI_ERR_INVALID_ARG;
+  if (prec != FDI_PREC_FP64 && prec != FDI_PREC_MIXED_F16) {
+    set_error("a cylindrical plan takes FDI_PREC_FP64 or FDI_PREC_MIXED_F16");
+    return (prec == FDI_PREC_MIXED_TF32 || prec == FDI_PREC_MIXED_BF16) ? FDI_ERR_UNSUPPORTED : FDI_ERR_INVALID_ARG;
+  }
+  if (tpf && prec != FDI_PREC_FP64) {
+    set_error("the cylindrical TPF (Eq. 45-46) runs on the FP64 path only");
+    return FDI_ERR_UNSUPPORTED;
+  }
+  fdi_plan* p = new fdi_plan();
+  p->grid = FDI_GRID_CELL;
+  p->prec = prec;
+  p->cyl = true;
+  // external [z][theta][r] (r fastest) <-> internal [r][theta][z]: the x <-> z
+  // swap of a Thomas-along-x plan
+  p->thomas_ext = 0;
+  p->perm[0] = 2;
+  p->perm[2] = 0;
+  p->thomas_axis = tpf ? -1 : 2;
+  p->n[0] = nz;
+  p->n[1] = ntheta;
+  p->n[2] = nr;
+  p->n_ext[0] = nr;
+  p->n_ext[1] = ntheta;
+  p->n_ext[2] = nz;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    set_error("no CUDA device");
+    return FDI_ERR_CUDA;
+  }
+  if (prec == FDI_PREC_FP64) {
+    p->tol = 1e-11;
+    p->max_refine = 2;
+    p->ktol = 1e-11;
+  } else {
+    p->tol = 1e-10;
+    p->max_refine = 3;
+    p->ktol = 1e-10;
+  }
+  cudaStream_t s;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    delete p;
+    set_error("stream creation failed");
+    return FDI_ERR_CUDA;
+  }
+  fdi_status st = build_cyl_plan(p, rfaces, nr, ntheta, zfaces, nz, bc_r_in, bc_r_out, bc_z_lo, bc_z_hi, s);
+  if (st == FDI_OK) {
+    const size_t P = (size_t)nr * ntheta * nz;
+    for (double*& t : p->tstage) {
+      if (cudaMalloc(&t, P * sizeof(double)) != cudaSuccess) {
+        set_error("cudaMalloc of the permuted staging fields failed");
+        st = FDI_ERR_OUT_OF_MEMORY;
+        break;
+      }
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (st == FDI_OK && e != cudaSuccess) {
+    set_error(std::string("plan creation: ") + cudaGetErrorString(e));
+    st = FDI_ERR_CUDA;
+  }
+  if (st != FDI_OK) {
+    cudaDeviceSynchronize();
+    free_plan(p);
+    return st;
+  }
   *out = p;
   return FDI_OK;
 }

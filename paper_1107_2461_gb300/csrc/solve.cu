@@ -45,6 +45,10 @@ fdi_status validate_field_args(const fdi_plan* p, int field, double sigma, doubl
     set_error("the Laplace problem (sigma = 0) is defined on the cell field only");
     return FDI_ERR_INVALID_ARG;
   }
+  if (sigma == 0.0 && p->cyl && p->fields[0].zero_flux_all) {
+    set_error("the zero-flux Laplacian of a cylindrical plan is singular; not handled");
+    return FDI_ERR_UNSUPPORTED;
+  }
   return FDI_OK;
 }
 
@@ -66,6 +70,14 @@ fdi_status solve_once_f64(fdi_plan* p, const Field& f, double sigma, double lamb
     FDI_TRY(launch_thomas_f64(p, f, sigma, lambda, t1, t0, t2, skip, s));
     FDI_TRY(launch_slab_f64(p, t0, t1, ay->E, ny, ny, nx, nz, skip, s));
     FDI_TRY(launch_lines_f64(p, t1, out, ax->E, nx, nx, (long long)ny * nz, accumulate, skip, s));
+  } else if (p->cyl) {
+    // cylindrical TPF (Eq. 45-46): the radial transform of theta mode j uses
+    // that mode's own eigenbasis, the divide its own eigenvalues
+    FDI_TRY(launch_modes_f64(p, t1, t0, p->cyl_Eri, nz, nx, ny, skip, s));
+    FDI_TRY(launch_divide_modes_f64(p, f, sigma, lambda, t0, skip, s));
+    FDI_TRY(launch_modes_f64(p, t0, t1, p->cyl_Er, nz, nx, ny, skip, s));
+    FDI_TRY(launch_slab_f64(p, t1, t0, ay->E, ny, ny, nx, nz, skip, s));
+    FDI_TRY(launch_lines_f64(p, t0, out, ax->E, nx, nx, (long long)ny * nz, accumulate, skip, s));
   } else {
     FDI_TRY(launch_slab_f64(p, t1, t0, az->Einv, nz, nz, (long long)nx * ny, 1, skip, s));
     FDI_TRY(launch_divide_f64(p, f, sigma, lambda, t0, skip, s));

@@ -64,6 +64,7 @@ SIGNATURES = {
     "fdi_plan_set_krylov": (_i, [_vp, _i]),
     "fdi_eigen_noalloc": (_i, [C.POINTER(_d), _i, _i, _i, _i, _vp, _vp, _vp, C.POINTER(_i), _vp]),
     "fdi_plan_set_graphs": (_i, [_vp, _i]),
+    "fdi_plan_create_cyl": (_i, [C.POINTER(_d), _i, _i, C.POINTER(_d), _i, _i, _i, _i, _i, _i, _i, C.POINTER(_vp)]),
     "fdi_plan_set_thomas_config": (_i, [_vp, _i]),
     "fdi_plan_set_wait_limit": (_i, [_vp, C.c_longlong]),
     "fdi_plan_autotune": (_i, [_vp, _d, _vp, _vp, _i, C.POINTER(_i), _vp]),
@@ -201,6 +202,33 @@ class Plan:
 
 def plan_create(faces, n=None, bc_lo=(0, 0, 0), bc_hi=(0, 0, 0), grid=GRID_CELL, prec=PREC_FP64, thomas_axis=2):
     return Plan(faces, n, bc_lo, bc_hi, grid, prec, thomas_axis)
+
+
+class CylPlan(Plan):
+    """Owning handle of a cylindrical plan (fdi_plan_create_cyl): fields in C
+    order [n_z][n_theta][n_r], r fastest."""
+
+    def __init__(self, rfaces, ntheta, zfaces, bc_r=(0, 0), bc_z=(0, 0), prec=PREC_FP64, tpf=False):
+        lib = load()
+        self._faces = [np.ascontiguousarray(np.asarray(f, dtype=np.float64)) for f in (rfaces, zfaces)]
+        nr, nz = self._faces[0].size - 1, self._faces[1].size - 1
+        self.n = (nr, int(ntheta), nz)
+        self.grid, self.prec, self.thomas_axis = GRID_CELL, prec, -1 if tpf else 0
+        dp = C.POINTER(C.c_double)
+        h = C.c_void_p()
+        _check(lib.fdi_plan_create_cyl(self._faces[0].ctypes.data_as(dp), nr, int(ntheta),
+                                       self._faces[1].ctypes.data_as(dp), nz, int(bc_r[0]), int(bc_r[1]),
+                                       int(bc_z[0]), int(bc_z[1]), prec, 1 if tpf else 0, C.byref(h)),
+               "fdi_plan_create_cyl")
+        self.handle = h.value
+
+
+def plan_create_cyl(rfaces, ntheta, zfaces, bc_r=(0, 0), bc_z=(0, 0), prec=PREC_FP64, tpf=False):
+    """Cylindrical plan (Sec. 6): radial faces (rfaces[0] = 0: the axis),
+    ntheta uniform periodic cells, axial faces; bc_r = (inner, outer),
+    bc_z = (low, high) wall types; tpf: eigen decomposition along r per theta
+    mode (Eq. 45-46, FP64 only) instead of the radial Thomas sweep (Eq. 44)."""
+    return CylPlan(rfaces, ntheta, zfaces, bc_r, bc_z, prec, tpf)
 
 
 def plan_destroy(plan: Plan):
