@@ -230,9 +230,11 @@ def tensor_flops(name, n):
     return 6.0 * P * n[d] if name.endswith("_tc") else None
 
 
-def run_arm(fdi, torch, prec, n, K, W, dev, rank, stream, thomas_axis=2, refine_tol=None):
+def run_arm(fdi, torch, prec, n, K, W, dev, rank, stream, thomas_axis=2, refine_tol=None, thomas_config=None):
     faces = workloads.box_faces(n, BETA)
     plan = fdi.plan_create(faces, n, prec=prec, thomas_axis=thomas_axis)
+    if thomas_config is not None and prec != fdi.PREC_FP64:
+        fdi.set_thomas_config(plan, thomas_config)
     if refine_tol is not None:
         plan.set_tolerances(refine_tol, 3)
     f = workloads.rhs_uniform(n[::-1], rank)
@@ -372,12 +374,12 @@ def pct(v, q):
     return v[min(len(v) - 1, int(q * len(v)))] if v else None
 
 
-def run_serving(fdi, prec, count, rate_hz, max_n, slots):
+def run_serving(fdi, torch, prec, count, rate_hz, max_n, slots):
     """Serving trace: Poisson arrivals (rate_hz, seed 0) of Stokes-inverse
     requests on stretched no-slip boxes (beta 1.5), cubic n uniform over
     {48, 64, 96, 128, 160, 192, 256} up to max_n, dt log-uniform in [1e-2, 1e3],
-    Re in {100, 1000, 5000}; host arrays in and out, submitted at their
-    arrival times into a server with `slots` workers and a 64 GB device budget.
+    Re in {100, 1000, 5000}; pinned host arrays in and out, submitted at their
+    arrival times into a server with `slots` workers and a 160 GB device budget.
     Host memory stays bounded: the Gaussian forcing is one seeded set per grid
     size, shared read-only by that size's requests, and the outputs come from a
     pool of buffers per size; a request whose pool buffer is still held by an
@@ -393,12 +395,23 @@ def run_serving(fdi, prec, count, rate_hz, max_n, slots):
              for _ in range(count)]
     pool_len = {256: 6, 192: 8, 160: 12, 128: 16}
     forcing, pools, owner, used = {}, {}, {}, {}
+
+    def pinned(shape, src=None):
+        # page-locked host array (a client next to the GPU keeps its buffers
+        # pinned, so the request copies run at the host link's rate)
+        t = torch.empty(tuple(shape), dtype=torch.float64, pin_memory=True)
+        a = t.numpy()
+        a[...] = 0.0 if src is None else src
+        keep.append(t)
+        return a
+
+    keep = []
     for nn in sorted({d[0] for d in draws}):
         sh = workloads.mac_shapes((nn, nn, nn))
-        forcing[nn] = [np.ascontiguousarray(workloads.rhs_gaussian(sh[c], 1000 * nn + i)) for i, c in enumerate("uvw")]
-        pools[nn] = [([np.zeros(sh[c]) for c in "uvw"], np.zeros(sh["p"])) for _ in range(pool_len.get(nn, 32))]
+        forcing[nn] = [pinned(sh[c], workloads.rhs_gaussian(sh[c], 1000 * nn + i)) for i, c in enumerate("uvw")]
+        pools[nn] = [([pinned(sh[c]) for c in "uvw"], pinned(sh["p"])) for _ in range(pool_len.get(nn, 32))]
         used[nn] = 0
-    srv = fdi.Server(64 << 30, slots)
+    srv = fdi.Server(160 << 30, slots)
     t0 = time.perf_counter()
     tickets, waits = [], 0
     for q, (nn, dt, Re) in enumerate(draws):
@@ -452,10 +465,12 @@ def main():
     ap.add_argument("--stokes-reps", type=int, default=10)
     ap.add_argument("--batch", type=int, default=64, help="batched uneven-grid solves per batch (0: skip)")
     ap.add_argument("--serve", type=int, default=2000, help="serving-trace requests, mixed precision (0: skip)")
-    ap.add_argument("--serve-fp64", type=int, default=200,
+    ap.add_argument("--serve-fp64", type=int, default=60,
                     help="serving-trace requests of the FP64 arm (the first ones of the same trace; 0: skip)")
     ap.add_argument("--serve-max-n", type=int, default=256, help="largest cubic grid in the serving trace")
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--thomas-config", type=int, default=None,
+                    help="FP32 Thomas configuration of the mixed arms (fdi_plan_set_thomas_config)")
     args = ap.parse_args()
     n = (args.n, args.n, args.n)
     P = n[0] * n[1] * n[2]
@@ -504,8 +519,11 @@ def main():
     # the TPF variant (eigen transforms in all three directions, Eq. 29) runs on the FP64 path
     # mixed_fp64tol: the mixed path refined to the FP64 path's tolerance
     helm_arms = {"fp64": (fdi.PREC_FP64, 1e-11, 2), "mixed": (fdi.PREC_MIXED_F16, 1e-10, 2),
-                 "fp64_tpf": (fdi.PREC_FP64, 1e-11, -1), "mixed_fp64tol": (fdi.PREC_MIXED_F16, 1e-11, 2)}
-    helm_names = args.arms.split(",") + ([] if args.no_tpf else ["fp64_tpf"])
+                 "fp64_tpf": (fdi.PREC_FP64, 1e-11, -1), "mixed_tpf": (fdi.PREC_MIXED_F16, 1e-10, -1),
+                 "mixed_fp64tol": (fdi.PREC_MIXED_F16, 1e-11, 2)}
+    helm_names = args.arms.split(",")
+    if not args.no_tpf:
+        helm_names += [a + "_tpf" for a in ("fp64", "mixed") if a in helm_names]
     if "mixed" in helm_names and not args.no_fp64tol:
         helm_names.append("mixed_fp64tol")
     for name in helm_names:
@@ -513,7 +531,7 @@ def main():
         try:
             slow = name == "fp64_tpf"  # FP64-pipe bound: fewer solves
             arms[name] = run_arm(fdi, torch, prec, n, max(3, K // 10) if slow else K, W, dev, rank, stream,
-                                 thomas_axis=taxis,
+                                 thomas_axis=taxis, thomas_config=args.thomas_config,
                                  refine_tol=tol if name == "mixed_fp64tol" else None)
             if slow:
                 arms[name]["K"] = max(3, K // 10)
@@ -591,13 +609,14 @@ def main():
         serving = {"config": f"Stokes-inverse requests ({args.serve} mixed, the first {args.serve_fp64} of the "
                              f"same trace FP64), Poisson arrivals at 200/s (seed 0), cubic n from {{48..256}} up to "
                              f"{args.serve_max_n}, dt log-uniform [1e-2,1e3], Re in {{100,1000,5000}}, beta 1.5, "
-                             f"{args.serve_slots} slots, 64 GB budget, tolerance 1e-10 (mixed) / 1e-11 (FP64)"}
+                             f"{args.serve_slots} slots, 160 GB budget, tolerance 1e-10 (mixed) / 1e-11 (FP64)"}
         for name in args.arms.split(","):
             count = args.serve if name == "mixed" else args.serve_fp64
             if count <= 0:
                 continue
             try:
-                serving[name] = run_serving(fdi, precs[name][0], count, 200.0, args.serve_max_n, args.serve_slots)
+                serving[name] = run_serving(fdi, torch, precs[name][0], count, 200.0, args.serve_max_n,
+                                            args.serve_slots)
             except fdi.FdiError as e:
                 serving[name] = {"error": str(e)}
     cpu = None

@@ -286,13 +286,15 @@ fdi_status fdi_eigen_noalloc(const double* faces, int n, int face_kind, fdi_bc b
 fdi_status fdi_plan_set_wait_limit(fdi_plan* plan, long long cycles);
 
 /* FP32 Thomas sweep of mixed plans: 64 or 128 lines (one per thread) per
- * CTA, or 2: two adjacent lines per thread, 64 threads per CTA (default 2).
- * A tuning knob: results are bitwise identical. */
+ * CTA; 2: two adjacent lines per thread, 64 threads per CTA (default); 3: as
+ * 2, with the forward sweep's intermediate values of the top 128 planes kept in
+ * shared memory instead of the field (64 KB per CTA).  A tuning knob: results
+ * are bitwise identical.  Other values: FDI_ERR_INVALID_ARG. */
 fdi_status fdi_plan_set_thomas_config(fdi_plan* plan, int lines_per_cta);
 
 /* Autotuner for mixed plans: times `reps` complete Helmholtz solves
  * (sigma = 1, `lambda`, rhs -> out on `stream`, after one warm-up solve each)
- * for every Thomas configuration (2, 64, 128), keeps the fastest on the plan
+ * for every Thomas configuration (2, 3, 64, 128), keeps the fastest on the plan
  * and records it for the plan's grid shape:
  * plans created later with the same shape and precision start with it.  Every
  * configuration computes bitwise-identical results.  rhs and out: device FP64
@@ -343,7 +345,9 @@ const char* fdi_status_string(fdi_status s);
  * fields) fits the device-memory budget, idle plans being evicted least
  * recently used; `slots` worker threads with one CUDA stream each run admitted
  * requests concurrently (continuous batching: a request arriving while others
- * run starts as soon as a slot and memory free up).  Each request is solved
+ * run starts as soon as a slot and memory free up); requests of at most 128^3
+ * cells run on high-priority streams, so the GPU dispatches their blocks ahead
+ * of those of larger requests running at the same time.  Each request is solved
  * exactly as a lone fdi_stokes_solve on a plan of its grid, so its result does
  * not depend on the mix.
  * ------------------------------------------------------------------------- */

@@ -46,6 +46,9 @@ namespace {
 
 constexpr int kBlocks = 152 * 8;
 constexpr int kThreads = 256;
+// per refinement round, the max |value| of each pass input: [0] r, [1] F1,
+// [2] the z step's output, [3] F4, [4] F2 and [5] the divided spectrum (TPF)
+constexpr int kScaleStride = 8;
 
 int pitch4(int n) { return (n + 3) / 4 * 4; }
 
@@ -1208,6 +1211,190 @@ __global__ void __launch_bounds__(TL) k_thomas2_f32(Thomas32Args a, const int* _
   if ((threadIdx.x & 31) == 0 && vmax > 0.f) atomicMax(reinterpret_cast<unsigned int*>(a.fmax), __float_as_uint(vmax));
 }
 
+// The same two-lines-per-thread sweep keeping d' of the top kTopBlocks blocks
+// of planes in shared memory: the forward sweep stores them there instead of
+// in the field, and the back substitution, which starts at the top, reads them
+// back without a round trip to HBM (8 bytes per point less for those planes;
+// every plane for nz <= 128).  Arithmetic and results are those of
+// k_thomas2_f32.  64 KB of dynamic shared memory per CTA.
+constexpr int kTopBlocks = 8;
+constexpr int kTopBytes = kTopBlocks * kTB * 64 * (int)sizeof(float2);
+
+template <bool FULL, bool CYL>
+__global__ void __launch_bounds__(64) k_thomas2c_f32(Thomas32Args a, const int* __restrict__ skip) {
+  constexpr int TL = 64;
+  pdl_wait();
+  if (skip && *skip) return;
+  __shared__ float4 s_co[kMaxN];
+  __shared__ float2 ring[kNBR * kTB][TL];
+  __shared__ float2 ckp[kMaxN / kTB][TL];
+  __shared__ float s_wy[CYL ? kMaxN : 1];
+  extern __shared__ float2 s_top[];  // [kTopBlocks * kTB][TL]
+  const int nz = a.nz;
+  const float lam = (float)a.lambda;
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+    const float lko_k = (k + 1 < nz) ? lam * a.koz[k] : 0.f;
+    const float lko_m = (k > 0) ? lam * a.koz[k - 1] : 0.f;
+    s_co[k] = make_float4(a.mz[k], lam * a.kdz[k], -lko_m, -lko_k);
+    if (CYL) s_wy[k] = lam * a.wy[k];
+  }
+  __syncthreads();
+  const int tid = threadIdx.x;
+  const int npair = (a.ny + 1) / 2;
+  const long long t = (long long)blockIdx.x * blockDim.x + tid;
+  float vmax = 0.f;
+  if (t < (long long)a.nx * npair) {
+    const int i = (int)(t / npair), j0 = 2 * (int)(t % npair);
+    const bool second = j0 + 1 < a.ny;
+    const int pl2 = (int)(a.plane / 2);
+    const double lab0 = a.lamx[i] + a.lamy[j0];
+    const double lab1 = a.lamx[i] + a.lamy[second ? j0 + 1 : j0];
+    if (!(a.singular_possible && (lab0 == 0.0 || lab1 == 0.0))) {
+      const float s0 = (float)(a.sigma - a.lambda * (CYL ? a.lamx[i] : lab0));
+      const float s1 = (float)(a.sigma - a.lambda * (CYL ? a.lamx[i] : lab1));
+      const float ly0 = CYL ? (float)(-a.lamy[j0]) : 0.f;
+      const float ly1 = CYL ? (float)(-a.lamy[second ? j0 + 1 : j0]) : 0.f;
+      float2* f = reinterpret_cast<float2*>(a.f + (long long)i * a.pitch + j0);
+      const int nb = (nz + kTB - 1) / kTB;
+      const int gb = nb > kTopBlocks ? nb - kTopBlocks : 0;  // blocks below gb go through the field
+      const unsigned ring0 = (unsigned)__cvta_generic_to_shared(&ring[0][tid]);
+      auto fetch = [&](int b) {
+        if (b >= 0 && b < nb) {
+          const unsigned dst = ring0 + (unsigned)((b % kNBR) * kTB * TL * 8);
+          const float2* src = f + (long long)b * kTB * pl2;
+          const int cnt = FULL ? kTB : min(kTB, nz - b * kTB);
+#pragma unroll
+          for (int e = 0; e < kTB; ++e)
+            if (FULL || e < cnt) cp_async8(dst + e * TL * 8, src + e * pl2);
+        }
+        cp_async_commit();
+      };
+      for (int q = 0; q < kNBR - 1; ++q) fetch(q);
+      float cp0 = 0.f, dp0 = 0.f, cp1 = 0.f, dp1 = 0.f;
+      for (int b = 0; b < nb; ++b) {
+        fetch(b + kNBR - 1);
+        cp_async_wait<kNBR - 1>();
+        ckp[b][tid] = make_float2(cp0, cp1);
+        const float2* rs = &ring[(b % kNBR) * kTB][tid];
+        float2* fo = f + (long long)b * kTB * pl2;
+        float2* to = &s_top[(b - gb) * kTB * TL + tid];
+        const int k0 = b * kTB;
+#pragma unroll
+        for (int e = 0; e < kTB; ++e) {
+          if (FULL || k0 + e < nz) {
+            const float4 co = s_co[k0 + e];
+            const float2 fv = rs[e * TL];
+            const float inv0 = rcp_fast(fmaf(-co.z, cp0, thomas_diag<CYL>(s0, ly0, co, s_wy, k0 + e)));
+            const float inv1 = rcp_fast(fmaf(-co.z, cp1, thomas_diag<CYL>(s1, ly1, co, s_wy, k0 + e)));
+            cp0 = co.w * inv0;
+            cp1 = co.w * inv1;
+            dp0 = fmaf(co.x, fv.x, -co.z * dp0) * inv0;
+            dp1 = fmaf(co.x, fv.y, -co.z * dp1) * inv1;
+            if (b >= gb)
+              to[e * TL] = make_float2(dp0, dp1);
+            else
+              fo[e * pl2] = make_float2(dp0, dp1);
+          }
+        }
+      }
+      cp_async_wait<0>();
+      // back substitution: the on-chip blocks first, then the field's, whose
+      // copies are requested kNBR - 1 blocks ahead
+      for (int q = 0; q < kNBR - 1; ++q) fetch(gb - 1 - q);
+      float u0 = 0.f, u1 = 0.f;
+      for (int b = nb - 1; b >= 0; --b) {
+        if (b < gb) fetch(b - (kNBR - 1));
+        const int k0 = b * kTB;
+        float cpb0[kTB], cpb1[kTB];
+        const float2 cc = ckp[b][tid];
+        float c0 = cc.x, c1 = cc.y;
+#pragma unroll
+        for (int e = 0; e < kTB; ++e) {
+          if (FULL || k0 + e < nz) {
+            const float4 co = s_co[k0 + e];
+            c0 = co.w * rcp_fast(fmaf(-co.z, c0, thomas_diag<CYL>(s0, ly0, co, s_wy, k0 + e)));
+            c1 = co.w * rcp_fast(fmaf(-co.z, c1, thomas_diag<CYL>(s1, ly1, co, s_wy, k0 + e)));
+          }
+          cpb0[e] = c0;
+          cpb1[e] = c1;
+        }
+        const float2* rs;
+        int rstride;
+        if (b < gb) {
+          cp_async_wait<kNBR - 1>();
+          rs = &ring[(b % kNBR) * kTB][tid];
+        } else {
+          rs = &s_top[(b - gb) * kTB * TL + tid];
+        }
+        rstride = TL;
+        float2* fo = f + (long long)k0 * pl2;
+#pragma unroll
+        for (int e = kTB - 1; e >= 0; --e) {
+          if (FULL || k0 + e < nz) {
+            const float2 dv = rs[e * rstride];
+            u0 = fmaf(-cpb0[e], u0, dv.x);
+            u1 = fmaf(-cpb1[e], u1, dv.y);
+            fo[e * pl2] = make_float2(u0, u1);
+            vmax = fmaxf(vmax, fabsf(u0));
+            if (second) vmax = fmaxf(vmax, fabsf(u1));
+          }
+        }
+      }
+      cp_async_wait<0>();
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  if ((threadIdx.x & 31) == 0 && vmax > 0.f) atomicMax(reinterpret_cast<unsigned int*>(a.fmax), __float_as_uint(vmax));
+}
+
+// TPF spectral divide (Eq. 26-28 with sigma): f[k][i][j] /= sigma - lambda
+// (Lambda_x,i + Lambda_y,j + Lambda_z,k) on the padded [nz][nx][py] layout
+// (padding columns untouched), and max |result|.  The shifted eigenvalues are
+// FP32 (every term has the same sign, so the sum loses nothing to
+// cancellation); the null mode of the singular zero-flux Laplacian is set to 0.
+// One warp per (k, i) row, four columns per lane and step.
+__global__ void __launch_bounds__(256) k_divide_tpf(float* __restrict__ f, int nx, int ny, int py, int nz,
+                                                    const double* __restrict__ lx, const double* __restrict__ ly,
+                                                    const double* __restrict__ lz, double sigma, double lambda,
+                                                    int singular, float* __restrict__ fmax,
+                                                    const int* __restrict__ skip) {
+  pdl_wait();
+  if (skip && *skip) return;
+  __shared__ float s_lx[kMaxN], s_ly[kMaxN], s_lz[kMaxN];
+  for (int t = threadIdx.x; t < kMaxN; t += blockDim.x) {
+    s_lx[t] = t < nx ? (float)(-lambda * lx[t]) : 0.f;
+    s_ly[t] = t < ny ? (float)(-lambda * ly[t]) : 0.f;
+    s_lz[t] = t < nz ? (float)(-lambda * lz[t]) : 0.f;
+  }
+  __syncthreads();
+  const float sg = (float)sigma;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  float vmax = 0.f;
+  for (long long row = (long long)blockIdx.x * 8 + warp; row < (long long)nz * nx; row += (long long)gridDim.x * 8) {
+    const int i = (int)(row % nx), k = (int)(row / nx);
+    const float base = sg + s_lx[i] + s_lz[k];
+    float4* fr = reinterpret_cast<float4*>(f + row * py);
+    for (int q = lane; q < py / 4; q += 32) {
+      float4 v = fr[q];
+      float* e = reinterpret_cast<float*>(&v);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int j = 4 * q + c;
+        if (j < ny) {
+          const float den = base + s_ly[j];
+          e[c] = (singular && den == 0.f) ? 0.f : e[c] / den;
+          vmax = fmaxf(vmax, fabsf(e[c]));
+        }
+      }
+      fr[q] = v;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+  if (lane == 0 && vmax > 0.f) atomicMax(reinterpret_cast<unsigned int*>(fmax), __float_as_uint(vmax));
+}
+
 __global__ void k_absmax(const float* __restrict__ in, long long rows, int n, int pitch, float* __restrict__ mx) {
   float v = 0.f;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < rows * n;
@@ -1288,8 +1475,8 @@ fdi_status mixed_setup(fdi_plan* p) {
     set_error("mixed precision modes other than FDI_PREC_MIXED_F16 are not built");
     return FDI_ERR_UNSUPPORTED;
   }
-  if (p->thomas_axis != 2) {
-    set_error("the mixed-precision path runs TPT (thomas_axis 0, 1, 2 or -2), not TPF (-1)");
+  if (p->thomas_axis == -1 && p->cyl) {
+    set_error("the cylindrical TPF runs on the FP64 path only");
     return FDI_ERR_UNSUPPORTED;
   }
   cudaStream_t s;
@@ -1319,12 +1506,23 @@ fdi_status mixed_alloc_workspace(fdi_plan* p) {
   const size_t szw = std::max(szr, szf);  // F1 and F4 take either orientation
   FDI_CUDA_TRY(cudaMalloc(&p->wf[0], szw * sizeof(float)));   // r, reused as F4
   FDI_CUDA_TRY(cudaMalloc(&p->wf[1], szw * sizeof(float)));   // F1
-  FDI_CUDA_TRY(cudaMalloc(&p->wf[2], szw * sizeof(float)));   // F2 / F3
-  FDI_CUDA_TRY(cudaMalloc(&p->wf[3], szw * sizeof(float)));   // Thomas scratch
+  FDI_CUDA_TRY(cudaMalloc(&p->wf[2], szw * sizeof(float)));   // F2
+  FDI_CUDA_TRY(cudaMalloc(&p->wf[3], szw * sizeof(float)));   // Thomas scratch / TPF spectrum F3
+  // rows are padded to 4 floats and no pass writes the padding: keep it zero
+  // (the TPF z passes read whole padded planes)
+  {
+    cudaStream_t ms = nullptr;
+    FDI_CUDA_TRY(cudaStreamCreateWithFlags(&ms, cudaStreamNonBlocking));
+    cudaError_t e = cudaMemsetAsync(p->wf[2], 0, szw * sizeof(float), ms);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->wf[3], 0, szw * sizeof(float), ms);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ms);
+    cudaStreamDestroy(ms);
+    FDI_CUDA_TRY(e);
+  }
   FDI_CUDA_TRY(cudaMalloc(&p->xdf, (size_t)p->Pmax * 3 * sizeof(float)));  // planes H, L, low part of L
   FDI_CUDA_TRY(cudaMalloc(&p->wr1, szr * 2 * sizeof(float)));              // r_1 as (hi, lo) planes
   p->wr1_plane = (long long)szr;
-  FDI_CUDA_TRY(cudaMalloc(&p->d_scales, (size_t)(kMaxRefineCap + 2) * 4 * sizeof(float)));
+  FDI_CUDA_TRY(cudaMalloc(&p->d_scales, (size_t)(kMaxRefineCap + 2) * kScaleStride * sizeof(float)));
   FDI_CUDA_TRY(cudaMalloc(&p->lam_w, (size_t)10 * kMaxN * sizeof(float2)));
   FDI_CUDA_TRY(cudaMalloc(&p->d_counter, 4 * sizeof(unsigned)));
   FDI_CUDA_TRY(cudaMemset(p->d_counter, 0, 4 * sizeof(unsigned)));
@@ -1348,6 +1546,31 @@ fdi_status launch_thomas32(fdi_plan* p, const Thomas32Args& ta, bool pdl, bool s
     FDI_LAUNCH_CHECK(p);
     if (singular) {
       // the null line (0, 0) and its pair partner, one line per thread
+      Thomas32Args t1 = ta;
+      t1.nx = 1;
+      t1.ny = std::min(ta.ny, 2);
+      if (full)
+        k_thomas_f32<64, true, CYL><<<1, 64, 0, s>>>(t1, skip);
+      else
+        k_thomas_f32<64, false, CYL><<<1, 64, 0, s>>>(t1, skip);
+      FDI_LAUNCH_CHECK(p);
+    }
+    return FDI_OK;
+  }
+  if (p->thomas_tl == 3) {
+    // two lines per thread with the top planes' d' on chip
+    static bool attr[2] = {false, false};
+    auto kfull = k_thomas2c_f32<true, CYL>;
+    auto kpart = k_thomas2c_f32<false, CYL>;
+    if (!attr[full ? 1 : 0]) {
+      FDI_CUDA_TRY(cudaFuncSetAttribute(full ? kfull : kpart, cudaFuncAttributeMaxDynamicSharedMemorySize, kTopBytes));
+      attr[full ? 1 : 0] = true;
+    }
+    const long long pairs = (long long)ta.nx * ((ta.ny + 1) / 2);
+    const unsigned g = (unsigned)((pairs + 63) / 64);
+    FDI_CUDA_TRY(launch_pdl(pdl, full ? kfull : kpart, dim3(g), dim3(64), (size_t)kTopBytes, s, ta, skip));
+    FDI_LAUNCH_CHECK(p);
+    if (singular) {
       Thomas32Args t1 = ta;
       t1.nx = 1;
       t1.ny = std::min(ta.ny, 2);
@@ -1385,7 +1608,7 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
   const MixedAxis* my = static_cast<const MixedAxis*>(f.ax[1]->mixed);
   const MixedAxis* mz = static_cast<const MixedAxis*>(f.ax[2]->mixed);
   FDI_TRY(launch_reset_status(p, s));
-  FDI_CUDA_TRY(cudaMemsetAsync(p->d_scales, 0, (size_t)(kMaxRefineCap + 2) * 4 * sizeof(float), s));
+  FDI_CUDA_TRY(cudaMemsetAsync(p->d_scales, 0, (size_t)(kMaxRefineCap + 2) * kScaleStride * sizeof(float), s));
   const double* b = rhs;
   if (out == rhs) {
     FDI_CUDA_TRY(cudaMemcpyAsync(p->ws[4], rhs, f.P * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1473,8 +1696,8 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
   auto enqueue_round = [&](int round, cudaStream_t s, cudaGraphConditionalHandle next_round) -> fdi_status {
     const bool pdl = p->pdl && round < 2;  // later rounds may run inside conditional graph bodies
     const int* skip = round == 0 ? nullptr : done;
-    float* sc = p->d_scales + 4 * round;
-    float* sc_next = p->d_scales + 4 * (round + 1);
+    float* sc = p->d_scales + kScaleStride * round;
+    float* sc_next = p->d_scales + kScaleStride * (round + 1);
     // forward x: r [z][y][x] -> F1 [z][i][y] (round 1 reads r_1 from its own planes)
     TcArgs t{};
     t.pdl = pdl ? 1 : 0;
@@ -1518,10 +1741,52 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
     t.slab_stride = 0;
     t.row_stride = py;
     t.col_stride = 1;
-    t.scale_out = nullptr;
+    const bool tpf = p->thomas_axis == -1;
+    t.scale_out = tpf ? sc + 4 : nullptr;  // TPF: the z transform needs the scale of F2
     FDI_TRY(launch_tc_transform(p, my->fwd, t, "transform_yf_tc", s));
-    // Thomas along z, in place on F2
-    {
+    if (tpf) {
+      // TPF (Eq. 29): z transform, spectral divide, back z transform.  F2
+      // [z][i][j] is read with the contraction index z strided: the padded
+      // plane (nx * py values) is one MN-major slab of R = nx * py rows, and
+      // the transforms write [z'][i][j] back in the same layout
+      const int plane = nx * py;
+      TcArgs tz{};
+      tz.pdl = t.pdl;
+      tz.skip = skip;
+      tz.err = p->d_err;
+      tz.in = F2;
+      tz.R = plane;
+      tz.K = nz;
+      tz.in_pitch = plane;
+      tz.a_mn = 1;
+      tz.a_mslab = plane;
+      tz.a_rows = nz;
+      tz.scale_in = sc + 4;
+      tz.mode = TC_OUT_F32;
+      tz.n_out = nz;
+      tz.out_f32 = CS;
+      tz.S = plane;
+      tz.slab_stride = 0;
+      tz.row_stride = 1;
+      tz.col_stride = plane;
+      tz.scale_out = nullptr;  // the divide measures its own output
+      FDI_TRY(launch_tc_transform(p, mz->fwd, tz, "transform_zf_tc", s));
+      {
+        FDI_KTIMER(p, "divide_f32", s);
+        const long long rows = (long long)nz * nx;
+        FDI_CUDA_TRY(launch_pdl(pdl, k_divide_tpf, dim3((unsigned)std::min<long long>((rows + 7) / 8, 152 * 8)),
+                                dim3(256), 0, s, CS, nx, ny, py, nz, (const double*)f.ax[0]->lam,
+                                (const double*)f.ax[1]->lam, (const double*)f.ax[2]->lam, sigma, lambda,
+                                singular ? 1 : 0, sc + 5, skip));
+        FDI_LAUNCH_CHECK(p);
+      }
+      tz.in = CS;
+      tz.scale_in = sc + 5;
+      tz.out_f32 = F2;
+      tz.scale_out = sc + 2;
+      FDI_TRY(launch_tc_transform(p, mz->bwd, tz, "transform_zb_tc", s));
+    } else {
+      // Thomas along z, in place on F2
       FDI_KTIMER(p, "thomas_z_f32", s);
       Thomas32Args ta;
       ta.f = F2;

@@ -106,7 +106,7 @@ extern "C" size_t fdi_stokes_plan_bytes_estimate(const int n[3], int prec) {
   size_t slot = 5 * (size_t)P * 8 + (size_t)16384 * 4 * 8;  // FP64 workspace, partials
   if (prec != FDI_PREC_FP64) slot += 4 * Pp * 4 + 3 * (size_t)P * 4 + 2 * Pp * 4;
   b += 4 * slot;
-  b += 10 * (size_t)P * 8 + 6 * (size_t)P * 8;  // Krylov vectors, face work fields
+  b += 11 * (size_t)P * 8 + 6 * (size_t)P * 8;  // Krylov vectors, cell volumes, face work fields
   b += (size_t)4 << 20;                          // small tables, slack
   return b;
 }
@@ -179,10 +179,19 @@ bool try_admit(fdi_server* sv, Request* rq, PlanEntry** entry, bool* need_new, s
   return true;
 }
 
+// Requests up to this many cells run on a worker's high-priority stream: the
+// GPU dispatches their blocks ahead of those of large requests running on
+// other workers, so a small request's many short kernels are not queued behind
+// a large solve's blocks (results are unaffected: the same launches run).
+constexpr long long kHighPriorityCells = 128LL * 128 * 128;
+
 void worker(fdi_server* sv) {
   cudaSetDevice(sv->device);
-  cudaStream_t s = nullptr;
-  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  cudaStream_t s_lo = nullptr, s_hi = nullptr;
+  if (cudaStreamCreateWithPriority(&s_lo, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&s_hi, cudaStreamNonBlocking, prio_hi) != cudaSuccess) {
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->worker_error = FDI_ERR_CUDA;
     return;
@@ -218,6 +227,7 @@ void worker(fdi_server* sv) {
       sv->running += 1;
     }
     const fdi_stokes_request& r = rq->req;
+    cudaStream_t s = cells(r.n) <= kHighPriorityCells ? s_hi : s_lo;
     fdi_status st = FDI_OK;
     fdi_plan* plan = plan_in;
     if (need_new) {
@@ -301,7 +311,8 @@ void worker(fdi_server* sv) {
     sv->cv.notify_all();
     sv->cv_done.notify_all();
   }
-  cudaStreamDestroy(s);
+  cudaStreamDestroy(s_lo);
+  cudaStreamDestroy(s_hi);
 }
 
 double percentile(std::vector<double> v, double q) {

@@ -453,7 +453,8 @@ fdi_status fdi_helmholtz_solve_batched(fdi_plan* const* plans, const double* lam
 }
 
 fdi_status fdi_plan_set_thomas_config(fdi_plan* plan, int lines_per_cta) {
-  if (!plan || (lines_per_cta != 2 && lines_per_cta != 64 && lines_per_cta != 128)) return FDI_ERR_INVALID_ARG;
+  if (!plan || (lines_per_cta != 2 && lines_per_cta != 3 && lines_per_cta != 64 && lines_per_cta != 128))
+    return FDI_ERR_INVALID_ARG;
   plan->thomas_tl = lines_per_cta;
   invalidate_graph(plan);
   return FDI_OK;
@@ -466,7 +467,7 @@ fdi_status fdi_plan_autotune(fdi_plan* plan, double lambda, const double* rhs, d
   if (!rhs || !out || rhs == out || reps < 1 || reps > 1000) return FDI_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (plan->prec != FDI_PREC_FP64) {
-    const int tls[3] = {2, 64, 128};
+    const int tls[4] = {2, 3, 64, 128};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     FDI_CUDA_TRY(cudaEventCreate(&e0));
     FDI_CUDA_TRY(cudaEventCreate(&e1));
@@ -475,7 +476,7 @@ fdi_status fdi_plan_autotune(fdi_plan* plan, double lambda, const double* rhs, d
     const bool timing = plan->timing;
     plan->timing = false;
     {
-      for (int ti = 0; ti < 3 && st == FDI_OK; ++ti) {
+      for (int ti = 0; ti < 4 && st == FDI_OK; ++ti) {
         plan->thomas_tl = tls[ti];
         st = field_solve(plan, FDI_FIELD_CELL, 1.0, lambda, rhs, out, s);  // warm-up
         if (st != FDI_OK) break;

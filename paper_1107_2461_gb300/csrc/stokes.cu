@@ -55,20 +55,38 @@ struct MacGeom {
   const double* ih[3];   // 1 / h_i (cell widths), n_d each
   const double* idc[3];  // 1 / (c_j - c_{j-1}), interior faces, n_d - 1 each
   const double* m[3];    // cell widths (volumes = products)
+  const double* vol;     // cell volumes, [z][y][x]
 };
 
-// g_c = scale * (G q)_c on the interior faces (Eq. 31's D_p)
-__global__ void k_grad(MacGeom g, const double* __restrict__ q, double scale, double* __restrict__ gu,
-                       double* __restrict__ gv, double* __restrict__ gw) {
+// cell volumes m_x[i] m_y[j] m_z[k] of the pressure grid
+__global__ void k_volumes(MacGeom g, double* __restrict__ vol) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q % g.nx);
+    const long long t = q / g.nx;
+    const int j = (int)(t % g.ny), k = (int)(t / g.ny);
+    vol[q] = g.m[0][i] * g.m[1][j] * g.m[2][k];
+  }
+}
+
+// g_c = (G q)_c, or -(G q)_c with NEG, on the interior faces (Eq. 31's D_p):
+// one FP64 difference and one product per face (GB300 runs FP64 at 2
+// operations per clock per SM, so the sign is folded into the product)
+template <bool NEG>
+__global__ void k_grad(MacGeom g, const double* __restrict__ q, double* __restrict__ gu, double* __restrict__ gv,
+                       double* __restrict__ gw) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   if (i >= nx || j >= ny) return;
   const long long c = ((long long)k * ny + j) * nx + i;
   const double qc = q[c];
-  if (i + 1 < nx) gu[((long long)k * ny + j) * (nx - 1) + i] = scale * ((q[c + 1] - qc) * g.idc[0][i]);
-  if (j + 1 < ny) gv[((long long)k * (ny - 1) + j) * nx + i] = scale * ((q[c + nx] - qc) * g.idc[1][j]);
-  if (k + 1 < nz) gw[((long long)k * ny + j) * nx + i] = scale * ((q[c + (long long)nx * ny] - qc) * g.idc[2][k]);
+  const double sx = NEG ? -g.idc[0][min(i, nx - 2)] : g.idc[0][min(i, nx - 2)];
+  const double sy = NEG ? -g.idc[1][min(j, ny - 2)] : g.idc[1][min(j, ny - 2)];
+  const double sz = NEG ? -g.idc[2][min(k, nz - 2)] : g.idc[2][min(k, nz - 2)];
+  if (i + 1 < nx) gu[((long long)k * ny + j) * (nx - 1) + i] = (q[c + 1] - qc) * sx;
+  if (j + 1 < ny) gv[((long long)k * (ny - 1) + j) * nx + i] = (q[c + nx] - qc) * sy;
+  if (k + 1 < nz) gw[((long long)k * ny + j) * nx + i] = (q[c + (long long)nx * ny] - qc) * sz;
 }
 
 // y = D h at the cells (Eq. 30's D_u), wall velocities zero
@@ -456,10 +474,7 @@ __global__ void __launch_bounds__(kDotThreads) k_vsum(MacGeom g, const double* _
   const long long n = (long long)g.nx * g.ny * g.nz;
   double s0 = 0.0, s1 = 0.0;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % g.nx);
-    const long long t = q / g.nx;
-    const int j = (int)(t % g.ny), k = (int)(t / g.ny);
-    const double v = g.m[0][i] * g.m[1][j] * g.m[2][k];
+    const double v = g.vol[q];
     s0 = fma(v, x[q], s0);
     s1 += v;
   }
@@ -496,14 +511,10 @@ __global__ void k_axpy(double* __restrict__ y, double c, const double* __restric
 __global__ void __launch_bounds__(kDotThreads) k_wdot(MacGeom g, const double* __restrict__ a,
                                                       const double* __restrict__ b, const double* __restrict__ c,
                                                       double* __restrict__ partials) {
-  const int nx = g.nx, ny = g.ny;
-  const long long n = (long long)nx * ny * g.nz;
+  const long long n = (long long)g.nx * g.ny * g.nz;
   double s0 = 0.0, s1 = 0.0;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(q % nx);
-    const long long t = q / nx;
-    const int j = (int)(t % ny), k = (int)(t / ny);
-    const double vb = g.m[0][i] * g.m[1][j] * g.m[2][k] * b[q];
+    const double vb = g.vol[q] * b[q];
     s0 = fma(vb, a[q], s0);
     if (c) s1 = fma(vb, c[q], s1);
   }
@@ -612,6 +623,7 @@ MacGeom geom(const fdi_plan* p) {
     g.idc[d] = p->mac_idc[d];
     g.m[d] = p->fields[FDI_FIELD_CELL].ax[d]->m;
   }
+  g.vol = p->sk[10];
   return g;
 }
 
@@ -633,8 +645,20 @@ fdi_status stokes_setup(fdi_plan* p) {
   const long long Pc = p->fields[FDI_FIELD_CELL].P;
   long long Pf = 0;
   for (int c = 1; c <= 3; ++c) Pf = std::max(Pf, p->fields[c].P);
-  for (int i = 0; i < 10; ++i) FDI_TRY(dalloc(&p->sk[i], Pc));   // b x r rhat p v s t y z
+  for (int i = 0; i < 11; ++i) FDI_TRY(dalloc(&p->sk[i], Pc));   // b x r rhat p v s t y z, cell volumes
   for (int i = 0; i < 6; ++i) FDI_TRY(dalloc(&p->skf[i], Pf));  // g_u g_v g_w h_u h_v h_w
+  {
+    // on a private stream (plans may be created while other threads capture
+    // or run work on theirs)
+    cudaStream_t vs = nullptr;
+    FDI_CUDA_TRY(cudaStreamCreateWithFlags(&vs, cudaStreamNonBlocking));
+    const MacGeom g = geom(p);
+    k_volumes<<<kDotBlocks, kDotThreads, 0, vs>>>(g, p->sk[10]);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(vs);
+    cudaStreamDestroy(vs);
+    FDI_CUDA_TRY(e);
+  }
   FDI_TRY(dalloc(&p->d_kry, 2));
   FDI_TRY(dalloc(&p->kpartials, 2 * kDotBlocks));
   return FDI_OK;
@@ -669,7 +693,7 @@ fdi_status cmatvec(fdi_plan* p, const MacGeom& g, double lambda, double* q, doub
   dim3 blk(32, 8), grd((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz);
   {
     FDI_KTIMER(p, "stokes_grad", s);
-    k_grad<<<grd, blk, 0, s>>>(g, q, -1.0, p->skf[0], p->skf[1], p->skf[2]);
+    k_grad<true><<<grd, blk, 0, s>>>(g, q, p->skf[0], p->skf[1], p->skf[2]);
     FDI_LAUNCH_CHECK(p);
   }
   {
@@ -972,7 +996,7 @@ fdi_status stokes_solve(fdi_plan* p, double dt, double Re, const double* const f
     FDI_LAUNCH_CHECK(p);
   }
   // step 3: u_c = u_hat_c - H_c^{-1} (G q)_c   (x holds q; grad with +1)
-  k_grad<<<grd, blk, 0, s>>>(g, x, 1.0, p->skf[0], p->skf[1], p->skf[2]);
+  k_grad<false><<<grd, blk, 0, s>>>(g, x, p->skf[0], p->skf[1], p->skf[2]);
   FDI_LAUNCH_CHECK(p);
   {
     const double* in[3] = {p->skf[0], p->skf[1], p->skf[2]};

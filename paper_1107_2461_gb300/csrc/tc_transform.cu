@@ -687,8 +687,12 @@ fdi_status launch_tc_transform(fdi_plan* p, const TcMatrix& m, TcArgs args, cons
     return FDI_ERR_CUDA;
   }
   CUtensorMap mapA;
-  if (args.a_mn && (args.a_mslab % BM != 0 || args.R % args.a_mslab != 0 || args.a_mslab > args.in_pitch ||
-                    args.a_rows < (args.R / args.a_mslab) * (long long)args.K || args.a_rows > 0x7fffffffLL)) {
+  // MN-major slabs hold whole 128-row tiles, or there is one slab as wide as
+  // the tensor row (a ragged last tile then reads the zero fill past its end)
+  const bool one_slab = args.a_mslab == args.R && args.a_mslab == args.in_pitch;
+  if (args.a_mn && ((args.a_mslab % BM != 0 && !one_slab) || args.R % args.a_mslab != 0 ||
+                    args.a_mslab > args.in_pitch || args.a_rows < (args.R / args.a_mslab) * (long long)args.K ||
+                    args.a_rows > 0x7fffffffLL)) {
     set_error("MN-major transform input: slabs must hold whole 128-row tiles");
     return FDI_ERR_INVALID_ARG;
   }

@@ -173,3 +173,60 @@ def test_mixed_refined_to_fp64_tolerance(fdi):
         got = out.cpu().numpy()
         assert st == 0 and rel <= 1e-11, (lam, sigma, steps, rel)
         assert asm.relative_residual(ops, got, f, lam, sigma) <= 1e-11
+
+
+def _mixed_tpf(fdi, faces, bc, lam, sigma, f, tol=None):
+    import torch
+    n = tuple(len(fc) - 1 for fc in faces)
+    plan = fdi.plan_create(faces, n, bc, bc, prec=fdi.PREC_MIXED_F16, thomas_axis=-1)
+    try:
+        # a pipeline that stops making progress reports a wait limit quickly
+        fdi.set_wait_limit(plan, 100_000_000)
+        if tol is not None:
+            plan.set_tolerances(tol, 3)
+        rhs = torch.from_numpy(np.ascontiguousarray(f)).cuda()
+        out = torch.empty_like(rhs)
+        fdi.field_solve(plan, fdi.FIELD_CELL, sigma, lam, rhs, out)
+        torch.cuda.synchronize()
+        _, steps, rel, st = fdi.last_result(plan)
+    finally:
+        plan.destroy()
+    return out.cpu().numpy(), steps, rel, st
+
+
+@pytest.mark.parametrize("n,bc,lam,sigma", [
+    ((16, 12, 9), (D, D, D), 1.0, 1.0),       # one z chunk, ragged plane (192 rows)
+    ((40, 36, 33), (N, D, N), 1e-3, 1.0),     # two z chunks, ragged chunk
+    ((24, 20, 70), (D, N, D), 1.0, 0.0),      # three z chunks, Laplacian
+    ((32, 28, 17), (N, N, N), 1.0, 0.0),      # the singular zero-flux Laplacian
+])
+def test_mixed_tpf_small(fdi, n, bc, lam, sigma):
+    # mixed-precision TPF (Eq. 29): the z transforms on the tensor cores and the
+    # spectral divide, refined to 1e-10, against the oracle's TPF and its
+    # assembled operator
+    faces = box_faces(n, 1.5)
+    ops = asm.cell_ops(faces, bc, bc)
+    f = rhs_uniform(n[::-1], 31)
+    got, steps, rel, st = _mixed_tpf(fdi, faces, bc, lam, sigma, f)
+    assert st == 0 and rel <= MIXED_TOL, (steps, rel, st)
+    assert asm.relative_residual(ops, got, f, lam, sigma) <= MIXED_TOL
+    ref = dec.tpf_solve(f, ops, lam, sigma)
+    if sigma == 0.0 and bc == (N, N, N):
+        V = asm.volumes(ops)
+        got = got - np.sum(V * got.ravel()) / V.sum()
+        ref = ref - np.sum(V * ref.ravel()) / V.sum()
+    assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n", [(128, 64, 40), (128, 128, 128), (256, 256, 256)])
+def test_mixed_tpf_at_scale(fdi, n):
+    # larger grids, after the small ones: many plane tiles, two to eight z
+    # chunks; the 256^3 benchmark grid included
+    faces = box_faces(n, 1.5)
+    ops = asm.cell_ops(faces, (D, D, D), (D, D, D))
+    f = rhs_uniform(n[::-1], 7)
+    got, steps, rel, st = _mixed_tpf(fdi, faces, (D, D, D), 1.0, 1.0, f)
+    assert st == 0 and rel <= MIXED_TOL, (steps, rel, st)
+    assert asm.relative_residual(ops, got, f, 1.0) <= MIXED_TOL
+    ref = dec.tpf_solve(f, ops, 1.0)
+    assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
