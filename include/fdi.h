@@ -285,11 +285,17 @@ fdi_status fdi_eigen_noalloc(const double* faces, int n, int face_kind, fdi_bc b
  * the call and have no such waits.  cycles < 0: FDI_ERR_INVALID_ARG. */
 fdi_status fdi_plan_set_wait_limit(fdi_plan* plan, long long cycles);
 
-/* FP32 Thomas sweep of mixed plans: 64 or 128 lines (one per thread) per
- * CTA; 2: two adjacent lines per thread, 64 threads per CTA (default); 3: as
- * 2, with the forward sweep's intermediate values of the top 128 planes kept in
- * shared memory instead of the field (64 KB per CTA).  A tuning knob: results
- * are bitwise identical.  Other values: FDI_ERR_INVALID_ARG. */
+/* Thomas sweep of mixed plans: 64 or 128 lines (one per thread) per CTA;
+ * 2: two adjacent lines per thread, 64 threads per CTA (default); 3: as 2,
+ * with the forward sweep's intermediate values of the top 128 planes kept in
+ * shared memory instead of the field (64 KB per CTA).  These four are FP32
+ * recurrences and a tuning knob: their results are bitwise identical.
+ * 4: an FP64 recurrence on the FP32 fields with the line factors (reciprocal
+ * pivots and c') cached per (sigma, lambda, field) in every workspace
+ * (allocated by this call: 16 bytes per point per workspace); results differ
+ * from the FP32 sweeps by rounding, within the refinement.  The singular
+ * zero-flux Laplacian keeps the FP32 sweep.  FP64 plans always sweep in FP64
+ * with such a cache.  Other values: FDI_ERR_INVALID_ARG. */
 fdi_status fdi_plan_set_thomas_config(fdi_plan* plan, int lines_per_cta);
 
 /* Autotuner for mixed plans: times `reps` complete Helmholtz solves

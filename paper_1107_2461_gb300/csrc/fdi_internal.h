@@ -73,6 +73,8 @@ struct fdi_work_slot {
   double* partials = nullptr;
   fdi::DevStatus* d_status = nullptr;
   unsigned* d_counter = nullptr;
+  double* tf = nullptr;             // Thomas factor cache (see fdi_plan::tf)
+  long long tf_q = 0;
 };
 
 struct fdi_plan {
@@ -108,6 +110,12 @@ struct fdi_plan {
   cudaStream_t cstream = nullptr;   // mixed plans: captures the bodies of conditional refinement rounds
   double* partials = nullptr;       // reduction partials
   int npartials = 0;
+  // Thomas factor cache of this workspace: the reciprocal pivots and c' of
+  // every z line ([k][line], tf_q doubles each) for the (sigma, lambda, field)
+  // stored in the 4 doubles after them; a sweep whose arguments match reuses
+  // them (decided on the device), any other sweep recomputes and stores them
+  double* tf = nullptr;
+  long long tf_q = 0;
   fdi::DevStatus* d_status = nullptr;
   int* h_flag = nullptr;            // pinned host flag for Krylov convergence
   // Stokes workspace (MAC plans): 10 cell vectors, 6 face fields, geometry
@@ -312,7 +320,14 @@ fdi_status launch_modes_f64(fdi_plan* p, const double* in, double* out, const do
                             int ny, const int* skip, cudaStream_t s);
 fdi_status launch_divide_modes_f64(fdi_plan* p, const Field& f, double sigma, double lambda, double* data,
                                   const int* skip, cudaStream_t s);
-fdi_status launch_thomas_f64(fdi_plan* p, const Field& f, double sigma, double lambda, const double* in,
+// Thomas factor cache of the plan's current workspace: allocated for q line
+// points (FP64 plans at creation, mixed plans when configuration 4 is chosen)
+fdi_status alloc_thomas_cache(fdi_plan* p, long long q);
+// cached-factor FP64 sweep over FP32 data in the mixed path's layout
+// (configuration 4); f, layout and coefficients as the FP32 sweeps
+fdi_status launch_thomas_cached_f32(fdi_plan* p, const Field& f, double sigma, double lambda, int field, float* data,
+                                    int pitch, long long plane, float* fmax, const int* skip, cudaStream_t s);
+fdi_status launch_thomas_f64(fdi_plan* p, const Field& f, double sigma, double lambda, int field, const double* in,
                              double* out, double* scratch, const int* skip, cudaStream_t s);
 fdi_status launch_divide_f64(fdi_plan* p, const Field& f, double sigma, double lambda, double* data,
                              const int* skip, cudaStream_t s);

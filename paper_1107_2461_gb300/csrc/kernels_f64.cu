@@ -145,11 +145,27 @@ __global__ void __launch_bounds__(256) k_slab_f64(const double* __restrict__ A, 
   }
 }
 
+// Thomas sweep along z (TPT, end of Sec. 3) in FP64 for every (x-mode,
+// y-mode) line: [(sigma - lam Lx_i) M_z - lam K_z - lam Ly_j W] u = M_z f with
+// W = M_z (Cartesian) or the theta weight A g (cylindrical plans).  The line
+// factorisation (c'_k and the reciprocal pivots) depends on (sigma, lambda,
+// field) only; it is kept in a per-workspace cache whose key the sweep reads
+// on the device: a matching key runs the cached sweep (about four FP64
+// operations per point, no divide), any other runs the factorising sweep and
+// refreshes the cache (the key is written by a one-thread kernel after it, so
+// every block of a sweep sees the same key, also in replayed graphs).  T is
+// the field type: double (FP64 path) or float (the mixed path's FP32 fields,
+// configuration 4, FP64 recurrence).  Field element (k, line l) at
+// k * kstride + (l / ny) * pitch + l % ny, l = i * ny + j ... for the FP64
+// path pitch = ny = lines per x mode is replaced by the [z][y][x] order below.
 struct ThomasArgs {
-  const double* in;
-  double* out;
-  double* cs;        // scratch c'_k
+  const void* in;
+  void* out;
+  double* cs;        // scratch c'_k (no cache)
   int nx, ny, nz;
+  int mixed_layout;  // 0: FP64 field [z][y][x] (line l = j*nx + i); 1: FP32 [z][i][pitch] (l = i*ny + j)
+  int pitch;
+  long long kstride;
   const double* lamx;
   const double* lamy;
   const double* mz;
@@ -157,71 +173,150 @@ struct ThomasArgs {
   const double* koz;
   const double* wy;  // per z: weight of the y eigenvalue (cylindrical theta: A_i g_i); null: M_z
   double sigma, lambda;
+  int field;
   int singular_possible;  // sigma == 0 and zero-flux walls everywhere
+  double* cinv;      // factor cache: reciprocal pivots [k][line] (null: no cache)
+  double* ccp;       //               c'_k [k][line]
+  const double* key; //               (sigma, lambda, field) of the cached factors
+  long long q;       // line points per plane of the cache (>= lines)
+  float* fmax;       // FP32 fields: atomic max |u| (the next pass's scale)
 };
 
+__device__ __forceinline__ void warp_max_out(float v, float* fmax) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0 && v > 0.f) atomicMax(reinterpret_cast<unsigned int*>(fmax), __float_as_uint(v));
+}
+
+template <typename T>
 __global__ void __launch_bounds__(128) k_thomas_f64(ThomasArgs a, const int* __restrict__ skip) {
   if (skip && *skip) return;
+  __shared__ double s_m[kMaxN], s_lo[kMaxN];  // M_k and lambda K_{k,k+1}
+  const int nz = a.nz;
+  for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+    s_m[k] = a.mz[k];
+    s_lo[k] = a.lambda * a.koz[k];
+  }
+  __syncthreads();
   const long long NL = (long long)a.nx * a.ny;
-  const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= NL) return;
-  const int i = (int)(l % a.nx), j = (int)(l / a.nx);
+  const long long l0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float vmax = 0.f;
+  // lines past the end run line NL - 1 again without storing (the warp stays
+  // whole for the max reduction)
+  const bool live = l0 < NL;
+  const long long l = live ? l0 : NL - 1;
+  int i, j;
+  long long off;
+  if (a.mixed_layout) {
+    i = (int)(l / a.ny);
+    j = (int)(l % a.ny);
+    off = (long long)i * a.pitch + j;
+  } else {
+    i = (int)(l % a.nx);
+    j = (int)(l / a.nx);
+    off = l;
+  }
+  const T* in = static_cast<const T*>(a.in) + off;
+  T* out = static_cast<T*>(a.out) + off;
+  const long long ks = a.kstride;
   const double lab = a.lamx[i] + a.lamy[j];
   // the y eigenvalue takes its own weight on cylindrical plans (Eq. 44: the
   // theta eigenvalue multiplies the discrete 1/r^2 of the radial cell)
   const double s = a.sigma - a.lambda * (a.wy ? a.lamx[i] : lab);
   const double ly = a.wy ? a.lambda * a.lamy[j] : 0.0;
-  const int nz = a.nz;
   const double lam = a.lambda;
   if (!(a.singular_possible && lab == 0.0)) {
-    double cprev = 0.0, dprev = 0.0;
-    for (int k = 0; k < nz; ++k) {
-      double lo = (k > 0) ? -lam * a.koz[k - 1] : 0.0;
-      double up = (k + 1 < nz) ? -lam * a.koz[k] : 0.0;
-      double di = s * a.mz[k] - lam * a.kdz[k];
-      if (a.wy) di -= ly * a.wy[k];
-      double inv = 1.0 / (di - lo * cprev);
-      cprev = up * inv;
-      dprev = (a.mz[k] * a.in[k * NL + l] - lo * dprev) * inv;
-      a.cs[k * NL + l] = cprev;
-      a.out[k * NL + l] = dprev;
+    const bool cached = a.cinv && a.key[0] == a.sigma && a.key[1] == a.lambda && a.key[2] == (double)a.field;
+    double* cp_arr = a.cinv ? a.ccp + l : a.cs + off;
+    const long long cstride = a.cinv ? a.q : ks;
+    if (cached && live) {
+      const double* inv = a.cinv + l;
+      double d = 0.0;
+      for (int k = 0; k < nz; ++k) {
+        double t = __dmul_rn(s_m[k], (double)in[k * ks]);
+        if (k > 0) t = __fma_rn(s_lo[k - 1], d, t);
+        d = __dmul_rn(t, inv[k * a.q]);
+        out[k * ks] = (T)d;
+      }
+      double u = d;
+      vmax = fmaxf(vmax, fabsf((float)u));
+      for (int k = nz - 2; k >= 0; --k) {
+        u = __fma_rn(-cp_arr[k * cstride], u, (double)out[k * ks]);
+        out[k * ks] = (T)u;
+        vmax = fmaxf(vmax, fabsf((float)u));
+      }
+    } else if (live) {
+      double cprev = 0.0, dprev = 0.0;
+      for (int k = 0; k < nz; ++k) {
+        const double lo = (k > 0) ? -s_lo[k - 1] : 0.0;
+        const double up = (k + 1 < nz) ? -s_lo[k] : 0.0;
+        double di = s * s_m[k] - lam * a.kdz[k];
+        if (a.wy) di -= ly * a.wy[k];
+        const double inv = 1.0 / (di - lo * cprev);
+        cprev = up * inv;
+        // the same operations, in the same order, as the cached sweep: a
+        // solve gives the same bits whether its factors were cached or not
+        double t = __dmul_rn(s_m[k], (double)in[k * ks]);
+        if (k > 0) t = __fma_rn(s_lo[k - 1], dprev, t);
+        dprev = __dmul_rn(t, inv);
+        cp_arr[k * cstride] = cprev;
+        if (a.cinv) a.cinv[l + k * a.q] = inv;
+        out[k * ks] = (T)dprev;
+      }
+      double u = dprev;
+      vmax = fmaxf(vmax, fabsf((float)u));
+      for (int k = nz - 2; k >= 0; --k) {
+        u = __fma_rn(-cp_arr[k * cstride], u, (double)out[k * ks]);
+        out[k * ks] = (T)u;
+        vmax = fmaxf(vmax, fabsf((float)u));
+      }
     }
-    double u = dprev;
-    for (int k = nz - 2; k >= 0; --k) {
-      u = a.out[k * NL + l] - a.cs[k * NL + l] * u;
-      a.out[k * NL + l] = u;
-    }
-  } else {
+  } else if (live) {
     // singular line of the zero-flux Laplacian (Eq. 28 reading): project the
     // right-hand side to zero M_z-weighted mean, pin u_0 = 0, solve rows 1..nz-1,
     // then remove the weighted mean of the solution.
+    double* cs = a.cs + off;
     double sm = 0.0, sf = 0.0;
     for (int k = 0; k < nz; ++k) {
-      sm += a.mz[k];
-      sf += a.mz[k] * a.in[k * NL + l];
+      sm += s_m[k];
+      sf += s_m[k] * (double)in[k * ks];
     }
     const double mu = sf / sm;
     double cprev = 0.0, dprev = 0.0;
     for (int k = 1; k < nz; ++k) {
-      double lo = (k > 1) ? -lam * a.koz[k - 1] : 0.0;
-      double up = (k + 1 < nz) ? -lam * a.koz[k] : 0.0;
-      double di = s * a.mz[k] - lam * a.kdz[k];
-      double inv = 1.0 / (di - lo * cprev);
+      const double lo = (k > 1) ? -s_lo[k - 1] : 0.0;
+      const double up = (k + 1 < nz) ? -s_lo[k] : 0.0;
+      const double di = s * s_m[k] - lam * a.kdz[k];
+      const double inv = 1.0 / (di - lo * cprev);
       cprev = up * inv;
-      dprev = (a.mz[k] * (a.in[k * NL + l] - mu) - lo * dprev) * inv;
-      a.cs[k * NL + l] = cprev;
-      a.out[k * NL + l] = dprev;
+      dprev = (s_m[k] * ((double)in[k * ks] - mu) - lo * dprev) * inv;
+      cs[k * ks] = cprev;
+      out[k * ks] = (T)dprev;
     }
-    double u = dprev, su = a.mz[nz - 1] * dprev;
+    double u = dprev, su = s_m[nz - 1] * dprev;
     for (int k = nz - 2; k >= 1; --k) {
-      u = a.out[k * NL + l] - a.cs[k * NL + l] * u;
-      a.out[k * NL + l] = u;
-      su += a.mz[k] * u;
+      u = (double)out[k * ks] - cs[k * ks] * u;
+      out[k * ks] = (T)u;
+      su += s_m[k] * u;
     }
-    a.out[l] = 0.0;
+    out[0] = (T)0.0;
     const double mean = su / sm;
-    for (int k = 0; k < nz; ++k) a.out[k * NL + l] -= mean;
+    for (int k = 0; k < nz; ++k) {
+      const double w = (double)out[k * ks] - mean;
+      out[k * ks] = (T)w;
+      vmax = fmaxf(vmax, fabsf((float)w));
+    }
   }
+  // one reduction point for the whole warp
+  if (a.fmax) warp_max_out(vmax, a.fmax);
+}
+
+// the factors now in the cache belong to (sigma, lambda, field)
+__global__ void k_thomas_key(double* key, double sigma, double lambda, int field, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  key[0] = sigma;
+  key[1] = lambda;
+  key[2] = (double)field;
 }
 
 __global__ void k_divide_f64(double* __restrict__ data, int nx, int ny, int nz, const double* __restrict__ lx,
@@ -459,16 +554,19 @@ fdi_status launch_modes_f64(fdi_plan* p, const double* in, double* out, const do
   return FDI_OK;
 }
 
-fdi_status launch_thomas_f64(fdi_plan* p, const Field& f, double sigma, double lambda, const double* in,
+fdi_status launch_thomas_f64(fdi_plan* p, const Field& f, double sigma, double lambda, int field, const double* in,
                              double* out, double* scratch, const int* skip, cudaStream_t s) {
   FDI_KTIMER(p, "thomas_z_f64", s);
-  ThomasArgs a;
+  ThomasArgs a{};
   a.in = in;
   a.out = out;
   a.cs = scratch;
   a.nx = f.n[0];
   a.ny = f.n[1];
   a.nz = f.n[2];
+  a.mixed_layout = 0;
+  a.pitch = f.n[0];
+  a.kstride = (long long)f.n[0] * f.n[1];
   a.lamx = f.ax[0]->lam;
   a.lamy = f.ax[1]->lam;
   a.mz = f.ax[2]->m;
@@ -477,9 +575,57 @@ fdi_status launch_thomas_f64(fdi_plan* p, const Field& f, double sigma, double l
   a.wy = p->cyl_wy;
   a.sigma = sigma;
   a.lambda = lambda;
+  a.field = field;
   a.singular_possible = (sigma == 0.0 && f.zero_flux_all) ? 1 : 0;
-  long long NL = (long long)a.nx * a.ny;
-  k_thomas_f64<<<(unsigned)((NL + 127) / 128), 128, 0, s>>>(a, skip);
+  const long long NL = (long long)a.nx * a.ny;
+  const bool cache = p->tf && p->tf_q >= f.P;
+  if (cache) {
+    a.q = NL;
+    a.cinv = p->tf;
+    a.ccp = p->tf + p->tf_q;
+    a.key = p->tf + 2 * p->tf_q;
+  }
+  k_thomas_f64<double><<<(unsigned)((NL + 127) / 128), 128, 0, s>>>(a, skip);
+  FDI_LAUNCH_CHECK(p);
+  if (cache) {
+    k_thomas_key<<<1, 1, 0, s>>>(p->tf + 2 * p->tf_q, sigma, lambda, field, skip);
+    FDI_LAUNCH_CHECK(p);
+  }
+  return FDI_OK;
+}
+
+fdi_status launch_thomas_cached_f32(fdi_plan* p, const Field& f, double sigma, double lambda, int field, float* data,
+                                    int pitch, long long plane, float* fmax, const int* skip, cudaStream_t s) {
+  FDI_KTIMER(p, "thomas_z_f64rec", s);
+  ThomasArgs a{};
+  a.in = data;
+  a.out = data;
+  a.cs = nullptr;
+  a.nx = f.n[0];
+  a.ny = f.n[1];
+  a.nz = f.n[2];
+  a.mixed_layout = 1;
+  a.pitch = pitch;
+  a.kstride = plane;
+  a.lamx = f.ax[0]->lam;
+  a.lamy = f.ax[1]->lam;
+  a.mz = f.ax[2]->m;
+  a.kdz = f.ax[2]->kd;
+  a.koz = f.ax[2]->ko;
+  a.wy = p->cyl_wy;
+  a.sigma = sigma;
+  a.lambda = lambda;
+  a.field = field;
+  a.singular_possible = 0;  // the singular problem keeps the FP32 sweep's null-line kernel
+  a.fmax = fmax;
+  const long long NL = (long long)a.nx * a.ny;
+  a.q = NL;
+  a.cinv = p->tf;
+  a.ccp = p->tf + p->tf_q;
+  a.key = p->tf + 2 * p->tf_q;
+  k_thomas_f64<float><<<(unsigned)((NL + 127) / 128), 128, 0, s>>>(a, skip);
+  FDI_LAUNCH_CHECK(p);
+  k_thomas_key<<<1, 1, 0, s>>>(p->tf + 2 * p->tf_q, sigma, lambda, field, skip);
   FDI_LAUNCH_CHECK(p);
   return FDI_OK;
 }

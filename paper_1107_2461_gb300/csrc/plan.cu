@@ -196,6 +196,21 @@ void swap_slot(fdi_plan* p, fdi_work_slot& w) {
   std::swap(p->partials, w.partials);
   std::swap(p->d_status, w.d_status);
   std::swap(p->d_counter, w.d_counter);
+  std::swap(p->tf, w.tf);
+  std::swap(p->tf_q, w.tf_q);
+}
+
+fdi_status alloc_thomas_cache(fdi_plan* p, long long q) {
+  if (p->tf && p->tf_q >= q) return FDI_OK;
+  if (p->tf) cudaFree(p->tf);
+  p->tf = nullptr;
+  p->tf_q = 0;
+  FDI_TRY(dev_alloc(&p->tf, (size_t)(2 * q + 4)));
+  // an impossible key (lambda < 0): the first sweep computes the factors
+  const double key[4] = {0.0, -1.0, -1.0, 0.0};
+  FDI_CUDA_TRY(cudaMemcpy(p->tf + 2 * q, key, sizeof(key), cudaMemcpyHostToDevice));
+  p->tf_q = q;
+  return FDI_OK;
 }
 
 fdi_status alloc_workspace(fdi_plan* p) {
@@ -203,6 +218,8 @@ fdi_status alloc_workspace(fdi_plan* p) {
   FDI_TRY(dev_alloc(&p->partials, (size_t)p->npartials * 4));
   FDI_TRY(dev_alloc(&p->d_status, 1));
   FDI_CUDA_TRY(cudaMemset(p->d_status, 0, sizeof(DevStatus)));
+  // FP64 TPT sweeps keep their line factors for repeated (sigma, lambda)
+  if (p->prec == FDI_PREC_FP64 && p->thomas_axis == 2) FDI_TRY(alloc_thomas_cache(p, p->Pmax));
   return FDI_OK;
 }
 
@@ -215,7 +232,7 @@ void free_workspace(fdi_plan* p) {
     if (w) cudaFree(w);
     w = nullptr;
   }
-  void* ptrs[] = {p->xdf, p->wr1, p->d_counter, p->d_scales, p->lam_w, p->partials, p->d_status};
+  void* ptrs[] = {p->xdf, p->wr1, p->d_counter, p->d_scales, p->lam_w, p->partials, p->d_status, p->tf};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   p->xdf = nullptr;
@@ -225,6 +242,8 @@ void free_workspace(fdi_plan* p) {
   p->lam_w = nullptr;
   p->partials = nullptr;
   p->d_status = nullptr;
+  p->tf = nullptr;
+  p->tf_q = 0;
 }
 
 namespace {

@@ -104,6 +104,7 @@ extern "C" size_t fdi_stokes_plan_bytes_estimate(const int n[3], int prec) {
   const size_t Pp = (size_t)(n[0] + 4) * (n[1] + 4) * n[2];  // padded FP32 rows
   // four per-solve workspaces (the plan's own and one per velocity component)
   size_t slot = 5 * (size_t)P * 8 + (size_t)16384 * 4 * 8;  // FP64 workspace, partials
+  if (prec == FDI_PREC_FP64) slot += 2 * (size_t)P * 8;      // Thomas factor cache
   if (prec != FDI_PREC_FP64) slot += 4 * Pp * 4 + 3 * (size_t)P * 4 + 2 * Pp * 4;
   b += 4 * slot;
   b += 11 * (size_t)P * 8 + 6 * (size_t)P * 8;  // Krylov vectors, cell volumes, face work fields

@@ -55,8 +55,9 @@ fdi_status validate_field_args(const fdi_plan* p, int field, double sigma, doubl
 namespace {
 
 // One direct solve in FP64: out (+)= A^{-1} in.
-fdi_status solve_once_f64(fdi_plan* p, const Field& f, double sigma, double lambda, const double* in,
-                          double* out, bool accumulate, const int* skip, cudaStream_t s) {
+fdi_status solve_once_f64(fdi_plan* p, int field, double sigma, double lambda, const double* in, double* out,
+                          bool accumulate, const int* skip, cudaStream_t s) {
+  const Field& f = p->fields[field];
   const int nx = f.n[0], ny = f.n[1], nz = f.n[2];
   double* t0 = p->ws[0];
   double* t1 = p->ws[1];
@@ -67,7 +68,7 @@ fdi_status solve_once_f64(fdi_plan* p, const Field& f, double sigma, double lamb
   FDI_TRY(launch_lines_f64(p, in, t0, ax->Einv, nx, nx, (long long)ny * nz, false, skip, s));
   FDI_TRY(launch_slab_f64(p, t0, t1, ay->Einv, ny, ny, nx, nz, skip, s));
   if (p->thomas_axis == 2) {
-    FDI_TRY(launch_thomas_f64(p, f, sigma, lambda, t1, t0, t2, skip, s));
+    FDI_TRY(launch_thomas_f64(p, f, sigma, lambda, field, t1, t0, t2, skip, s));
     FDI_TRY(launch_slab_f64(p, t0, t1, ay->E, ny, ny, nx, nz, skip, s));
     FDI_TRY(launch_lines_f64(p, t1, out, ax->E, nx, nx, (long long)ny * nz, accumulate, skip, s));
   } else if (p->cyl) {
@@ -106,11 +107,11 @@ fdi_status field_solve_internal(fdi_plan* p, int field, double sigma, double lam
   if (singular) FDI_TRY(launch_mean_f64(p, f, b, s));
   const int* done = &p->d_status->done;
   double* r = p->ws[3];
-  FDI_TRY(solve_once_f64(p, f, sigma, lambda, b, out, false, nullptr, s));
+  FDI_TRY(solve_once_f64(p, field, sigma, lambda, b, out, false, nullptr, s));
   FDI_TRY(launch_residual_f64(p, f, sigma, lambda, b, out, r, singular, nullptr, s));
   FDI_TRY(launch_finish_residual(p, 0, true, 0, nullptr, s));
   for (int k = 0; k < p->max_refine; ++k) {
-    FDI_TRY(solve_once_f64(p, f, sigma, lambda, r, out, true, done, s));
+    FDI_TRY(solve_once_f64(p, field, sigma, lambda, r, out, true, done, s));
     FDI_TRY(launch_residual_f64(p, f, sigma, lambda, b, out, r, singular, done, s));
     FDI_TRY(launch_finish_residual(p, 0, false, 1, done, s));
   }
@@ -260,7 +261,7 @@ namespace {
 
 // ---- batched solves: independent plans run concurrently on a pool of streams ----
 
-constexpr int kBatchStreams = 8;
+constexpr int kBatchStreams = 32;
 
 struct StreamPool {
   cudaStream_t st[kBatchStreams] = {};
@@ -453,8 +454,19 @@ fdi_status fdi_helmholtz_solve_batched(fdi_plan* const* plans, const double* lam
 }
 
 fdi_status fdi_plan_set_thomas_config(fdi_plan* plan, int lines_per_cta) {
-  if (!plan || (lines_per_cta != 2 && lines_per_cta != 3 && lines_per_cta != 64 && lines_per_cta != 128))
+  if (!plan || (lines_per_cta != 2 && lines_per_cta != 3 && lines_per_cta != 4 && lines_per_cta != 64 &&
+                lines_per_cta != 128))
     return FDI_ERR_INVALID_ARG;
+  if (lines_per_cta == 4 && plan->prec != FDI_PREC_FP64) {
+    // FP64 recurrence with cached line factors: a cache in every workspace
+    long long q = 0;
+    for (int fi = 0; fi < plan->nfields; ++fi) q = std::max(q, plan->fields[fi].P);
+    FDI_TRY(alloc_thomas_cache(plan, q));
+    for (int c = 0; c < plan->nextra; ++c) {
+      SlotSwap guard(plan, &plan->extra[c]);
+      FDI_TRY(alloc_thomas_cache(plan, q));
+    }
+  }
   plan->thomas_tl = lines_per_cta;
   invalidate_graph(plan);
   return FDI_OK;

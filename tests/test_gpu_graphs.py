@@ -78,3 +78,58 @@ def test_graph_dropped_on_new_arrays(fdi):
         want = dec.solve(rhs_uniform(n[::-1], seed), ops, 1.0, 1.0, "tpt")
         assert np.abs(o.cpu().numpy() - want).max() <= 1e-9 * np.abs(want).max()
     plan.destroy()
+
+
+def test_thomas_factor_cache_alternating_lambdas(fdi):
+    # FP64 TPT sweeps reuse their line factors while (sigma, lambda, field)
+    # repeats; alternating lambdas on one plan and stream, so that a graph
+    # captured for lambda_1 is replayed after the cache holds lambda_2's
+    # factors: every result must still be the oracle's (the device-side key
+    # check makes the replay factorise again)
+    import numpy as np
+    import torch
+    from oracle import assembled as asm
+    from workloads import box_faces, rhs_uniform
+    n = (40, 36, 33)
+    faces = box_faces(n, 1.5)
+    ops = asm.cell_ops(faces, (0, 0, 0), (0, 0, 0))
+    f = rhs_uniform(n[::-1], 3)
+    plan = fdi.plan_create(faces, n)
+    stream = torch.cuda.Stream()
+    rhs = torch.from_numpy(f).cuda()
+    outs = {lam: torch.empty_like(rhs) for lam in (1.0, 1e-3)}
+    try:
+        for lam in (1.0, 1.0, 1e-3, 1.0, 1e-3, 1.0, 1.0):
+            fdi.helmholtz_solve(plan, lam, rhs, outs[lam], stream)
+            stream.synchronize()
+            _, _, rel, st = fdi.last_result(plan)
+            assert st == 0 and rel <= 1e-11, (lam, rel)
+            assert asm.relative_residual(ops, outs[lam].cpu().numpy(), f, lam) <= 1e-11
+    finally:
+        plan.destroy()
+
+
+def test_mixed_thomas_fp64_recurrence(fdi):
+    # configuration 4: the mixed path's z sweep as an FP64 recurrence with
+    # cached line factors (on the FP32 fields); refined to the same tolerance
+    import torch
+    from oracle import assembled as asm
+    from workloads import box_faces, rhs_uniform
+    for n, bc, lam, sigma in (((64, 48, 40), (0, 0, 0), 1.0, 1.0), ((32, 40, 24), (1, 0, 1), 1e-3, 1.0),
+                              ((24, 20, 18), (1, 1, 1), 1.0, 0.0)):
+        faces = box_faces(n, 1.5)
+        ops = asm.cell_ops(faces, bc, bc)
+        f = rhs_uniform(n[::-1], 4)
+        plan = fdi.plan_create(faces, n, bc, bc, prec=fdi.PREC_MIXED_F16)
+        try:
+            fdi.set_thomas_config(plan, 4)
+            rhs = torch.from_numpy(f).cuda()
+            out = torch.empty_like(rhs)
+            for _ in range(2):  # the second solve takes the cached factors
+                fdi.field_solve(plan, fdi.FIELD_CELL, sigma, lam, rhs, out)
+                torch.cuda.synchronize()
+                _, steps, rel, st = fdi.last_result(plan)
+                assert st == 0 and rel <= 1e-10, (n, steps, rel)
+                assert asm.relative_residual(ops, out.cpu().numpy(), f, lam, sigma) <= 1e-10
+        finally:
+            plan.destroy()
