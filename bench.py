@@ -304,13 +304,15 @@ def run_arm(fdi, torch, prec, n, K, W, dev, rank, stream, thomas_axis=2, refine_
             "d2h": f.nbytes, "clocks": clk.summary()}
 
 
-def run_stokes(fdi, torch, prec, n, reps, warm, stream, krylov=0):
+def run_stokes(fdi, torch, prec, n, reps, warm, stream, krylov=0, resident=False):
     """Stokes-inverse latency on the staggered n^3 no-slip box (tanh 1.5, Re 1000,
     dt in {1e-2, 1e3}, Gaussian forcing seeds 0-2): p50 / p99 of the wall time of
-    complete solves (each call ends with the stream synchronised)."""
+    complete solves (each call ends with the stream synchronised).  resident:
+    the Helmholtz solves as resident launches (fdi_plan_set_resident)."""
     faces = workloads.box_faces((n, n, n), BETA)
     plan = fdi.plan_create(faces, (n, n, n), grid=fdi.GRID_MAC, prec=prec)
     fdi.set_krylov(plan, krylov)
+    fdi.set_resident(plan, resident)
     shapes = workloads.mac_shapes((n, n, n))
     f = [torch.from_numpy(workloads.rhs_gaussian(shapes[c], i)).cuda() for i, c in enumerate("uvw")]
     u = [torch.empty_like(t) for t in f]
@@ -589,10 +591,13 @@ def main():
         stokes = {}
         for name in args.arms.split(","):
             prec = precs[name][0]
-            for kname, kry in (("", 0), ("/bicgstab2", 1), ("/cg", 2)):
+            variants = [("", 0, False), ("/bicgstab2", 1, False), ("/cg", 2, False)]
+            if prec != fdi.PREC_FP64:
+                variants += [("/resident", 0, True), ("/cg/resident", 2, True)]
+            for kname, kry, res in variants:
                 try:
                     stokes[name + kname] = run_stokes(fdi, torch, prec, args.stokes_n, args.stokes_reps, 2, stream,
-                                                      krylov=kry)
+                                                      krylov=kry, resident=res)
                 except fdi.FdiError as e:
                     stokes[name + kname] = {"error": str(e)}
     batch = None
@@ -645,7 +650,9 @@ def main():
         "clocks": best["clocks"],
         "stokes_latency": ({"config": f"MAC {args.stokes_n}^3, tanh {BETA}, no-slip, Re 1000, Gaussian forcing; "
                                       "BiCGstab (default), BiCGstab(2) (/bicgstab2; iterations are outer ones) and "
-                                      "volume-weighted CG (/cg; one C-product per iteration)",
+                                      "volume-weighted CG (/cg; one C-product per iteration); /resident: the "
+                                      "Helmholtz solves as resident launches (one cooperative launch per solve, "
+                                      "the three velocity solves sharing one)",
                             **stokes} if stokes is not None else None),
         "batched": batch,
         "serving": serving,

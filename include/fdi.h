@@ -272,18 +272,39 @@ fdi_status fdi_apply_transform(fdi_plan* plan, fdi_field field, int d, int inver
 fdi_status fdi_eigen_noalloc(const double* faces, int n, int face_kind, fdi_bc bc_lo, fdi_bc bc_hi, double* lam,
                              double* E, double* Einv, int* converged, fdi_stream_t stream);
 
-/* Bound on every wait inside the tensor-core transform kernels of a mixed plan
- * (a CTA's roles hand shared-memory stages to one another through mbarriers),
- * in SM clock cycles; 0 restores the default of 4e9 cycles (about two seconds
- * at 2 GHz).  A wait that runs out stops every role of its CTA, lets the
- * asynchronous copies and MMAs already issued finish, frees its tensor memory
- * and returns; the plan then records the failure in a flag that stays set, so
+/* Bound on every wait inside the kernels of a mixed plan that wait: the
+ * tensor-core transforms (a CTA's roles hand shared-memory stages to one
+ * another through mbarriers) and the grid barrier of the resident solve (its
+ * CTAs meet between passes), in SM clock cycles; 0 restores the default of
+ * 4e9 cycles (about two seconds at 2 GHz).  A transform wait that runs out
+ * stops every role of its CTA, lets the asynchronous copies and MMAs already
+ * issued finish, frees its tensor memory and returns; a barrier wait that runs
+ * out raises an abort flag on which every CTA of the launch returns at its
+ * next barrier.  The plan then records the failure in a flag that stays set, so
  * fdi_last_result (and every later solve's result) reports FDI_ERR_TIMEOUT,
  * until the next call of this function clears it.  The solution of a solve
  * that timed out is undefined.  Synchronises the device (the flag is cleared
  * once nothing runs); drops the plan's captured graphs.  FP64 plans accept
  * the call and have no such waits.  cycles < 0: FDI_ERR_INVALID_ARG. */
 fdi_status fdi_plan_set_wait_limit(fdi_plan* plan, long long cycles);
+
+/* Resident solve of mixed plans (enable = 1; default 0): a field whose x
+ * and y extents are at most 128 is solved by one cooperative launch that runs
+ * every pass of the TPT solve (Sec. 3, end) and of its refinement rounds, the
+ * CTAs meeting at a grid barrier between passes; a z-plane fits in shared
+ * memory there and one CTA applies both plane transforms to it in FP32.  The
+ * three velocity solves of a Stokes step (fdi_stokes_solve) and the small
+ * grids of fdi_helmholtz_solve_batched share such launches (up to 64 solves
+ * each), with results bitwise equal to the same solve launched alone.
+ * Cylindrical plans, TPF plans and larger fields always run pass by pass.
+ * Each pass of the resident launch takes about 10 us on a 64^3 field (a
+ * chain of dependent steps per unit), so a lone solve costs about what the
+ * pass-by-pass graph costs (0.12 ms at 64^3) in one launch instead of 28;
+ * for larger planes and for several solves per launch it is slower.
+ * enable = 0: every field pass by pass (tensor-core transforms, one launch
+ * per pass).  Drops the plan's captured graphs.  FP64 plans accept the call
+ * and ignore it.  Other values: FDI_ERR_INVALID_ARG. */
+fdi_status fdi_plan_set_resident(fdi_plan* plan, int enable);
 
 /* Thomas sweep of mixed plans: 64 or 128 lines (one per thread) per CTA;
  * 2: two adjacent lines per thread, 64 threads per CTA (default); 3: as 2,

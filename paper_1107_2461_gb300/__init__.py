@@ -13,7 +13,7 @@ from .fdi import (  # noqa: F401
     field_solve, field_solve_host,
     helmholtz_solve, helmholtz_solve_batched, kernel_times, laplace_solve, last_launch_count, last_result,
     plan_create, plan_create_cyl, plan_destroy, reset_kernel_times, set_graphs, set_krylov, set_stokes_preconditioner,
-    set_thomas_config,
+    set_resident, set_thomas_config,
     set_wait_limit,
     status_string, stokes_plan_bytes_estimate,
     stokes_solve,

@@ -102,7 +102,9 @@ struct fdi_plan {
   float* wr1 = nullptr;             // mixed: first residual r_1 as (hi, lo) FP32 planes
   long long wr1_plane = 0;
   float* d_scales = nullptr;        // per refinement round: max |field| of the pass inputs
-  int* d_err = nullptr;             // nonzero: a tensor-core kernel hit a wait limit (sticky)
+  int* d_err = nullptr;             // nonzero: a kernel hit a wait limit (sticky)
+  unsigned* res_bar = nullptr;      // grid barrier of the plan's resident launches (zero between launches)
+  int resident = 0;                 // 1: mixed fields with x, y extents <= 128 solved by one resident launch
   long long wait_cycles = 0;        // bound of every tensor-core kernel wait, cycles (0: about 2 s)
   int thomas_tl = 2;                // FP32 Thomas: lines per CTA (64, 128) or 2 = two lines per thread
   float2* lam_w = nullptr;          // lambda-scaled double-float flux weights [3][3][kMaxN]

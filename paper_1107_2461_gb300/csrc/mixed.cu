@@ -28,6 +28,7 @@
 #include "df.cuh"
 #include "fdi_internal.h"
 #include "resid.cuh"
+#include "resident.h"
 #include "tc_transform.h"
 
 namespace fdi {
@@ -41,6 +42,9 @@ struct MixedAxis {
   float2* wm = nullptr;
   float2* w0 = nullptr;
   float2* m_df = nullptr; // control-volume widths in double-float
+  // resident solve (n <= 128): fwd and bwd in the shared-memory layout of its
+  // MMAs (see tc_resident_image)
+  uint8_t* rimg[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -843,6 +847,10 @@ fdi_status setup_axis(fdi_plan* p, Axis* ax, cudaStream_t s) {
   const int n = ax->n;
   FDI_TRY(tc_prepare_matrix(p, ax->Einv, n, &mx->fwd, s));
   FDI_TRY(tc_prepare_matrix(p, ax->E, n, &mx->bwd, s));
+  if (n <= kResMaxPlane) {
+    FDI_TRY(tc_resident_image(p, mx->fwd, &mx->rimg[0], s));
+    FDI_TRY(tc_resident_image(p, mx->bwd, &mx->rimg[1], s));
+  }
   FDI_TRY(upload_f(&mx->m_f, ax->h_m));
   FDI_TRY(upload_f(&mx->kd_f, ax->h_kd));
   FDI_TRY(upload_f(&mx->ko_f, ax->h_ko));
@@ -868,7 +876,7 @@ void mixed_free_axis(Axis* ax) {
   if (!mx) return;
   tc_free_matrix(&mx->fwd);
   tc_free_matrix(&mx->bwd);
-  void* ptrs[] = {mx->m_f, mx->kd_f, mx->ko_f, mx->wp, mx->wm, mx->w0, mx->m_df};
+  void* ptrs[] = {mx->m_f, mx->kd_f, mx->ko_f, mx->wp, mx->wm, mx->w0, mx->m_df, mx->rimg[0], mx->rimg[1]};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete mx;
@@ -897,6 +905,8 @@ fdi_status mixed_setup(fdi_plan* p) {
   FDI_CUDA_TRY(e);
   FDI_CUDA_TRY(cudaMalloc(&p->d_err, sizeof(int)));
   FDI_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
+  FDI_CUDA_TRY(cudaMalloc(&p->res_bar, 4 * sizeof(unsigned)));
+  FDI_CUDA_TRY(cudaMemset(p->res_bar, 0, 4 * sizeof(unsigned)));
   FDI_CUDA_TRY(cudaStreamCreateWithFlags(&p->cstream, cudaStreamNonBlocking));
   return mixed_alloc_workspace(p);
 }
@@ -931,6 +941,88 @@ fdi_status mixed_alloc_workspace(fdi_plan* p) {
   FDI_CUDA_TRY(cudaMalloc(&p->lam_w, (size_t)10 * kMaxN * sizeof(float2)));
   FDI_CUDA_TRY(cudaMalloc(&p->d_counter, 4 * sizeof(unsigned)));
   FDI_CUDA_TRY(cudaMemset(p->d_counter, 0, 4 * sizeof(unsigned)));
+  return FDI_OK;
+}
+
+bool resident_eligible(const fdi_plan* p, int field) {
+  if (!p || p->prec == FDI_PREC_FP64 || !p->resident || p->cyl || p->thomas_axis != 2) return false;
+  if (field < 0 || field >= p->nfields || !p->res_bar) return false;
+  const Field& f = p->fields[field];
+  if (f.n[0] > kResMaxPlane || f.n[1] > kResMaxPlane) return false;
+  for (int d = 0; d < 2; ++d)
+    if (!static_cast<const MixedAxis*>(f.ax[d]->mixed)->rimg[0]) return false;
+  return true;
+}
+
+fdi_status resident_describe(fdi_plan* p, int field, double sigma, double lambda, const double* rhs, double* out,
+                             ResJob* job) {
+  const Field& f = p->fields[field];
+  ResJob& J = *job;
+  J = ResJob{};
+  J.nx = f.n[0];
+  J.ny = f.n[1];
+  J.nz = f.n[2];
+  J.px = pitch4(J.nx);
+  J.cls = (J.nx <= 64 && J.ny <= 64) ? 64 : 128;
+  J.singular = (sigma == 0.0 && f.zero_flux_all) ? 1 : 0;
+  J.single_pass = p->single_pass ? 1 : 0;
+  J.vec = (J.nx % 2 == 0 && (reinterpret_cast<uintptr_t>(rhs) & 15u) == 0 &&
+           (reinterpret_cast<uintptr_t>(out) & 15u) == 0) ? 1 : 0;
+  J.max_refine = p->max_refine;
+  int zc = 0;
+  const dim3 rg = resid_grid(J.nx, J.ny, J.nz, &zc);
+  J.rgx = (int)rg.x;
+  J.rgy = (int)rg.y;
+  J.rgz = (int)rg.z;
+  J.zchunk = zc;
+  if ((long long)J.rgx * J.rgy * J.rgz > p->npartials || J.nz > p->npartials) {
+    set_error("grid too large for the reduction buffer");
+    return FDI_ERR_INVALID_ARG;
+  }
+  J.sigma = sigma;
+  J.lambda = lambda;
+  J.tol = p->tol;
+  // FP32 correction residual: error at most about 16 u ||r_1|| (u = 2^-24),
+  // kept below tol / 4 of ||b||
+  J.fast_limit = p->tol / (4.0 * 16.0 * 5.9604644775390625e-8);
+  J.b = rhs;
+  J.out = out;
+  const MixedAxis* mx = static_cast<const MixedAxis*>(f.ax[0]->mixed);
+  const MixedAxis* my = static_cast<const MixedAxis*>(f.ax[1]->mixed);
+  const MixedAxis* mz = static_cast<const MixedAxis*>(f.ax[2]->mixed);
+  J.kx = (J.nx + 31) / 32;
+  J.ky = (J.ny + 31) / 32;
+  J.img[0][0] = mx->rimg[0];
+  J.img[0][1] = my->rimg[0];
+  J.img[1][0] = mx->rimg[1];
+  J.img[1][1] = my->rimg[1];
+  J.csc[0][0] = mx->fwd.col_scale;
+  J.csc[0][1] = my->fwd.col_scale;
+  J.csc[1][0] = mx->bwd.col_scale;
+  J.csc[1][1] = my->bwd.col_scale;
+  J.lamx = f.ax[0]->lam;
+  J.lamy = f.ax[1]->lam;
+  J.mz = mz->m_f;
+  J.kdz = mz->kd_f;
+  J.koz = mz->ko_f;
+  for (int d = 0; d < 3; ++d) {
+    const MixedAxis* m = static_cast<const MixedAxis*>(f.ax[d]->mixed);
+    J.w[d][0] = m->wp;
+    J.w[d][1] = m->wm;
+    J.w[d][2] = m->w0;
+    J.m[d] = m->m_df;
+  }
+  J.lam_w = p->lam_w;
+  J.r = p->wf[0];
+  J.F = p->wf[2];
+  J.cs = p->wf[3];
+  J.xh = reinterpret_cast<float*>(p->xdf);
+  J.r1 = p->wr1;
+  J.r1_plane = p->wr1_plane;
+  J.partials = p->partials;
+  J.st = p->d_status;
+  J.ticket = p->d_counter + 2;
+  J.rmax = p->d_scales;
   return FDI_OK;
 }
 
@@ -1006,6 +1098,13 @@ fdi_status launch_thomas32(fdi_plan* p, const Thomas32Args& ta, bool pdl, bool s
 
 fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda, const double* rhs, double* out,
                              cudaStream_t s) {
+  if (resident_eligible(p, field)) {
+    // every pass and refinement round in one cooperative launch
+    ResJob job;
+    FDI_TRY(resident_describe(p, field, sigma, lambda, rhs, out, &job));
+    FDI_KTIMER(p, "resident", s);
+    return resident_launch(p, &job, 1, s);
+  }
   const Field& f = p->fields[field];
   const int nx = f.n[0], ny = f.n[1], nz = f.n[2];
   const int px = pitch4(nx), py = pitch4(ny);
@@ -1409,5 +1508,12 @@ extern "C" fdi_status fdi_plan_set_wait_limit(fdi_plan* plan, long long cycles) 
     FDI_CUDA_TRY(cudaDeviceSynchronize());
     FDI_CUDA_TRY(cudaMemset(plan->d_err, 0, sizeof(int)));
   }
+  return FDI_OK;
+}
+
+extern "C" fdi_status fdi_plan_set_resident(fdi_plan* plan, int enable) {
+  if (!plan || (enable != 0 && enable != 1)) return FDI_ERR_INVALID_ARG;
+  plan->resident = enable;
+  fdi::invalidate_graph(plan);  // captured solves took the other route
   return FDI_OK;
 }

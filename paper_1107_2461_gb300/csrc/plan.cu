@@ -286,6 +286,7 @@ void free_plan(fdi_plan* p) {
   if (p->d_kry) cudaFree(p->d_kry);
   if (p->kpartials) cudaFree(p->kpartials);
   if (p->d_err) cudaFree(p->d_err);
+  if (p->res_bar) cudaFree(p->res_bar);
   if (p->h_flag) cudaFreeHost(p->h_flag);
   delete p;
 }

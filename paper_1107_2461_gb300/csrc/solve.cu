@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "fdi_internal.h"
+#include "resident.h"
 
 namespace fdi {
 
@@ -296,14 +297,48 @@ fdi_status enqueue_batch(StreamPool* sp, fdi_plan* const* plans, const double* l
   FDI_CUDA_TRY(cudaEventRecord(sp->fork, s));
   std::vector<int> lane(count, -1);
   bool used[kBatchStreams] = {false};
+  // small grids: resident launches of up to kResMaxJobs solves on pool stream
+  // 0 (a plan repeated in the batch goes to a later launch, in order); the
+  // other plans one stream each on streams 1...
+  std::vector<char> res(count, 0);
+  for (int i = 0; i < count; ++i)
+    res[i] = (plans[i]->tstage[0] == nullptr && resident_eligible(plans[i], FDI_FIELD_CELL) &&
+              validate_field_args(plans[i], FDI_FIELD_CELL, 1.0, lambdas[i]) == FDI_OK) ? 1 : 0;
+  {
+    std::vector<char> taken(count, 0);
+    for (;;) {
+      std::vector<ResJob> jobs;
+      std::vector<fdi_plan*> in_launch;
+      for (int i = 0; i < count && (int)jobs.size() < kResMaxJobs; ++i) {
+        if (!res[i] || taken[i]) continue;
+        bool dup = false;
+        for (fdi_plan* q : in_launch) dup = dup || q == plans[i];
+        for (int j = 0; j < i && !dup; ++j) dup = res[j] && !taken[j] && plans[j] == plans[i];
+        if (dup) continue;
+        ResJob job;
+        FDI_TRY(resident_describe(plans[i], FDI_FIELD_CELL, 1.0, lambdas[i], rhs[i], out[i], &job));
+        jobs.push_back(job);
+        in_launch.push_back(plans[i]);
+        taken[i] = 1;
+        plans[i]->launches = 0;
+      }
+      if (jobs.empty()) break;
+      if (!used[0]) {
+        FDI_CUDA_TRY(cudaStreamWaitEvent(sp->st[0], sp->fork, 0));
+        used[0] = true;
+      }
+      FDI_TRY(resident_launch(in_launch[0], jobs.data(), (int)jobs.size(), sp->st[0]));
+    }
+  }
   int next = 0;
   for (int i = 0; i < count; ++i) {
+    if (res[i]) continue;
     for (int j = 0; j < i; ++j)
       if (plans[j] == plans[i]) {
         lane[i] = lane[j];
         break;
       }
-    if (lane[i] < 0) lane[i] = (next++) % kBatchStreams;
+    if (lane[i] < 0) lane[i] = 1 + (next++) % (kBatchStreams - 1);
     const int k = lane[i];
     if (!used[k]) {
       FDI_CUDA_TRY(cudaStreamWaitEvent(sp->st[k], sp->fork, 0));

@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "fdi_internal.h"
+#include "resident.h"
 
 namespace fdi {
 
@@ -671,6 +672,18 @@ namespace {
 // joined back to s (also inside a stream capture)
 fdi_status three_solves(fdi_plan* p, double lambda, const double* const in[3], double* const out[3],
                         cudaStream_t s) {
+  if (p->nextra >= 3 && p->tstage[0] == nullptr && resident_eligible(p, 1) && resident_eligible(p, 2) &&
+      resident_eligible(p, 3)) {
+    // small grids: the three solves share one resident launch (every pass of
+    // all three, each on its own workspace slot)
+    ResJob jobs[3];
+    for (int c = 0; c < 3; ++c) {
+      SlotSwap guard(p, &p->extra[c]);
+      FDI_TRY(resident_describe(p, 1 + c, 1.0, lambda, in[c], out[c], &jobs[c]));
+    }
+    FDI_KTIMER(p, "resident", s);
+    return resident_launch(p, jobs, 3, s);
+  }
   if (p->nextra < 3) {
     for (int c = 0; c < 3; ++c) FDI_TRY(field_solve(p, 1 + c, 1.0, lambda, in[c], out[c], s));
     return FDI_OK;

@@ -634,6 +634,25 @@ fdi_status tc_prepare_matrix(fdi_plan* p, const double* T, int n, TcMatrix* m, c
   return FDI_OK;
 }
 
+// The matrix as the resident solve's MMA reads it from shared memory: for
+// every K chunk of 32, the hi rows then the lo rows (N_pad each), every row 64
+// bytes in the 64-byte swizzle layout; copied into shared memory as it is.
+__global__ void k_res_image(const __half* __restrict__ B, int N_pad, int K_pad, uint8_t* __restrict__ img) {
+  const int half = blockIdx.y, n = blockIdx.x;
+  for (int k = threadIdx.x; k < K_pad; k += blockDim.x) {
+    const size_t off = (size_t)(k / BK) * (2 * N_pad * ROWB) + (size_t)half * N_pad * ROWB + tc::sw64_offset(n, k % BK);
+    *reinterpret_cast<__half*>(img + off) = B[((size_t)half * N_pad + n) * K_pad + k];
+  }
+}
+
+fdi_status tc_resident_image(fdi_plan* p, const TcMatrix& m, uint8_t** img, cudaStream_t s) {
+  const size_t bytes = (size_t)(m.K_pad / BK) * 2 * m.N_pad * ROWB;
+  FDI_CUDA_TRY(cudaMalloc(img, bytes));
+  k_res_image<<<dim3((unsigned)m.N_pad, 2), 128, 0, s>>>((const __half*)m.B, m.N_pad, m.K_pad, *img);
+  FDI_LAUNCH_CHECK(p);
+  return FDI_OK;
+}
+
 void tc_free_matrix(TcMatrix* m) {
   if (m->B) cudaFree(m->B);
   if (m->col_scale) cudaFree(m->col_scale);

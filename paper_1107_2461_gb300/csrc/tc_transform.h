@@ -58,6 +58,9 @@ struct TcArgs {
 
 fdi_status tc_prepare_matrix(fdi_plan* p, const double* T, int n, TcMatrix* m, cudaStream_t s);
 void tc_free_matrix(TcMatrix* m);
+// the matrix in the resident solve's shared-memory layout (K chunks of 32:
+// hi rows, lo rows, 64-byte swizzle); cudaMalloc'ed, the caller frees it
+fdi_status tc_resident_image(fdi_plan* p, const TcMatrix& m, uint8_t** img, cudaStream_t s);
 fdi_status launch_tc_transform(fdi_plan* p, const TcMatrix& m, TcArgs args, const char* name, cudaStream_t s);
 
 }  // namespace fdi

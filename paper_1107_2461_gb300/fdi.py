@@ -67,6 +67,7 @@ SIGNATURES = {
     "fdi_plan_create_cyl": (_i, [C.POINTER(_d), _i, _i, C.POINTER(_d), _i, _i, _i, _i, _i, _i, _i, C.POINTER(_vp)]),
     "fdi_plan_set_thomas_config": (_i, [_vp, _i]),
     "fdi_plan_set_wait_limit": (_i, [_vp, C.c_longlong]),
+    "fdi_plan_set_resident": (_i, [_vp, C.c_int]),
     "fdi_plan_autotune": (_i, [_vp, _d, _vp, _vp, _i, C.POINTER(_i), _vp]),
     "fdi_plan_enable_timing": (_i, [_vp, _i]),
     "fdi_plan_kernel_times": (_i, [_vp, _i, C.POINTER(C.c_char_p), C.POINTER(_d), C.POINTER(C.c_longlong),
@@ -340,6 +341,12 @@ def set_wait_limit(plan: Plan, cycles: int):
     """Bound (SM cycles, 0 = default) on the waits inside the tensor-core
     kernels; also clears the plan's sticky wait-limit flag."""
     _check(load().fdi_plan_set_wait_limit(plan.handle, int(cycles)), "fdi_plan_set_wait_limit")
+
+
+def set_resident(plan: Plan, enable: bool):
+    """Resident small-grid solve (one cooperative launch per solve) on or off
+    for the plan's fields with x and y extents <= 128 (mixed plans)."""
+    _check(load().fdi_plan_set_resident(plan.handle, 1 if enable else 0), "fdi_plan_set_resident")
 
 
 def set_thomas_config(plan: Plan, lines_per_cta: int):

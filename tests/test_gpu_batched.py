@@ -25,13 +25,14 @@ def fdi():
     return pkg
 
 
-def make_batch(fdi, count, prec, seed=0):
+def make_batch(fdi, count, prec, seed=0, resident=False):
     import torch
     probs = mixed_shape_batch(count, seed)
     plans, lams, rhs, outs, host = [], [], [], [], []
     for q, (n, beta, lam) in enumerate(probs):
         faces = [tanh_faces(n[d], beta) for d in range(3)]
         plans.append(fdi.plan_create(faces, n, prec=prec))
+        fdi.set_resident(plans[-1], resident)
         f = rhs_uniform(n[::-1], q + 1)
         host.append((faces, f))
         rhs.append(torch.from_numpy(f).cuda())
@@ -40,12 +41,14 @@ def make_batch(fdi, count, prec, seed=0):
     return probs, plans, lams, rhs, outs, host
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "mixed_resident"])
 def test_batch_equals_alone_and_oracle(fdi, prec):
+    # mixed_resident: the grids with x, y extents <= 128 share resident
+    # launches in the batch and each has its own alone
     import torch
     p = fdi.PREC_FP64 if prec == "fp64" else fdi.PREC_MIXED_F16
     count = 16 if prec == "fp64" else 64
-    probs, plans, lams, rhs, outs, host = make_batch(fdi, count, p)
+    probs, plans, lams, rhs, outs, host = make_batch(fdi, count, p, resident=prec == "mixed_resident")
     stream = torch.cuda.Stream()
     # alone: each plan solved by itself on the legacy stream (eager)
     alone = []

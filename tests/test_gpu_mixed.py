@@ -57,10 +57,13 @@ def test_tensor_core_transform_matches_fp64(fdi, n, rows, inverse):
     assert err.max() < 2e-6, err.max()
 
 
-def mixed_solve(fdi, faces, bc_lo, bc_hi, lam, sigma, f, alias=False):
+def mixed_solve(fdi, faces, bc_lo, bc_hi, lam, sigma, f, alias=False, resident=False):
+    # resident=True: the resident launch (one cooperative launch per solve)
+    # instead of the pass-by-pass solve
     import torch
     n = tuple(len(fc) - 1 for fc in faces)
     plan = fdi.plan_create(faces, n, bc_lo, bc_hi, prec=fdi.PREC_MIXED_F16)
+    fdi.set_resident(plan, resident)
     rhs = torch.from_numpy(np.ascontiguousarray(f)).cuda()
     out = rhs if alias else torch.empty_like(rhs)
     fdi.field_solve(plan, fdi.FIELD_CELL, sigma, lam, rhs, out)
@@ -71,12 +74,13 @@ def mixed_solve(fdi, faces, bc_lo, bc_hi, lam, sigma, f, alias=False):
     return got, steps, rel, st
 
 
-def test_small_mixed_solve(fdi):
+@pytest.mark.parametrize("resident", [True, False])
+def test_small_mixed_solve(fdi, resident):
     n = (32, 32, 32)
     faces = box_faces(n, 1.5)
     ops = asm.cell_ops(faces, (D, D, D), (D, D, D))
     f = rhs_uniform(n[::-1], 0)
-    got, steps, rel, st = mixed_solve(fdi, faces, (D, D, D), (D, D, D), 1.0, 1.0, f)
+    got, steps, rel, st = mixed_solve(fdi, faces, (D, D, D), (D, D, D), 1.0, 1.0, f, resident=resident)
     assert st == 0 and rel <= MIXED_TOL, (steps, rel)
     assert asm.relative_residual(ops, got, f, 1.0) <= MIXED_TOL
     ref = asm.solve(ops, f, 1.0)
@@ -86,15 +90,17 @@ def test_small_mixed_solve(fdi):
 BCS = [((D, D, D), (D, D, D)), ((N, N, N), (N, N, N)), ((D, N, D), (N, D, N)), ((N, N, D), (N, N, N))]
 
 
+@pytest.mark.parametrize("resident", [True, False])
 @pytest.mark.parametrize("lo,hi", BCS)
 @pytest.mark.parametrize("lam,sigma", [(1e-5, 1.0), (1e-3, 1.0), (1.0, 1.0), (1.0, 0.0)])
-def test_ragged_grids_mixed(fdi, lo, hi, lam, sigma):
+def test_ragged_grids_mixed(fdi, lo, hi, lam, sigma, resident):
     # sizes that are not multiples of the 128-row tile / 64-wide K chunk / 32-wide N pad
+    # (resident: plane class 128, odd x extent, scalar residual pairs)
     n = (67, 13, 29)
     faces = [tanh_faces(67, 1.5), tanh_faces(13, 2.0), tanh_faces(29, 1.2)]
     ops = asm.cell_ops(faces, lo, hi)
     f = rhs_uniform(n[::-1], 3)
-    got, steps, rel, st = mixed_solve(fdi, faces, lo, hi, lam, sigma, f)
+    got, steps, rel, st = mixed_solve(fdi, faces, lo, hi, lam, sigma, f, resident=resident)
     assert st == 0 and rel <= MIXED_TOL, (steps, rel)
     assert asm.relative_residual(ops, got, f, lam, sigma) <= MIXED_TOL
     ref = asm.solve(ops, f, lam, sigma)
@@ -114,7 +120,8 @@ def test_out_may_alias_rhs_mixed(fdi):
     assert asm.relative_residual(ops, got, f, 0.3) <= MIXED_TOL
 
 
-def test_config2_shape_mixed(fdi):
+@pytest.mark.parametrize("resident", [True, False])
+def test_config2_shape_mixed(fdi, resident):
     # 128^3, tanh 2.0: three Dirichlet Helmholtz (dt in {1e-2, 1, 1e3}, Re 1000) + one
     # zero-flux Laplace, refined to 1e-10 and checked against the oracle
     n = (128, 128, 128)
@@ -123,14 +130,14 @@ def test_config2_shape_mixed(fdi):
         lam = dt / 1000.0
         ops = asm.cell_ops(faces, (D, D, D), (D, D, D))
         f = rhs_uniform(n[::-1], seed)
-        got, steps, rel, st = mixed_solve(fdi, faces, (D, D, D), (D, D, D), lam, 1.0, f)
+        got, steps, rel, st = mixed_solve(fdi, faces, (D, D, D), (D, D, D), lam, 1.0, f, resident=resident)
         assert st == 0 and rel <= MIXED_TOL, (dt, steps, rel)
         assert asm.relative_residual(ops, got, f, lam) <= MIXED_TOL
         ref = dec.tpt_solve(f, ops, lam)
         assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
     ops = asm.cell_ops(faces, (N, N, N), (N, N, N))
     f = rhs_uniform(n[::-1], 3)
-    got, steps, rel, st = mixed_solve(fdi, faces, (N, N, N), (N, N, N), 1.0, 0.0, f)
+    got, steps, rel, st = mixed_solve(fdi, faces, (N, N, N), (N, N, N), 1.0, 0.0, f, resident=resident)
     assert st == 0 and rel <= MIXED_TOL, (steps, rel)
     assert asm.relative_residual(ops, got, f, 1.0, 0.0) <= MIXED_TOL
 

@@ -21,11 +21,12 @@ def fdi():
     return pkg
 
 
-def gpu_stokes(fdi, faces, dt, Re, f, prec, precond=1):
+def gpu_stokes(fdi, faces, dt, Re, f, prec, precond=1, resident=False):
     import torch
     n = tuple(len(fc) - 1 for fc in faces)
     plan = fdi.plan_create(faces, n, grid=fdi.GRID_MAC, prec=prec)
     fdi.set_stokes_preconditioner(plan, precond)
+    fdi.set_resident(plan, resident)
     ft = [torch.from_numpy(np.ascontiguousarray(fc)).cuda() for fc in f]
     ut = [torch.empty_like(t) for t in ft]
     vs, ps = st.shapes(faces)
@@ -80,14 +81,16 @@ def test_manufactured_pressure_only(fdi):
     assert np.abs(p.ravel() - p0).max() <= 1e-9 * np.abs(p0).max()
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (3, 1e-10)])
+@pytest.mark.parametrize("prec,tol,resident", [(0, 1e-11, False), (3, 1e-10, False), (3, 1e-10, True)])
 @pytest.mark.parametrize("dt", [1e-2, 1e3])
-def test_config3_stokes_64(fdi, prec, tol, dt):
+def test_config3_stokes_64(fdi, prec, tol, dt, resident):
     # 64^3 staggered no-slip box, tanh 1.5, Re = 1000, Gaussian forcing seeds 0-2;
     # checked with the oracle's assembled operators and its semi-direct solve
+    # (resident: the three velocity solves share one resident launch, the
+    # preconditioner's Laplace solve has its own)
     faces = box_faces((64, 64, 64), 1.5)
     f = forcing(faces, 0)
-    vel, p, it, res, status = gpu_stokes(fdi, faces, dt, 1000.0, f, prec)
+    vel, p, it, res, status = gpu_stokes(fdi, faces, dt, 1000.0, f, prec, resident=resident)
     assert status == 0 and res <= tol, (it, res)
     mom, div = st.saddle_residual(faces, dt, 1000.0, f, vel, p)
     assert mom <= 1e-9 and div <= 1000 * tol, (mom, div)
@@ -109,19 +112,21 @@ def test_paper_preconditioner_small_dt(fdi):
         assert rel(vel[c], vel_o[c]) <= 1e-8
 
 
-@pytest.mark.parametrize("prec", [0, 3])
-def test_stokes_graph_replay_matches_eager(fdi, prec):
+@pytest.mark.parametrize("prec,resident", [(0, False), (3, False), (3, True)])
+def test_stokes_graph_replay_matches_eager(fdi, prec, resident):
     # on an explicit stream the BiCGstab iterations after the first replay one
     # captured graph; the arithmetic is the same launch sequence, so the result
     # equals the eager (legacy-stream) solve bit for bit, also on repeated calls
+    # (resident: cooperative launches inside the graph's device-side loop)
     import torch
     faces = box_faces((24, 20, 18), 1.5)
     f = forcing(faces, 5)
     dt = 1.0
-    vel_e, p_e, it_e, res_e, st_e = gpu_stokes(fdi, faces, dt, 1000.0, f, prec)
+    vel_e, p_e, it_e, res_e, st_e = gpu_stokes(fdi, faces, dt, 1000.0, f, prec, resident=resident)
     assert st_e == 0 and it_e >= 2
     n = tuple(len(fc) - 1 for fc in faces)
     plan = fdi.plan_create(faces, n, grid=fdi.GRID_MAC, prec=prec)
+    fdi.set_resident(plan, resident)
     stream = torch.cuda.Stream()
     ft = [torch.from_numpy(np.ascontiguousarray(fc)).cuda() for fc in f]
     vs, ps = st.shapes(faces)
