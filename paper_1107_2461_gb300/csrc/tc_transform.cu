@@ -143,7 +143,23 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t tmem_base = *tmem_slot;
 
   const long long num_tiles = (a.R + BM - 1) / BM;
-  const long long my_iters = blockIdx.x < num_tiles ? (num_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  // work items: tiles below n_full whole, the tail's tiles as two halves
+  // (columns [0, N_pad / 2) and [N_pad / 2, N_pad)); every role walks the same
+  // items in the same order
+  const long long n_full = (a.n_full > 0 && a.n_full < num_tiles) ? a.n_full : num_tiles;
+  const long long num_items = n_full + 2 * (num_tiles - n_full);
+  const long long my_iters = blockIdx.x < num_items ? (num_items - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  // item `it` of this CTA: its tile, and half = -1 (whole), 0 or 1
+  auto item_tile = [&](long long it, int* half) -> long long {
+    const long long item = blockIdx.x + it * gridDim.x;
+    if (item < n_full) {
+      *half = -1;
+      return item;
+    }
+    const long long h = item - n_full;
+    *half = (int)(h & 1);
+    return n_full + (h >> 1);
+  };
   const int nK = a.nK;
 
   if (warp == 0) {
@@ -175,9 +191,13 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      const uint32_t idesc = tc::idesc_f16_f32(BM, N_pad);
       uint32_t g = 0;
       for (long long it = 0; it < my_iters && !s_abort; ++it) {
+        int half = -1;
+        item_tile(it, &half);
+        // a half item accumulates its columns where the whole tile would
+        const uint32_t coff = half == 1 ? (uint32_t)(N_pad / 2) : 0u;
+        const uint32_t idesc = tc::idesc_f16_f32(BM, half < 0 ? N_pad : N_pad / 2);
         const int buf = (int)(it & 1);
         const uint32_t aph = (uint32_t)((it >> 1) & 1);
         if (!tc::mbar_wait(&acce[buf], aph ^ 1, &s_abort, wl)) {
@@ -186,7 +206,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           break;
         }
         tc::tc_fence_after();
-        const uint32_t d = tmem_base + (uint32_t)(buf * N_pad);
+        const uint32_t d = tmem_base + (uint32_t)(buf * N_pad) + coff;
         bool ok = true;
         for (int kc = 0; kc < nK; ++kc, ++g) {
           const int s = g % STAGES;
@@ -198,7 +218,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           tc::tc_fence_after();
           uint8_t* st = smem + s * STAGE_BYTES;
           const uint32_t ahi = tc::smem_u32(st), alo = tc::smem_u32(st + A_BYTES);
-          const uint32_t bhi = tc::smem_u32(st + 2 * A_BYTES), blo = tc::smem_u32(st + 2 * A_BYTES + B_BYTES);
+          const uint32_t bhi = tc::smem_u32(st + 2 * A_BYTES) + coff * ROWB;
+          const uint32_t blo = tc::smem_u32(st + 2 * A_BYTES + B_BYTES) + coff * ROWB;
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint32_t off = kk * 32;
@@ -306,7 +327,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       uint32_t g = 0;
       for (long long it = 0; it < my_iters && !s_abort; ++it) {
-        const long long tile = blockIdx.x + it * gridDim.x;
+        int half = -1;
+        const long long tile = item_tile(it, &half);
         const int row0 = (int)(tile * BM);
         for (int kc = 0; kc < nK; ++kc, ++g) {
           const int sa = g % NA32;
@@ -349,7 +371,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int g8 = lane >> 3, l8 = lane & 7;  // after the transpose: group of 8 lanes, lane in group
     float vmax = 0.f;
     for (long long it = 0; it < my_iters && !s_abort; ++it) {
-      const long long tile = blockIdx.x + it * gridDim.x;
+      int half = -1;
+      const long long tile = item_tile(it, &half);
+      const int c_lo = half == 1 ? N_pad / 2 : 0, c_hi = half == 0 ? N_pad / 2 : N_pad;
       const int buf = (int)(it & 1);
       const uint32_t aph = (uint32_t)((it >> 1) & 1);
       if (!tc::mbar_wait(&accf[buf], aph, &s_abort, wl)) {
@@ -370,7 +394,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       long long tb[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) tb[e] = __shfl_sync(0xffffffffu, base, 4 * l8 + e);
-      for (int c0 = 0; c0 < N_pad; c0 += 32) {
+      for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
         uint32_t r[32];
         tc::tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * N_pad + c0), r);
         tc::tmem_ld_wait();
@@ -670,6 +694,14 @@ fdi_status launch_kernel(fdi_plan* p, const TcMatrix& m, const CUtensorMap& mapA
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
   const long long grid = tiles < sms ? tiles : sms;
+  // a partial last wave of tiles runs as half-width items spread over twice
+  // as many CTAs (halves stay multiples of 32 columns)
+  TcArgs a2 = args;
+  a2.n_full = tiles;
+  if (tiles > grid && m.N_pad % 64 == 0) {
+    const long long tail = tiles % grid;
+    if (tail > 0 && 2 * tail <= grid) a2.n_full = tiles - tail;
+  }
   CUtensorMap map;
   memcpy(&map, m.tmap, sizeof(CUtensorMap));
   cudaLaunchConfig_t cfg = {};
@@ -682,7 +714,7 @@ fdi_status launch_kernel(fdi_plan* p, const TcMatrix& m, const CUtensorMap& mapA
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = args.pdl ? 1 : 0;
-  FDI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_transform, map, mapA, mapO, args));
+  FDI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_transform, map, mapA, mapO, a2));
   FDI_LAUNCH_CHECK(p);
   return FDI_OK;
 }

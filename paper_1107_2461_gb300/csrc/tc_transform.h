@@ -53,6 +53,9 @@ struct TcArgs {
   long long wait_cycles = 0;        // bound of every wait (cycles); 0: the default
   // filled by the launcher
   int N_pad = 0, nK = 0;
+  // tiles at and past n_full (the last, partial wave of a multi-wave grid) run
+  // as two half-width items of N_pad / 2 output columns each
+  long long n_full = 0;
   const float* col_scale = nullptr;
 };
 

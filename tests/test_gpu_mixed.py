@@ -30,10 +30,12 @@ def pitch4(n):
     return (n + 3) // 4 * 4
 
 
-@pytest.mark.parametrize("n", [16, 64, 100, 129, 256])
-@pytest.mark.parametrize("rows", [128, 1000])
+@pytest.mark.parametrize("n,rows", [(n, r) for n in (16, 64, 100, 129, 256) for r in (128, 1000)] +
+                         [(256, 63488), (128, 65529), (100, 40000)])
 @pytest.mark.parametrize("inverse", [1, 0])
 def test_tensor_core_transform_matches_fp64(fdi, n, rows, inverse):
+    # (the last three: more tiles than SMs with a partial last wave, which runs
+    # as half-width items; a ragged last tile among them)
     # one split-fp16 pass out[r][k] = sum_j T[k][j] in[r][j] vs the FP64 product
     import torch
     faces = [tanh_faces(n, 1.5), tanh_faces(8, 1.0), tanh_faces(8, 1.0)]
