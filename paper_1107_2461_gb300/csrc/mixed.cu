@@ -1111,7 +1111,7 @@ fdi_status mixed_field_solve(fdi_plan* p, int field, double sigma, double lambda
   const MixedAxis* mx = static_cast<const MixedAxis*>(f.ax[0]->mixed);
   const MixedAxis* my = static_cast<const MixedAxis*>(f.ax[1]->mixed);
   const MixedAxis* mz = static_cast<const MixedAxis*>(f.ax[2]->mixed);
-  FDI_TRY(launch_reset_status(p, s));
+  // (the first pass's reduction resets the solve's status)
   FDI_CUDA_TRY(cudaMemsetAsync(p->d_scales, 0, (size_t)(kMaxRefineCap + 2) * kScaleStride * sizeof(float), s));
   const double* b = rhs;
   if (out == rhs) {

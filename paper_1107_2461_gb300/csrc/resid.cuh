@@ -573,6 +573,11 @@ __device__ void finish_block(const double* __restrict__ partials, int nblocks, D
   for (int q = 0; q < nt / 32; ++q)
     for (int c = 0; c < 4; ++c) tt[c] += shf[4 * q + c];
   if (kind == 0) {
+    // the solve's status starts here (no kernel of the solve reads it before)
+    st->tol_used = tol;
+    st->refine_steps = 0;
+    st->iters = 0;
+    st->error = 0;
     st->bnorm2 = tt[1];
     if (want_mean) st->mean_b = tt[2] / tt[3];
     st->rel_res = 1.0;
