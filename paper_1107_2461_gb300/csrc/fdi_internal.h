@@ -144,6 +144,7 @@ struct fdi_plan {
   int stokes_precond = 1;           // 0: L_p^{-1} (paper), 1: L_p^{-1} - lambda I
   int krylov = 0;                   // 0: BiCGstab, 1: BiCGstab(2) (the paper's solver)
   double* kpartials = nullptr;
+  unsigned* kticket = nullptr;      // last-block ticket of the Krylov reductions
   // controls
   double tol = 1e-11;
   int max_refine = 2;

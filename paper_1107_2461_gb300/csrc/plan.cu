@@ -285,6 +285,7 @@ void free_plan(fdi_plan* p) {
     if (q) cudaFree(q);
   if (p->d_kry) cudaFree(p->d_kry);
   if (p->kpartials) cudaFree(p->kpartials);
+  if (p->kticket) cudaFree(p->kticket);
   if (p->d_err) cudaFree(p->d_err);
   if (p->res_bar) cudaFree(p->res_bar);
   if (p->h_flag) cudaFreeHost(p->h_flag);

@@ -131,10 +131,12 @@ __device__ __forceinline__ void block_reduce2(double& a, double& b) {
   }
 }
 
+__device__ void kry_finish_last(const double* partials, KryState* st, int kind, unsigned* ticket);
+
 // partial sums of a.b and c.d (c, d may be null) over n values
 __global__ void __launch_bounds__(kDotThreads) k_dot2(const double* __restrict__ a, const double* __restrict__ b,
                                                       const double* __restrict__ c, const double* __restrict__ d,
-                                                      long long n, double* __restrict__ partials) {
+                                                      long long n, double* __restrict__ partials, KryState* fst, int fkind, unsigned* ticket) {
   double s0 = 0.0, s1 = 0.0;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
     s0 = fma(a[q], b[q], s0);
@@ -145,6 +147,7 @@ __global__ void __launch_bounds__(kDotThreads) k_dot2(const double* __restrict__
     partials[2 * blockIdx.x] = s0;
     partials[2 * blockIdx.x + 1] = s1;
   }
+  kry_finish_last(partials, fst, fkind, ticket);
 }
 
 __device__ __forceinline__ void sum_partials(const double* partials, double& a, double& b) {
@@ -164,8 +167,9 @@ enum {
   KF_L2_CONV = 12, KF_CG_RHO = 13, KF_CG_ALPHA = 14, KF_CG_ITER = 15
 };
 
-__global__ void __launch_bounds__(kDotThreads) k_kry_finish(const double* __restrict__ partials, KryState* st,
-                                                            int kind) {
+// The scalar step after a reduction, by one block (every thread takes part
+// in the fixed-order sum; thread 0 updates the state).
+__device__ void kry_finish_body(const double* partials, KryState* st, int kind) {
   double a, b;
   sum_partials(partials, a, b);
   if (threadIdx.x != 0) return;
@@ -348,6 +352,24 @@ __global__ void __launch_bounds__(kDotThreads) k_kry_finish(const double* __rest
   }
 }
 
+// The producing kernel's last block to finish (atomic ticket after its
+// partials are visible) runs the scalar step and re-arms the ticket, so the
+// reduction needs no second launch; the order of the sums is that of a
+// separate finishing launch.
+__device__ void kry_finish_last(const double* partials, KryState* st, int kind, unsigned* ticket) {
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1 : 0;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  kry_finish_body(partials, st, kind);
+  if (threadIdx.x == 0) *ticket = 0u;
+}
+
 // ---- BiCGstab(2) vector updates (all read the device scalars) ----
 
 // j = 0: u_0 = r_0 - beta u_0;  j = 1: also u_1 = r_1 - beta u_1
@@ -385,12 +407,12 @@ __global__ void k_l2_tau(const KryState* __restrict__ st, double* __restrict__ r
 
 // minimal-residual update: y += g1 r_0 + g''1 r_1, r_0 -= g'2 r_2 + g'1 r_1,
 // u_0 -= g2 u_2 + g1 u_1; partial sums of r_0.r_0
-__global__ void __launch_bounds__(kDotThreads) k_l2_final(const KryState* __restrict__ st, double* __restrict__ y,
+__global__ void __launch_bounds__(kDotThreads) k_l2_final(const KryState* st, double* __restrict__ y,
                                                           double* __restrict__ r0, const double* __restrict__ r1,
                                                           const double* __restrict__ r2, double* __restrict__ u0,
                                                           const double* __restrict__ u1,
                                                           const double* __restrict__ u2, long long n,
-                                                          double* __restrict__ partials) {
+                                                          double* __restrict__ partials, KryState* fst, int fkind, unsigned* ticket) {
   const bool live = !st->done;
   const double g1 = st->g1, g2 = st->g2, gp1 = st->gp1, gp2 = st->gp2, gpp1 = st->gpp1;
   double s0 = 0.0, s1 = 0.0;
@@ -409,6 +431,7 @@ __global__ void __launch_bounds__(kDotThreads) k_l2_final(const KryState* __rest
     partials[2 * blockIdx.x] = s0;
     partials[2 * blockIdx.x + 1] = s1;
   }
+  kry_finish_last(partials, fst, fkind, ticket);
 }
 
 // x = -t
@@ -444,12 +467,12 @@ __global__ void k_bicg_s(const KryState* __restrict__ st, double* __restrict__ s
 
 // x <- x + alpha phat + omega shat with phat = -y, shat = -z (the Laplace solves
 // return -L_p^{-1}); r = s - omega t; partial sums of r.r and rhat.r
-__global__ void __launch_bounds__(kDotThreads) k_bicg_xr(const KryState* __restrict__ st, double* __restrict__ x,
+__global__ void __launch_bounds__(kDotThreads) k_bicg_xr(const KryState* st, double* __restrict__ x,
                                                          const double* __restrict__ y, const double* __restrict__ z,
                                                          double* __restrict__ r, const double* __restrict__ s,
                                                          const double* __restrict__ t,
                                                          const double* __restrict__ rhat, long long n,
-                                                         double* __restrict__ partials) {
+                                                         double* __restrict__ partials, KryState* fst, int fkind, unsigned* ticket) {
   const bool live = !st->done;
   const double al = st->alpha, om = st->omega;
   double s0 = 0.0, s1 = 0.0;
@@ -467,11 +490,12 @@ __global__ void __launch_bounds__(kDotThreads) k_bicg_xr(const KryState* __restr
     partials[2 * blockIdx.x] = s0;
     partials[2 * blockIdx.x + 1] = s1;
   }
+  kry_finish_last(partials, fst, fkind, ticket);
 }
 
 // partial sums of V x and V over the cells
 __global__ void __launch_bounds__(kDotThreads) k_vsum(MacGeom g, const double* __restrict__ x,
-                                                      double* __restrict__ partials) {
+                                                      double* __restrict__ partials, KryState* fst, int fkind, unsigned* ticket) {
   const long long n = (long long)g.nx * g.ny * g.nz;
   double s0 = 0.0, s1 = 0.0;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
@@ -484,6 +508,7 @@ __global__ void __launch_bounds__(kDotThreads) k_vsum(MacGeom g, const double* _
     partials[2 * blockIdx.x] = s0;
     partials[2 * blockIdx.x + 1] = s1;
   }
+  kry_finish_last(partials, fst, fkind, ticket);
 }
 
 // p = (x - mean) / dt
@@ -511,7 +536,7 @@ __global__ void k_axpy(double* __restrict__ y, double c, const double* __restric
 // (V = cell volume)
 __global__ void __launch_bounds__(kDotThreads) k_wdot(MacGeom g, const double* __restrict__ a,
                                                       const double* __restrict__ b, const double* __restrict__ c,
-                                                      double* __restrict__ partials) {
+                                                      double* __restrict__ partials, KryState* fst, int fkind, unsigned* ticket) {
   const long long n = (long long)g.nx * g.ny * g.nz;
   double s0 = 0.0, s1 = 0.0;
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
@@ -524,6 +549,7 @@ __global__ void __launch_bounds__(kDotThreads) k_wdot(MacGeom g, const double* _
     partials[2 * blockIdx.x] = s0;
     partials[2 * blockIdx.x + 1] = s1;
   }
+  kry_finish_last(partials, fst, fkind, ticket);
 }
 
 // p = z (first iteration) or z + beta p
@@ -536,10 +562,10 @@ __global__ void k_cg_p(const KryState* __restrict__ st, double* __restrict__ p, 
 }
 
 // x += alpha p, r -= alpha v (v = A p); partial sums of r.r
-__global__ void __launch_bounds__(kDotThreads) k_cg_xr(const KryState* __restrict__ st, double* __restrict__ x,
+__global__ void __launch_bounds__(kDotThreads) k_cg_xr(const KryState* st, double* __restrict__ x,
                                                        double* __restrict__ r, const double* __restrict__ p,
                                                        const double* __restrict__ v, long long n,
-                                                       double* __restrict__ partials) {
+                                                       double* __restrict__ partials, KryState* fst, int fkind, unsigned* ticket) {
   const bool live = !st->done;
   const double al = st->alpha;
   double s0 = 0.0, s1 = 0.0;
@@ -556,6 +582,7 @@ __global__ void __launch_bounds__(kDotThreads) k_cg_xr(const KryState* __restric
     partials[2 * blockIdx.x] = s0;
     partials[2 * blockIdx.x + 1] = s1;
   }
+  kry_finish_last(partials, fst, fkind, ticket);
 }
 
 __global__ void k_zero(double* __restrict__ a, long long n) {
@@ -662,6 +689,8 @@ fdi_status stokes_setup(fdi_plan* p) {
   }
   FDI_TRY(dalloc(&p->d_kry, 2));
   FDI_TRY(dalloc(&p->kpartials, 2 * kDotBlocks));
+  FDI_TRY(dalloc(&p->kticket, 1));
+  FDI_CUDA_TRY(cudaMemset(p->kticket, 0, sizeof(unsigned)));
   return FDI_OK;
 }
 
@@ -723,9 +752,7 @@ fdi_status cmatvec(fdi_plan* p, const MacGeom& g, double lambda, double* q, doub
 fdi_status wdots(fdi_plan* p, const MacGeom& g, const double* a, const double* b, const double* c, int kind,
                  cudaStream_t s) {
   FDI_KTIMER(p, "stokes_dot", s);
-  k_wdot<<<kDotBlocks, kDotThreads, 0, s>>>(g, a, b, c, p->kpartials);
-  FDI_LAUNCH_CHECK(p);
-  k_kry_finish<<<1, kDotThreads, 0, s>>>(p->kpartials, p->d_kry, kind);
+  k_wdot<<<kDotBlocks, kDotThreads, 0, s>>>(g, a, b, c, p->kpartials, p->d_kry, kind, p->kticket);
   FDI_LAUNCH_CHECK(p);
   return FDI_OK;
 }
@@ -733,9 +760,7 @@ fdi_status wdots(fdi_plan* p, const MacGeom& g, const double* a, const double* b
 fdi_status dots(fdi_plan* p, const double* a, const double* b, const double* c, const double* d, long long n,
                 int kind, cudaStream_t s) {
   FDI_KTIMER(p, "stokes_dot", s);
-  k_dot2<<<kDotBlocks, kDotThreads, 0, s>>>(a, b, c, d, n, p->kpartials);
-  FDI_LAUNCH_CHECK(p);
-  k_kry_finish<<<1, kDotThreads, 0, s>>>(p->kpartials, p->d_kry, kind);
+  k_dot2<<<kDotBlocks, kDotThreads, 0, s>>>(a, b, c, d, n, p->kpartials, p->d_kry, kind, p->kticket);
   FDI_LAUNCH_CHECK(p);
   return FDI_OK;
 }
@@ -913,9 +938,8 @@ fdi_status stokes_solve(fdi_plan* p, double dt, double Re, const double* const f
       FDI_TRY(wdots(p, g, pv, v, nullptr, KF_CG_ALPHA, s));
       {
         FDI_KTIMER(p, "stokes_update", s);
-        k_cg_xr<<<kDotBlocks, kDotThreads, 0, s>>>(p->d_kry, x, r, pv, v, Pc, p->kpartials);
-        FDI_LAUNCH_CHECK(p);
-        k_kry_finish<<<1, kDotThreads, 0, s>>>(p->kpartials, p->d_kry, KF_CG_ITER);
+        k_cg_xr<<<kDotBlocks, kDotThreads, 0, s>>>(p->d_kry, x, r, pv, v, Pc, p->kpartials, p->d_kry, KF_CG_ITER,
+                                                   p->kticket);
         FDI_LAUNCH_CHECK(p);
       }
       return FDI_OK;
@@ -962,9 +986,8 @@ fdi_status stokes_solve(fdi_plan* p, double dt, double Re, const double* const f
       FDI_TRY(dots(p, r2, r2, r0, r2, Pc, KF_L2_MR2, s));
       {
         FDI_KTIMER(p, "stokes_update", s);
-        k_l2_final<<<kDotBlocks, kDotThreads, 0, s>>>(p->d_kry, x, r0, r1, r2, u0, u1, u2, Pc, p->kpartials);
-        FDI_LAUNCH_CHECK(p);
-        k_kry_finish<<<1, kDotThreads, 0, s>>>(p->kpartials, p->d_kry, KF_L2_CONV);
+        k_l2_final<<<kDotBlocks, kDotThreads, 0, s>>>(p->d_kry, x, r0, r1, r2, u0, u1, u2, Pc, p->kpartials,
+                                                      p->d_kry, KF_L2_CONV, p->kticket);
         FDI_LAUNCH_CHECK(p);
       }
       return FDI_OK;
@@ -990,9 +1013,8 @@ fdi_status stokes_solve(fdi_plan* p, double dt, double Re, const double* const f
       FDI_TRY(dots(p, t, sv, t, t, Pc, KF_OMEGA, s));
       {
         FDI_KTIMER(p, "stokes_update", s);
-        k_bicg_xr<<<kDotBlocks, kDotThreads, 0, s>>>(p->d_kry, x, y, z, r, sv, t, rhat, Pc, p->kpartials);
-        FDI_LAUNCH_CHECK(p);
-        k_kry_finish<<<1, kDotThreads, 0, s>>>(p->kpartials, p->d_kry, KF_ITER);
+        k_bicg_xr<<<kDotBlocks, kDotThreads, 0, s>>>(p->d_kry, x, y, z, r, sv, t, rhat, Pc, p->kpartials, p->d_kry,
+                                                     KF_ITER, p->kticket);
         FDI_LAUNCH_CHECK(p);
       }
       return FDI_OK;
@@ -1001,9 +1023,7 @@ fdi_status stokes_solve(fdi_plan* p, double dt, double Re, const double* const f
   }
   // zero-mean pressure q -> p = q / dt
   {
-    k_vsum<<<kDotBlocks, kDotThreads, 0, s>>>(g, x, p->kpartials);
-    FDI_LAUNCH_CHECK(p);
-    k_kry_finish<<<1, kDotThreads, 0, s>>>(p->kpartials, p->d_kry + 1, KF_MEAN);
+    k_vsum<<<kDotBlocks, kDotThreads, 0, s>>>(g, x, p->kpartials, p->d_kry + 1, KF_MEAN, p->kticket);
     FDI_LAUNCH_CHECK(p);
     k_pressure<<<vb, vt, 0, s>>>(p->d_kry + 1, x, 1.0 / dt, pr, Pc);
     FDI_LAUNCH_CHECK(p);
