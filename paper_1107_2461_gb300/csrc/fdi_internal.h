@@ -253,8 +253,9 @@ struct KTimer {
 // serialization is launched while its predecessor in the stream completes and
 // calls pdl_wait() before touching anything the predecessor writes (returns
 // once the predecessor has completed and its memory is visible); a no-op for
-// ordinary launches.  (Triggering the successor early, as each CTA starts,
-// measured slower: its CTAs then held SMs the predecessor's tail needed.)
+// ordinary launches.  (Triggering the successor early measured slower, both
+// as each CTA starts and, in the tensor-core transform, at each CTA's last
+// tile: 0.641 against 0.597 ms per 256^3 solve.)
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>

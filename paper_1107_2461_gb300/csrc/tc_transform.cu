@@ -78,12 +78,11 @@ __device__ __forceinline__ float scale_from_max(float mx) {
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_transform(const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmA,
                    const __grid_constant__ CUtensorMap tmO, TcArgs a) {
-  pdl_wait();
-  if (a.skip && *a.skip) return;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // the swizzled layouts need a 1024-byte aligned base; the launch reserves no
   // slack for re-alignment, so a misaligned block reports an error instead
   if ((tc::smem_u32(smem_raw) & 1023u) != 0u) {
+    pdl_wait();
     if (threadIdx.x == 0) atomicExch(a.err, 7);
     return;
   }
@@ -126,21 +125,42 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   if (warp == 0 && lane == 0) tc::prefetch_tmap(&tmB);
   if (warp == WARP_A && lane == 0) tc::prefetch_tmap(&tmA);
-  // per output column: the matrix row's scale times the input's inverse scale
-  // (both powers of two)
-  float* s_cs = reinterpret_cast<float*>(smem + BAR_OFF + BAR_BYTES);
-  {
-    const float inv_s = 1.0f / scale_from_max(a.scale_in ? *a.scale_in : 1.0f);
-    for (int k = threadIdx.x; k < N_pad; k += blockDim.x) s_cs[k] = a.col_scale[k] * inv_s;
-  }
   if (warp == 1) {
     tc::tmem_alloc(tmem_slot, tmem_cols);
     tc::tmem_relinquish();
+  }
+  // per output column: the matrix row's scale (plan data), times the input's
+  // inverse scale below (both powers of two)
+  float* s_cs = reinterpret_cast<float*>(smem + BAR_OFF + BAR_BYTES);
+  float csk[(NMAX + THREADS - 1) / THREADS];
+#pragma unroll
+  for (int q = 0; q < (NMAX + THREADS - 1) / THREADS; ++q) {
+    const int k = threadIdx.x + q * THREADS;
+    csk[q] = k < N_pad ? a.col_scale[k] : 0.f;
   }
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // Everything above touches no data of the previous kernel in the stream, so
+  // under programmatic dependent launch it overlaps that kernel's tail; from
+  // here on the previous kernel has completed and its writes are visible.
+  pdl_wait();
+  const int skip = a.skip ? *a.skip : 0;  // the same for every thread
+  const float in_scale = a.scale_in ? *a.scale_in : 1.0f;
+  if (skip) {
+    if (warp == 1) tc::tmem_dealloc(tmem_base, tmem_cols);
+    return;
+  }
+  {
+    const float inv_s = 1.0f / scale_from_max(in_scale);
+#pragma unroll
+    for (int q = 0; q < (NMAX + THREADS - 1) / THREADS; ++q) {
+      const int k = threadIdx.x + q * THREADS;
+      if (k < N_pad) s_cs[k] = csk[q] * inv_s;
+    }
+  }
+  __syncthreads();
 
   const long long num_tiles = (a.R + BM - 1) / BM;
   // work items: tiles below n_full whole, the tail's tiles as two halves
@@ -249,7 +269,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     // row r sits at unit u ^ (r & 7), conflict free), scales, splits and stores
     // 16 fp16 hi and lo values into the MMA stage.
     const int ct = (warp - 2) * 32 + lane;  // 0..255
-    const float sA = scale_from_max(a.scale_in ? *a.scale_in : 1.0f);
+    const float sA = scale_from_max(in_scale);
     const int c8 = ct & 3;                  // 32-byte group within the 128-byte row
     // the two (row, 8-wide k group) pieces this thread converts per chunk:
     // K-major slots: rows ct/4 and ct/4 + 64, k group c8; MN-major slots: row
