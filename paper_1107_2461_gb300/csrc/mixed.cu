@@ -508,6 +508,14 @@ __device__ __forceinline__ void cp_async8(unsigned dst, const float2* src) {
 // Laplacian is left to k_thomas_f32 (launched over that pair only).  When ny
 // is odd the last pair's second line is a padding column of the row: it is
 // swept with a valid eigenvalue and excluded from the scale.
+// The forward elimination stores nothing but c' and d' at the block
+// boundaries (shared memory); the back substitution reads f again and
+// recomputes c' and d' of each block of kTB planes from its boundary values,
+// with the forward pass's arithmetic (so the same values), before it runs the
+// block downwards.  Per point that is f read twice and u written once (12
+// bytes) instead of f read, d' written and read back, u written (16 bytes);
+// the top kNBR blocks are still in the copy ring when the back substitution
+// starts and are not read again.
 template <int TL, bool FULL, bool CYL>
 __global__ void __launch_bounds__(TL) k_thomas2_f32(Thomas32Args a, const int* __restrict__ skip) {
   pdl_wait();
@@ -515,6 +523,7 @@ __global__ void __launch_bounds__(TL) k_thomas2_f32(Thomas32Args a, const int* _
   __shared__ float4 s_co[kMaxN];
   __shared__ float2 ring[kNBR * kTB][TL];
   __shared__ float2 ckp[kMaxN / kTB][TL];
+  __shared__ float2 dkp[kMaxN / kTB][TL];
   __shared__ float s_wy[CYL ? kMaxN : 1];
   const int nz = a.nz;
   const float lam = (float)a.lambda;
@@ -560,8 +569,8 @@ __global__ void __launch_bounds__(TL) k_thomas2_f32(Thomas32Args a, const int* _
         fetch(b + kNBR - 1);
         cp_async_wait<kNBR - 1>();
         ckp[b][tid] = make_float2(cp0, cp1);
+        dkp[b][tid] = make_float2(dp0, dp1);
         const float2* rs = &ring[(b % kNBR) * kTB][tid];
-        float2* fo = f + (long long)b * kTB * pl2;
         const int k0 = b * kTB;
 #pragma unroll
         for (int e = 0; e < kTB; ++e) {
@@ -574,38 +583,48 @@ __global__ void __launch_bounds__(TL) k_thomas2_f32(Thomas32Args a, const int* _
             cp1 = co.w * inv1;
             dp0 = fmaf(co.x, fv.x, -co.z * dp0) * inv0;
             dp1 = fmaf(co.x, fv.y, -co.z * dp1) * inv1;
-            fo[e * pl2] = make_float2(dp0, dp1);
           }
         }
       }
       cp_async_wait<0>();
-      for (int q = 0; q < kNBR - 1; ++q) fetch(nb - 1 - q);
+      // blocks nb - kNBR .. nb - 1 are in the ring (f is not written above)
+      auto refetch = [&](int b) {
+        if (b < nb - kNBR) fetch(b);
+        else cp_async_commit();
+      };
+      for (int q = 0; q < kNBR - 1; ++q) refetch(nb - 1 - q);
       float u0 = 0.f, u1 = 0.f;
       for (int b = nb - 1; b >= 0; --b) {
-        fetch(b - (kNBR - 1));
+        refetch(b - (kNBR - 1));
         const int k0 = b * kTB;
-        float cpb0[kTB], cpb1[kTB];
-        const float2 cc = ckp[b][tid];
-        float c0 = cc.x, c1 = cc.y;
+        float cpb0[kTB], cpb1[kTB], dpb0[kTB], dpb1[kTB];
+        const float2 cc = ckp[b][tid], dd = dkp[b][tid];
+        float c0 = cc.x, c1 = cc.y, d0 = dd.x, d1 = dd.y;
+        cp_async_wait<kNBR - 1>();
+        const float2* rs = &ring[(b % kNBR) * kTB][tid];
 #pragma unroll
         for (int e = 0; e < kTB; ++e) {
           if (FULL || k0 + e < nz) {
             const float4 co = s_co[k0 + e];
-            c0 = co.w * rcp_fast(fmaf(-co.z, c0, thomas_diag<CYL>(s0, ly0, co, s_wy, k0 + e)));
-            c1 = co.w * rcp_fast(fmaf(-co.z, c1, thomas_diag<CYL>(s1, ly1, co, s_wy, k0 + e)));
+            const float2 fv = rs[e * TL];
+            const float inv0 = rcp_fast(fmaf(-co.z, c0, thomas_diag<CYL>(s0, ly0, co, s_wy, k0 + e)));
+            const float inv1 = rcp_fast(fmaf(-co.z, c1, thomas_diag<CYL>(s1, ly1, co, s_wy, k0 + e)));
+            c0 = co.w * inv0;
+            c1 = co.w * inv1;
+            d0 = fmaf(co.x, fv.x, -co.z * d0) * inv0;
+            d1 = fmaf(co.x, fv.y, -co.z * d1) * inv1;
           }
           cpb0[e] = c0;
           cpb1[e] = c1;
+          dpb0[e] = d0;
+          dpb1[e] = d1;
         }
-        cp_async_wait<kNBR - 1>();
-        const float2* rs = &ring[(b % kNBR) * kTB][tid];
         float2* fo = f + (long long)k0 * pl2;
 #pragma unroll
         for (int e = kTB - 1; e >= 0; --e) {
           if (FULL || k0 + e < nz) {
-            const float2 dv = rs[e * TL];
-            u0 = fmaf(-cpb0[e], u0, dv.x);
-            u1 = fmaf(-cpb1[e], u1, dv.y);
+            u0 = fmaf(-cpb0[e], u0, dpb0[e]);
+            u1 = fmaf(-cpb1[e], u1, dpb1[e]);
             fo[e * pl2] = make_float2(u0, u1);
             vmax = fmaxf(vmax, fabsf(u0));
             if (second) vmax = fmaxf(vmax, fabsf(u1));
