@@ -102,3 +102,49 @@ def test_stokes_plan_bytes_estimate_scales_with_the_grid(lib):
     assert est((128, 128, 128), fdi.PREC_MIXED_F16) > est((128, 128, 128), fdi.PREC_FP64)
     # 256^3 Stokes plans fit many times over in a GB300's 288 GB
     assert est((256, 256, 256), fdi.PREC_MIXED_F16) < 16e9
+
+
+def test_later_entry_points_reject_null_handles_and_bad_sizes(lib):
+    # every check below answers on the host, before any CUDA call
+    import numpy as np
+    from paper_1107_2461_gb300 import fdi
+    bad = fdi.ERR_INVALID_ARG
+    assert lib.fdi_field_solve(None, 0, 1.0, 1.0, None, None, None) == bad
+    assert lib.fdi_laplace_solve(None, None, None, None) == bad
+    assert lib.fdi_apply_transform(None, 0, 0, 0, None, None, 1, None) == bad
+    assert lib.fdi_plan_eigen(None, 0, 0, None, None, None, None) == bad
+    assert lib.fdi_plan_autotune(None, 1.0, None, None, 1, None, None) == bad
+    cnt = C.c_int(0)
+    assert lib.fdi_plan_kernel_times(None, 0, None, None, None, C.byref(cnt)) == bad
+    assert lib.fdi_plan_reset_kernel_times(None) == bad
+    assert lib.fdi_plan_set_resident(None, 1) == bad
+    assert lib.fdi_plan_set_wait_limit(None, 0) == bad
+    # serving runtime: null handles, and a server that could hold nothing
+    h = C.c_void_p()
+    assert lib.fdi_server_create(0, 4, C.byref(h)) == bad
+    assert lib.fdi_server_create(1 << 30, 0, C.byref(h)) == bad
+    assert lib.fdi_server_create(1 << 30, 65, C.byref(h)) == bad
+    assert lib.fdi_server_create(1 << 30, 4, None) == bad
+    t = C.c_longlong(0)
+    assert lib.fdi_server_submit(None, None, C.byref(t)) == bad
+    assert lib.fdi_server_poll(None, 1, 0, None) == bad
+    assert lib.fdi_server_drain(None) == bad
+    assert lib.fdi_server_stats(None, None) == bad
+    assert lib.fdi_server_destroy(None) == bad
+    # cylindrical plans: extents, radial faces below zero, descending faces
+    dp = C.POINTER(C.c_double)
+    r = np.linspace(0.0, 1.0, 9)
+    z = np.linspace(0.0, 1.0, 9)
+    out = C.c_void_p()
+
+    def cyl(rf, nr, nth, zf, nz):
+        return lib.fdi_plan_create_cyl(rf.ctypes.data_as(dp), nr, nth, zf.ctypes.data_as(dp), nz,
+                                       0, 0, 0, 0, fdi.PREC_FP64, 0, C.byref(out))
+    assert cyl(r, 8, 2, z, 8) == bad
+    assert cyl(r, 8, 300, z, 8) == bad
+    assert cyl(r, 1, 8, z, 8) == bad
+    assert cyl(r - 0.5, 8, 8, z, 8) == bad
+    assert cyl(r[::-1].copy(), 8, 8, z, 8) == bad
+    assert cyl(r, 8, 8, z[::-1].copy(), 8) == bad
+    assert not out.value
+    assert lib.fdi_plan_create_cyl(None, 8, 8, None, 8, 0, 0, 0, 0, fdi.PREC_FP64, 0, C.byref(out)) == bad
