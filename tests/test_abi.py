@@ -148,3 +148,29 @@ def test_later_entry_points_reject_null_handles_and_bad_sizes(lib):
     assert cyl(r, 8, 8, z[::-1].copy(), 8) == bad
     assert not out.value
     assert lib.fdi_plan_create_cyl(None, 8, 8, None, 8, 0, 0, 0, 0, fdi.PREC_FP64, 0, C.byref(out)) == bad
+
+
+def test_binding_refuses_arrays_it_cannot_pass():
+    # argument marshalling only, on the host: CPU, strided or non-FP64 tensors
+    # never reach the C ABI as device pointers, nor device or mistyped arrays
+    # as host buffers
+    torch = pytest.importorskip("torch")
+    import numpy as np
+    from paper_1107_2461_gb300 import fdi
+    with pytest.raises(ValueError):
+        fdi._ptr(torch.zeros(8, dtype=torch.float64))  # not on the device
+    with pytest.raises(TypeError):
+        fdi._ptr(np.zeros(8))
+    assert fdi._ptr(None) is None and fdi._ptr(1234) == 1234
+    with pytest.raises(ValueError):
+        fdi._host_ptr(np.zeros(8, dtype=np.float32), 8)
+    with pytest.raises(ValueError):
+        fdi._host_ptr(np.zeros((4, 4))[:, ::2], 8)
+    with pytest.raises(ValueError):
+        fdi._host_ptr(np.zeros(9), 8)
+    with pytest.raises(ValueError):
+        fdi._host_ptr(torch.zeros(8, dtype=torch.float32), 8)
+    a = np.zeros(8)
+    assert fdi._host_ptr(a, 8) == a.ctypes.data
+    t = torch.zeros(8, dtype=torch.float64)
+    assert fdi._host_ptr(t, 8) == t.data_ptr()
